@@ -1,0 +1,333 @@
+"""Benchmark of the active-dumbbell hot path on B300.
+
+Workload (default): one suspension of S=512 dumbbells (N=1024 spheres) at
+number density 0.002, stroke amplitude 0.2, k0=1, a=0.05, mu=1, T=1,
+dt=1e-3, RPY mobility, FP32 pair math with compensated accumulation and FP64
+state; plus the stroke-averaged model of the same initial condition and the
+pair-distance comparison of the two.
+
+One benchmark step = one stroke period of the whole hot path:
+  * 1000 Heun steps of the microscopic model (two all-pairs evaluations each,
+    spring forces, Heun update, stroke-average accumulation of the centres),
+  * the stroke-averaged model advanced over the same period (dt_SA = T/10),
+  * the pair-distance comparison of the period-averaged centres against the
+    averaged model (read back to the host).
+Metric: sphere-pair interactions per second = 2 N (N-1) Heun steps / s.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank runs its own independent suspension (seed = rank):
+weak scaling, no data-path collective; the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+STEPS_PER_PERIOD = 1000
+SA_STEPS_PER_PERIOD = 10
+FLOPS_PER_PAIR = {"oseen": 27, "rpy": 34}   # algorithmic FP32 flops (FMA = 2), rsqrt not counted
+METRIC = "sphere-pair interactions/s"
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200, help="timed stroke periods")
+    p.add_argument("--warmup", type=int, default=3, help="untimed stroke periods")
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--S", type=int, default=512)
+    p.add_argument("--mobility", default="rpy", choices=["rpy", "oseen"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-sample-steps", type=int, default=400,
+                   help="Heun steps of the oracle timed for the CPU baseline")
+    return p.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload_config(S, mobility, flush):
+    return {"workload": f"single suspension S={S} (N={2 * S}) density 0.002, lambda=0.2, "
+                        f"{mobility.upper()}, FP32 pair math + FP64 state, dt=1e-3, one step = "
+                        f"one stroke period ({STEPS_PER_PERIOD} Heun steps) + stroke-averaged "
+                        f"model + pair-distance comparison",
+            "S": S, "N": 2 * S, "heun_steps_per_step": STEPS_PER_PERIOD,
+            "sa_steps_per_step": SA_STEPS_PER_PERIOD, "mobility": mobility,
+            "l2": flush}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _fp32_peak_tflops(sms, mhz):
+    # 128 FP32 lanes per SM, one FMA (2 flops) per lane per clock
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def _cpu_baseline(S, mobility, nsteps):
+    """The FP64 oracle, as it stands, on the host cores: a bounded sample of the workload."""
+    import oracle
+    from paper_1004_1932_b300 import inputs
+    s = inputs.paper_scale(S, seed=0, mobility=mobility)
+    cores = os.cpu_count()
+    oracle.set_threads(cores)
+    mob = oracle.RPY if mobility == "rpy" else oracle.OSEEN
+    oracle.heun(s.x0, 0, 2, dt=s.dt, mobility=mob, **s.phys())  # load / first touch
+    t0 = time.perf_counter()
+    oracle.heun(s.x0, 0, nsteps, dt=s.dt, mobility=mob, **s.phys())
+    el = time.perf_counter() - t0
+    N = 2 * S
+    return {"value": 2 * N * (N - 1) * nsteps / el, "unit": METRIC, "cores": cores,
+            "kind": "oracle",
+            "sample": f"{nsteps} Heun steps of the same S={S} suspension (FP64 C oracle, OpenMP over "
+                      f"targets), {el:.2f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1004_1932_b300 import inputs
+    S, N = args.S, 2 * args.S
+    cores = os.cpu_count()
+    oracle.set_threads(cores)
+    s = inputs.paper_scale(S, seed=0, mobility=args.mobility)
+    mob = oracle.RPY if args.mobility == "rpy" else oracle.OSEEN
+    per_step = 10   # Heun steps of the oracle per reference step (bounded sample of a period)
+    x = s.x0
+    n = 0
+    for _ in range(args.warmup):
+        x = oracle.heun(x, n, per_step, dt=s.dt, mobility=mob, **s.phys())
+        n += per_step
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        x = oracle.heun(x, n, per_step, dt=s.dt, mobility=mob, **s.phys())
+        n += per_step
+    el = time.perf_counter() - t0
+    value = 2 * N * (N - 1) * per_step * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _workload_config(S, args.mobility, "n/a (CPU)"),
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step = {per_step} Heun steps of the S={S} "
+                                       f"suspension on the FP64 C oracle"},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1004_1932_b300 import dbs, inputs
+    dbs.load()
+
+    S, N = args.S, 2 * args.S
+    s = inputs.paper_scale(S, seed=rank, mobility=args.mobility)
+    stream = torch.cuda.Stream(device=dev)
+    T = 2 * math.pi / s.omega
+    m = STEPS_PER_PERIOD
+    dt_sa = T / SA_STEPS_PER_PERIOD
+    assert abs(m * s.dt - T) < 1e-12
+    total_periods = args.warmup + args.steps + 2
+    l2_bytes = torch.cuda.get_device_properties(dev).L2_cache_size
+    flush_buf = torch.empty(int(2 * l2_bytes) // 4, dtype=torch.float32, device=dev)
+
+    def make():
+        h = dbs.Suspension.from_inputs(s, precision="fp32c", stream=stream, device=local)
+        sa = dbs.StrokeAveraged(s.R0, s.N0, s.phi, s.lam, a=s.a, ell=s.ell, omega=s.omega,
+                                dt=dt_sa, precision="fp32c", stream=stream, device=local)
+        h.enable_period_average(m, max_periods=total_periods)
+        return h, sa
+
+    sa_ref = torch.empty((S, 3), dtype=torch.float64, device=dev)
+    errs = []
+
+    def period(h, sa, k):
+        """One benchmark step: stroke period k of the full hot path."""
+        h.step(m)
+        sa.step(SA_STEPS_PER_PERIOD // 2 if k == 0 else SA_STEPS_PER_PERIOD)
+        if k == 1:
+            sa.copy_centres(sa_ref)
+        if k >= 2:
+            e = dbs.pair_distance_error(S, h.period_average_device(1), h.period_average_device(k),
+                                        sa_ref.data_ptr(), sa.centres_device(), stream=stream)
+            errs.append(e)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # ---- device-resident run -------------------------------------------------
+    h, sa = make()
+    with torch.cuda.stream(stream):
+        for k in range(args.warmup):
+            period(h, sa, k)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    clocks = Clocks(cvd.split(",")[local] if cvd else str(local))
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush_buf.zero_()                       # L2 flush between timed iterations
+            ev0[i].record(stream)
+            period(h, sa, args.warmup + i)
+            ev1[i].record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+    h.sync()
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    pairs_per_step = 2 * N * (N - 1) * m
+    value = ws * pairs_per_step * args.steps / (ms / 1e3)
+    launches_per_step = 2 * m + 2 * SA_STEPS_PER_PERIOD + 1
+
+    # ---- live per-launch duration of the pair-sum kernel (CUDA events, its stream) ----
+    mean_ms = h.step_timed(200)
+    props = torch.cuda.get_device_properties(dev)
+    mhz_max = clk.get("sm_max_mhz") or 2032.0
+    peak = _fp32_peak_tflops(props.multi_processor_count, mhz_max)
+    flops_launch = N * (N - 1) * FLOPS_PER_PAIR[args.mobility]
+    achieved = flops_launch / (mean_ms / 1e3) / 1e12
+    last_err = errs[-1] if errs else None
+    h.close()
+    sa.close()
+
+    # ---- end to end through the C-ABI with host buffers -----------------------
+    e2e = None
+    if not args.no_e2e:
+        x_host = torch.from_numpy(s.x0.copy()).pin_memory()
+        out_host = torch.empty((N, 3), dtype=torch.float64).pin_memory()
+        h2d = x_host.numel() * 8
+        d2h = out_host.numel() * 8 + 4 * 8
+        h, sa = make()
+        errs.clear()
+        with torch.cuda.stream(stream):
+            for k in range(args.warmup):
+                period(h, sa, k)
+        barrier()
+        t0 = time.perf_counter()
+        xs = x_host.numpy()
+        for i in range(args.steps):
+            k = args.warmup + i
+            n_now = k * m
+            h.set_state(xs, n_now)                 # host -> device: this step's input state
+            with torch.cuda.stream(stream):
+                period(h, sa, k)                    # includes the comparison read-back
+            out_host.numpy()[:] = h.positions()     # device -> host: the step's result
+            xs = out_host.numpy()
+        barrier()
+        el = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([el], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": ws * pairs_per_step * args.steps / el, "unit": "pairs/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        h.close()
+        sa.close()
+
+    if rank != 0:
+        return
+    cpu = _cpu_baseline(S, args.mobility, args.cpu_sample_steps) if ws == 1 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 pair math, f64 state",
+        "data": "synthetic (seeded random suspension, no dataset)",
+        "config": _workload_config(S, args.mobility, "flushed between timed steps (2x L2 write)"),
+        "heun_steps_per_s": ws * m * args.steps / (ms / 1e3),
+        "roofline": {"bound": "alu", "kernel": "eval_kernel (pair sum + fused Heun epilogue)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "launch_ms": mean_ms, "flops_per_launch": flops_launch,
+                     "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
+                                   f"{mhz_max:.0f} MHz (max SM clock)"},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "sa_comparison": last_err,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,271 @@
+/*
+ * dbs.h -- C-ABI of the B300-native active-dumbbell suspension library (libdbs.so).
+ *
+ * The library advances S actively driven spring dumbbells (N = 2S spheres)
+ * in unbounded Stokes flow, the microscopic model of Putz, Dunkel & Yeomans,
+ * "CUDA simulations of active dumbbell suspensions":
+ *
+ *   dX_a/dt = sum_b H_ab F_b                       Eq. (1a) at zero temperature
+ *   H_aa = I / (6 pi mu a)                         Eq. (3a)
+ *   H_ab = (I + r r^T/r^2) / (8 pi mu r)
+ *        + 2 a^2 (I - 3 r r^T/r^2) / (24 pi mu r^3)   Eq. (3b) (RPY-Mazur);
+ *                                                  the Oseen form drops the a^2 line
+ *   F = -dU/dX,  U = sum_s k0/2 (d^s - L^s(t))^2,
+ *   L^s(t) = ell + lambda^s sin(omega t + phi^s)   Eq. (4)
+ *   Heun predictor-corrector in time               Sec. IV
+ *
+ * and the stroke-averaged far-field model of Eqs. (9a)-(9e) (Sec. III.B).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Spheres are 0-based.  Dumbbell s owns spheres 2s and 2s+1 (the paper's
+ *    2s-1 and 2s); its orientation points from sphere 2s to sphere 2s+1.
+ *  - Host arrays are row-major doubles, sphere-major [N][3] (positions,
+ *    forces, velocities) or [S] (amplitudes, phases).  They are owned by the
+ *    caller, read or written during the call only, and never retained.
+ *  - Arguments named *_dev are device pointers on the handle's device; the
+ *    library reads or writes them in stream order on the handle's stream and
+ *    returns without synchronising.
+ *  - Handles are opaque and own their device memory (cudaMalloc at create,
+ *    cudaFree at destroy).  A handle must not be used from two host threads
+ *    at once.
+ *  - Every call returns DBS_OK (0) or a negative DBS_E_* status.  Errors are
+ *    sticky: once a handle has failed, every later call on it returns the
+ *    same status until it is destroyed; dbs_last_error() describes it.
+ *  - Time is t_n = n dt, computed in double precision from the step counter n.
+ *
+ * Arithmetic: FP32C evaluates the pair sum of Eq. (3b) in single precision
+ * with per-target compensated (two-sum) accumulation across j-tiles, and
+ * keeps positions, spring forces, the self term, the clock and the Heun
+ * update in double precision.  FP64 does everything in double precision.
+ */
+#ifndef DBS_H
+#define DBS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DBS_API __attribute__((visibility("default")))
+#else
+#define DBS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define DBS_OK 0
+#define DBS_E_ARG (-1)       /* invalid argument (sizes, non-finite values, NULL) */
+#define DBS_E_NOMEM (-2)     /* device allocation failed */
+#define DBS_E_CUDA (-3)      /* a CUDA runtime call failed */
+#define DBS_E_OVERLAP (-4)   /* two distinct spheres coincide, or r < 2a under RPY */
+#define DBS_E_NONFINITE (-5) /* a velocity or position became NaN or Inf */
+#define DBS_E_TIMEOUT (-6)   /* a bounded device-side wait ran out */
+#define DBS_E_STATE (-7)     /* call not valid in the handle's current state */
+
+/* ---- enums --------------------------------------------------------------- */
+#define DBS_OSEEN 0 /* Eq. (3b) without its a^2 line (Sec. II) */
+#define DBS_RPY 1   /* full Eq. (3b), Rotne-Prager-Yamakawa-Mazur */
+
+#define DBS_FP32C 0 /* FP32 pair math, compensated accumulation, FP64 state */
+#define DBS_FP64 1  /* FP64 everywhere */
+
+/* Physical and numerical parameters of one suspension (Secs. II and IV). */
+typedef struct {
+    int64_t S;        /* number of dumbbells, >= 1; N = 2S spheres */
+    double a;         /* sphere radius, > 0 */
+    double mu;        /* viscosity, > 0 */
+    double k0;        /* spring constant, >= 0 */
+    double ell;       /* mean rest length, > 2a + max|lambda| (Sec. II) */
+    double omega;     /* stroke angular frequency, T = 2 pi / omega, > 0 */
+    double dt;        /* time step, > 0 */
+    int32_t mobility; /* DBS_OSEEN or DBS_RPY */
+    int32_t precision;/* DBS_FP32C or DBS_FP64 */
+    void *stream;     /* cudaStream_t for all device work, NULL = a stream the handle creates */
+    int32_t device;   /* CUDA device ordinal, -1 = the calling thread's current device */
+    int32_t flags;    /* reserved, must be 0 */
+} dbs_params;
+
+typedef struct dbs_suspension dbs_suspension;
+
+/*
+ * Create a suspension with initial sphere positions x0 [2S][3] (host).
+ * Stroke amplitudes start at 0 and phases at 0 (passive dumbbells); call
+ * dbs_set_stroke to make them active.  The step counter starts at n = 0.
+ * Errors: DBS_E_ARG (bad parameters, non-finite x0), DBS_E_NOMEM, DBS_E_CUDA.
+ * On failure *out is NULL.
+ */
+DBS_API int dbs_create_suspension(const dbs_params *p, const double *x0, dbs_suspension **out);
+
+/* Release the handle and its device memory (waits for its stream).  NULL is a no-op. */
+DBS_API int dbs_destroy(dbs_suspension *h);
+
+/*
+ * Stroke amplitudes lambda [S] and phases phi [S] (host) of Eq. (4).
+ * Requires ell > 2a + |lambda^s| for every s (Sec. II); else DBS_E_ARG.
+ */
+DBS_API int dbs_set_stroke(dbs_suspension *h, const double *lambda, const double *phase);
+
+/*
+ * Constant external force [2S][3] (host) added to the spring force of every
+ * sphere (Sec. II: F may include external fields).  NULL removes it.
+ */
+DBS_API int dbs_set_external_force(dbs_suspension *h, const double *F);
+
+/*
+ * Advance n >= 0 Heun steps (Sec. IV) on the device.  Asynchronous: returns
+ * after enqueuing; geometry faults found on the device (DBS_E_OVERLAP,
+ * DBS_E_NONFINITE) are reported by the next synchronising call
+ * (dbs_sync, dbs_positions, dbs_velocities, ...).
+ */
+DBS_API int dbs_step(dbs_suspension *h, int64_t n);
+
+/* Wait for the handle's stream and report any device-side fault flag. */
+DBS_API int dbs_sync(dbs_suspension *h);
+
+/*
+ * Velocities v [2S][3] (host) at the current state (x_n, t_n): spring (+
+ * external) forces pushed through Eq. (3).  Synchronising.
+ */
+DBS_API int dbs_velocities(dbs_suspension *h, double *v);
+
+/*
+ * Interaction part only, u_a = sum_{b != a} H_ab F_b (Eq. (3b)), for the
+ * current forces, into u [2S][3] (host).  Diagnostic.  Synchronising.
+ */
+DBS_API int dbs_interaction(dbs_suspension *h, double *u);
+
+/*
+ * Raw mobility product v = H F (Eq. (3), self term included) at the current
+ * positions for an arbitrary force F [2S][3] (host) into v [2S][3] (host).
+ * Does not touch the simulation state.  Synchronising.
+ */
+DBS_API int dbs_mobility_apply(dbs_suspension *h, const double *F, double *v);
+
+/*
+ * Velocities at the current state into a device buffer v_dev [2S][3] doubles.
+ * Asynchronous (stream-ordered on the handle's stream); faults are reported by
+ * the next synchronising call.
+ */
+DBS_API int dbs_velocities_device(dbs_suspension *h, double *v_dev);
+
+/*
+ * Profiling form of dbs_step: n Heun steps launched one kernel at a time (no
+ * graph), with a CUDA event pair recorded on the handle's stream around every
+ * pair-sum launch; *mean_ms receives the mean device time of one launch.
+ * Results are identical to dbs_step.  Synchronising.
+ */
+DBS_API int dbs_step_timed(dbs_suspension *h, int64_t n, double *mean_ms);
+
+/* Current positions x [2S][3] (host).  Synchronising. */
+DBS_API int dbs_positions(dbs_suspension *h, double *x);
+
+/* Copy current positions to a device buffer x_dev [2S][3] doubles, stream-ordered. */
+DBS_API int dbs_positions_device(dbs_suspension *h, double *x_dev);
+
+/* Step counter n and time t = n dt. */
+DBS_API int dbs_get_time(dbs_suspension *h, int64_t *n, double *t);
+
+/* Checkpoint: positions x [2S][3] (host) and step counter n (restart is bit-exact). */
+DBS_API int dbs_get_state(dbs_suspension *h, double *x, int64_t *n);
+DBS_API int dbs_set_state(dbs_suspension *h, const double *x, int64_t n);
+
+/*
+ * Stroke averages of the geometric centre, Eqs. (6b) and (7b): after this
+ * call, every complete block of m steps (a stroke period T = m dt) starting
+ * at the current step counter yields one snapshot
+ *   Rbar^s_k = (1/T) int_{t_k}^{t_k+T} (X_{2s} + X_{2s+1})/2 du
+ * (trapezoid rule on the discrete trajectory), accumulated on the device in
+ * the integrator's epilogue.  At most max_periods snapshots are kept.
+ * m = 0 switches the accumulation off.
+ */
+DBS_API int dbs_enable_period_average(dbs_suspension *h, int64_t m, int64_t max_periods);
+
+/* Number of complete snapshots so far. */
+DBS_API int dbs_period_count(dbs_suspension *h, int64_t *count);
+
+/* Snapshots k0 .. k0+count-1 into Rbar [count][S][3] (host).  Synchronising. */
+DBS_API int dbs_period_averages(dbs_suspension *h, int64_t k0, int64_t count, double *Rbar);
+
+/* Device pointer of snapshot k ([S][3] doubles) for device-side comparisons. */
+DBS_API int dbs_period_average_device(dbs_suspension *h, int64_t k, const double **Rbar_dev);
+
+/* Static description of the last error on h (or of the last failed create if h is NULL). */
+DBS_API const char *dbs_last_error(const dbs_suspension *h);
+
+/* Static name of a status code. */
+DBS_API const char *dbs_status_string(int status);
+
+/* ======================================================================== */
+/* Stroke-averaged far-field model, Eqs. (9a)-(9e), Sec. III.B              */
+/* ======================================================================== */
+
+typedef struct {
+    int64_t S;        /* number of dumbbells, >= 2 */
+    double a;         /* sphere radius */
+    double ell;       /* mean dumbbell length */
+    double omega;     /* stroke angular frequency */
+    double dt;        /* Heun time step of the averaged dynamics */
+    double kpref;     /* K prefactor; Eq. (9d) prints 15/64 */
+    int32_t precision;/* DBS_FP32C or DBS_FP64 */
+    int32_t device;   /* -1 = current */
+    void *stream;     /* cudaStream_t, NULL = own stream */
+} dbs_sa_params;
+
+typedef struct dbs_sa dbs_sa;
+
+/*
+ * Create the averaged model with centres R [S][3], unit orientations N [S][3],
+ * phases phi [S] and amplitudes lambda [S] (host).  Unequal amplitudes enter
+ * as lambda^s lambda^r / ell^2 in place of (lambda/ell)^2.
+ */
+DBS_API int dbs_sa_create(const dbs_sa_params *p, const double *R, const double *N, const double *phi,
+                  const double *lambda, dbs_sa **out);
+DBS_API int dbs_sa_destroy(dbs_sa *h);
+
+/*
+ * n Heun steps of
+ *   dR^s/dt = sum_{r != s} J^{sr},  dN^s/dt = -(I - N^s N^s^T) sum_{r != s} K^{sr},
+ * N renormalised to unit length after every step.  Asynchronous.
+ */
+DBS_API int dbs_sa_step(dbs_sa *h, int64_t n);
+
+/* Rates (dR/dt, dN/dt) at the current state into Rdot, Ndot [S][3] (host). */
+DBS_API int dbs_sa_rates(dbs_sa *h, double *Rdot, double *Ndot);
+
+/* Current state R, N [S][3] (host).  Synchronising. */
+DBS_API int dbs_sa_state(dbs_sa *h, double *R, double *N);
+
+/* Device pointer of the current centres R ([S][3] doubles). */
+DBS_API int dbs_sa_centres_device(dbs_sa *h, const double **R_dev);
+
+/* Stream-ordered copy of the current centres into R_dev [S][3] doubles (device). */
+DBS_API int dbs_sa_copy_centres(dbs_sa *h, double *R_dev);
+
+DBS_API const char *dbs_sa_last_error(const dbs_sa *h);
+
+/* ======================================================================== */
+/* Comparison of the two models (pair-distance error)                       */
+/* ======================================================================== */
+
+/*
+ * For S centres in four device arrays [S][3] (doubles), with
+ *   dA^{sr} = |A1^s - A1^r| - |A0^s - A0^r|,  dB^{sr} likewise,
+ * computes over all pairs s < r:
+ *   out[0] = max |dA - dB|,  out[1] = sum (dA - dB)^2,  out[2] = sum dB^2,
+ *   out[3] = number of pairs,
+ * into out (host, 4 doubles).  Stream-ordered on `stream`, then synchronises.
+ */
+DBS_API int dbs_pair_distance_error(int64_t S, const double *A0_dev, const double *A1_dev,
+                            const double *B0_dev, const double *B1_dev, double *out,
+                            void *stream);
+
+/* Library version string. */
+DBS_API const char *dbs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DBS_H */

@@ -199,3 +199,15 @@ def pair_distance_error(dD_model, dD_ref):
     e = np.abs(dD_model[iu] - dD_ref[iu])
     return {"max": float(e.max()), "rms": float(np.sqrt(np.mean(e * e))),
             "ref_rms": float(np.sqrt(np.mean(dD_ref[iu] ** 2)))}
+
+
+def mobility_rows(x, F, rows, a, mu, mobility=RPY):
+    """Eq. (3) evaluated only for the target spheres ``rows`` (int array)."""
+    x, px = _c(x)
+    F, pF = _c(F)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    v = np.empty((rows.shape[0], 3))
+    lib().orc_mobility_rows(_i64(x.shape[0]), px, pF, ctypes.c_double(a), ctypes.c_double(mu),
+                            ctypes.c_int(mobility), rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                            _i64(rows.shape[0]), v.ctypes.data_as(_dp))
+    return v

@@ -356,3 +356,22 @@ void orc_pair_distance_change(int64_t S, const double *R0, const double *R1, dou
         }
     }
 }
+
+/*
+ * Eq. (3) for a subset of target spheres: v[k] = H F restricted to rows[k]
+ * (same sum, same order as orc_mobility_apply), for parity checks of large
+ * systems on sampled targets.
+ */
+void orc_mobility_rows(int64_t N, const double *x, const double *F, double a, double mu,
+                       int mobility, const int64_t *rows, int64_t nrows, double *v)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < nrows; ++k) {
+        int64_t al = rows[k];
+        double acc[3];
+        for (int i = 0; i < 3; ++i) acc[i] = F[3 * al + i] / (6.0 * ORC_PI * mu * a);
+        for (int64_t be = 0; be < N; ++be)
+            if (be != al) add_pair_term(x + 3 * al, x + 3 * be, F + 3 * be, a, mu, mobility, acc);
+        for (int i = 0; i < 3; ++i) v[3 * k + i] = acc[i];
+    }
+}

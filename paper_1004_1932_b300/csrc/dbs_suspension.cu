@@ -1,0 +1,787 @@
+// C-ABI of the microscopic suspension (include/dbs.h): handle management,
+// validation, launches of the fused pair-sum/Heun kernels, checkpointing and
+// stroke averages.  All device work runs on the handle's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "dbs.h"
+#include "dbs_common.cuh"
+#include "eval_kernel.cuh"
+
+using namespace dbs;
+
+namespace {
+
+constexpr int BT32 = 128;    // dumbbells per CTA (FP32C, large systems)
+constexpr int TILE32 = 128;  // dumbbell records per shared-memory tile (FP32C, 6 KB)
+constexpr int BT32S = 32;    // dumbbells per CTA (FP32C, S <= SMALL_S): more CTAs, spread epilogue
+constexpr int TILE32S = 64;
+constexpr int BT64 = 128;    // dumbbells per CTA (FP64)
+constexpr int TILE64 = 64;   // dumbbell records per tile (FP64, 6 KB)
+constexpr int BT64S = 32;
+constexpr int TILE64S = 32;
+constexpr int64_t SMALL_S = 2048;
+constexpr int TRIG_RING = 4096;  // entries of the (sin, cos)(omega t_k) ring (power of two)
+constexpr int GRAPH_STEPS = 32;  // Heun steps per captured CUDA graph
+
+thread_local char g_create_error[256] = "";
+
+const double PI = 3.14159265358979323846;
+
+}  // namespace
+
+struct dbs_suspension {
+    dbs_params p{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int64_t S = 0, N = 0;
+    int64_t n_host = 0;
+    int status = DBS_OK;
+    char msg[256] = "";
+    // device state
+    double *x = nullptr, *v0 = nullptr, *Fd = nullptr, *Fext = nullptr, *lam = nullptr,
+           *sinphi = nullptr, *cosphi = nullptr, *vout = nullptr, *Ftmp = nullptr;
+    void *packA = nullptr, *packB = nullptr, *packT = nullptr;
+    double2 *trig = nullptr;
+    int64_t trig_hi = -1;  // ring holds (sin, cos)(omega t_k) for k <= trig_hi (last TRIG_RING/2 fills)
+    float *part = nullptr;
+    unsigned *tickets = nullptr, *done = nullptr;
+    int64_t *step = nullptr;
+    int *flags = nullptr;
+    double *Racc = nullptr, *Rbar = nullptr;
+    int64_t avg_m = 0, avg_n0 = 0, avg_maxk = 0;
+    double cx = 0, cy = 0, cz = 0;
+    double lam_max = 0;
+    // launch configuration
+    int grid = 1, chunks = 1, bt = 128;
+    // captured block of GRAPH_STEPS Heun steps
+    cudaGraphExec_t graph = nullptr;
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+static int fail(dbs_suspension *h, int status, const char *fmt, ...)
+{
+    char *buf = h ? h->msg : g_create_error;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 256, fmt, ap);
+    va_end(ap);
+    if (h) h->status = status;
+    return status;
+}
+
+#define CK(h, call)                                                                        \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail((h), e_ == cudaErrorMemoryAllocation ? DBS_E_NOMEM : DBS_E_CUDA,   \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define GUARD(h)                                                  \
+    do {                                                          \
+        if (!(h)) return DBS_E_ARG;                               \
+        if ((h)->status != DBS_OK) return (h)->status;            \
+        cudaError_t e0_ = cudaSetDevice((h)->device);             \
+        if (e0_ != cudaSuccess)                                   \
+            return fail((h), DBS_E_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e0_)); \
+    } while (0)
+
+static bool all_finite(const double *a, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+static bool is_f64(const dbs_suspension *h) { return h->p.precision == DBS_FP64; }
+
+static size_t pack_bytes(const dbs_suspension *h)
+{
+    return (size_t)h->S * (is_f64(h) ? sizeof(DbF64) : sizeof(DbF32));
+}
+
+static EvalArgs base_args(const dbs_suspension *h)
+{
+    EvalArgs A{};
+    A.S = h->S;
+    A.N = h->N;
+    A.x = h->x;
+    A.v0 = h->v0;
+    A.Fd = h->Fd;
+    A.Fext = h->Fext;
+    A.lam = h->lam;
+    A.sinphi = h->sinphi;
+    A.cosphi = h->cosphi;
+    A.trig = h->trig;
+    A.trig_mask = TRIG_RING - 1;
+    A.vout = h->vout;
+    A.part = h->part;
+    A.tickets = h->tickets;
+    A.done = h->done;
+    A.step = h->step;
+    A.Racc = h->Racc;
+    A.Rbar = h->Rbar;
+    A.avg_n0 = h->avg_n0;
+    A.avg_m = h->avg_m;
+    A.avg_maxk = h->avg_maxk;
+    A.flags = h->flags;
+    A.cx = h->cx;
+    A.cy = h->cy;
+    A.cz = h->cz;
+    A.a = h->p.a;
+    A.inv6pimua = 1.0 / (6.0 * PI * h->p.mu * h->p.a);
+    A.inv8pimu = 1.0 / (8.0 * PI * h->p.mu);
+    A.inv8pimu_f = (float)A.inv8pimu;
+    A.k0 = h->p.k0;
+    A.ell = h->p.ell;
+    A.omega = h->p.omega;
+    A.dt = h->p.dt;
+    A.c2 = (float)(2.0 * h->p.a * h->p.a / 3.0);
+    A.c3 = (float)(-2.0 * h->p.a * h->p.a);
+    A.overlap_r2 = (float)(4.0 * h->p.a * h->p.a);
+    A.chunks = h->chunks;
+    A.apply_self = 1;
+    return A;
+}
+
+template <typename Real, int MOB, int PHASE>
+static void launch_eval_t(const EvalArgs &A, int grid, int bt, cudaStream_t st)
+{
+    if constexpr (sizeof(Real) == 4) {
+        if (bt == BT32S) eval_kernel<float, MOB, PHASE, BT32S, TILE32S><<<grid, BT32S, 0, st>>>(A);
+        else eval_kernel<float, MOB, PHASE, BT32, TILE32><<<grid, BT32, 0, st>>>(A);
+    } else {
+        if (bt == BT64S) eval_kernel<double, MOB, PHASE, BT64S, TILE64S><<<grid, BT64S, 0, st>>>(A);
+        else eval_kernel<double, MOB, PHASE, BT64, TILE64><<<grid, BT64, 0, st>>>(A);
+    }
+}
+
+template <typename Real>
+static void launch_eval_r(int mob, int phase, const EvalArgs &A, int grid, int bt, cudaStream_t st)
+{
+    if (mob == DBS_OSEEN) {
+        if (phase == PHASE_PREDICT) launch_eval_t<Real, 0, PHASE_PREDICT>(A, grid, bt, st);
+        else if (phase == PHASE_CORRECT) launch_eval_t<Real, 0, PHASE_CORRECT>(A, grid, bt, st);
+        else launch_eval_t<Real, 0, PHASE_APPLY>(A, grid, bt, st);
+    } else {
+        if (phase == PHASE_PREDICT) launch_eval_t<Real, 1, PHASE_PREDICT>(A, grid, bt, st);
+        else if (phase == PHASE_CORRECT) launch_eval_t<Real, 1, PHASE_CORRECT>(A, grid, bt, st);
+        else launch_eval_t<Real, 1, PHASE_APPLY>(A, grid, bt, st);
+    }
+}
+
+static void launch_eval(const dbs_suspension *h, int phase, const EvalArgs &A)
+{
+    if (is_f64(h)) launch_eval_r<double>(h->p.mobility, phase, A, h->grid, h->bt, h->stream);
+    else launch_eval_r<float>(h->p.mobility, phase, A, h->grid, h->bt, h->stream);
+}
+
+// Pack the current positions with spring (+ external) forces at t_n, or with a
+// given force Fgiven, into `out`; optionally record the FP64 force in Fd.
+template <typename Real>
+__global__ void pack_kernel(EvalArgs A, const double *Fgiven, double *Fd_out, void *out)
+{
+    using Rec = typename RecOf<Real>::type;
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= A.S) return;
+    double xq[6];
+    for (int k = 0; k < 6; ++k) xq[k] = A.x[6 * s + k];
+    double F[6];
+    if (Fgiven) {
+        for (int k = 0; k < 6; ++k) F[k] = Fgiven[6 * s + k];
+    } else {
+        const double2 sc = A.trig[(*A.step) & A.trig_mask];
+        const double L = rest_length(A.ell, A.lam[s], sc.x, sc.y, A.sinphi[s], A.cosphi[s]);
+        spring_force(xq, xq + 3, L, A.k0, F, F + 3);
+        if (A.Fext)
+            for (int k = 0; k < 6; ++k) F[k] += A.Fext[6 * s + k];
+    }
+    if (Fd_out)
+        for (int k = 0; k < 6; ++k) Fd_out[6 * s + k] = F[k];
+    store_rec((Rec *)out, s, xq, F, A);
+}
+
+// ring[k & mask] = (sin, cos)(omega t_k), t_k = k dt, for k in [k0, k0 + count)
+__global__ void trig_fill_kernel(double2 *ring, int mask, int64_t k0, int count, double omega,
+                                 double dt)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int64_t k = k0 + i;
+    double sw, cw;
+    sincos(omega * ((double)k * dt), &sw, &cw);
+    ring[k & mask] = make_double2(sw, cw);
+}
+
+__global__ void avg_start_kernel(EvalArgs A)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= A.S) return;
+    for (int k = 0; k < 3; ++k) A.Racc[3 * s + k] = 0.5 * 0.5 * (A.x[6 * s + k] + A.x[6 * s + 3 + k]);
+}
+
+__global__ void set_step_kernel(int64_t *step, int64_t n) { *step = n; }
+
+// Make the trig ring cover step indices up to k_hi.  Fills are stream-ordered
+// before the launches that read them and cover TRIG_RING/2 steps at a time, so
+// a fill never overwrites an entry that later-enqueued work still needs.
+static int ensure_trig(dbs_suspension *h, int64_t k_hi)
+{
+    while (h->trig_hi < k_hi) {
+        const int count = TRIG_RING / 2;
+        trig_fill_kernel<<<(count + 127) / 128, 128, 0, h->stream>>>(
+            h->trig, TRIG_RING - 1, h->trig_hi + 1, count, h->p.omega, h->p.dt);
+        CK(h, cudaGetLastError());
+        h->trig_hi += count;
+    }
+    return DBS_OK;
+}
+
+static int reset_trig(dbs_suspension *h, int64_t n)
+{
+    h->trig_hi = n - 1;
+    return ensure_trig(h, n + 1);
+}
+
+static int repack(dbs_suspension *h)
+{
+    EvalArgs A = base_args(h);
+    const int thr = 128;
+    const int blocks = (int)((h->S + thr - 1) / thr);
+    if (is_f64(h)) pack_kernel<double><<<blocks, thr, 0, h->stream>>>(A, nullptr, h->Fd, h->packA);
+    else pack_kernel<float><<<blocks, thr, 0, h->stream>>>(A, nullptr, h->Fd, h->packA);
+    CK(h, cudaGetLastError());
+    return DBS_OK;
+}
+
+static void drop_graph(dbs_suspension *h)
+{
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+}
+
+template <typename K>
+static int occupancy(K kern, int bt)
+{
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, bt, 0) != cudaSuccess || occ < 1)
+        occ = 1;
+    return occ;
+}
+
+// Choose the j-split C and the persistent grid.  With U = iblocks * C equal
+// work units over G = SMs * occupancy resident CTAs, the kernel takes
+// ceil(U / G) unit-times of which U / G do work; C minimises that waste
+// (ties within 1% go to the smaller C, which writes fewer partial sums).
+static void choose_launch(dbs_suspension *h)
+{
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    const bool small = h->S <= SMALL_S;
+    int bt, occ;
+    if (is_f64(h)) {
+        bt = small ? BT64S : BT64;
+        occ = small ? occupancy(eval_kernel<double, 1, PHASE_CORRECT, BT64S, TILE64S>, bt)
+                    : occupancy(eval_kernel<double, 1, PHASE_CORRECT, BT64, TILE64>, bt);
+    } else {
+        bt = small ? BT32S : BT32;
+        occ = small ? occupancy(eval_kernel<float, 1, PHASE_CORRECT, BT32S, TILE32S>, bt)
+                    : occupancy(eval_kernel<float, 1, PHASE_CORRECT, BT32, TILE32>, bt);
+    }
+    h->bt = bt;
+    const int64_t gfull = (int64_t)sms * occ;
+    const int64_t iblocks = (h->S + bt - 1) / bt;
+    const int64_t max_chunks = std::max<int64_t>(1, h->S / (small ? 16 : 32));
+    auto waste = [&](int64_t c) {
+        const int64_t u = iblocks * c;
+        const int64_t waves = (u + gfull - 1) / gfull;
+        return (double)(waves * gfull) / (double)u;
+    };
+    double best = 1e300;
+    for (int64_t c = 1; c <= max_chunks; ++c) best = std::min(best, waste(c));
+    int64_t C = 1;
+    for (int64_t c = 1; c <= max_chunks; ++c)
+        if (waste(c) <= best * 1.01) {
+            C = c;
+            break;
+        }
+    h->chunks = (int)C;
+    h->grid = (int)std::min<int64_t>(gfull, iblocks * C);
+}
+
+static int alloc_all(dbs_suspension *h)
+{
+    const size_t v3 = sizeof(double) * 3 * h->N;
+    CK(h, cudaMalloc(&h->x, v3));
+    CK(h, cudaMalloc(&h->v0, v3));
+    CK(h, cudaMalloc(&h->Fd, v3));
+    CK(h, cudaMalloc(&h->vout, v3));
+    CK(h, cudaMalloc(&h->Ftmp, v3));
+    CK(h, cudaMalloc(&h->lam, sizeof(double) * h->S));
+    CK(h, cudaMalloc(&h->sinphi, sizeof(double) * h->S));
+    CK(h, cudaMalloc(&h->cosphi, sizeof(double) * h->S));
+    CK(h, cudaMalloc(&h->packA, pack_bytes(h)));
+    CK(h, cudaMalloc(&h->packB, pack_bytes(h)));
+    CK(h, cudaMalloc(&h->packT, pack_bytes(h)));
+    CK(h, cudaMalloc(&h->trig, sizeof(double2) * TRIG_RING));
+    const int64_t iblocks = (h->S + h->bt - 1) / h->bt;
+    if (h->chunks > 1) {
+        const size_t pb = (size_t)h->chunks * h->S * (is_f64(h) ? 6 * sizeof(double) : 12 * sizeof(float));
+        CK(h, cudaMalloc(&h->part, pb));
+    }
+    CK(h, cudaMalloc(&h->tickets, sizeof(unsigned) * iblocks));
+    CK(h, cudaMemsetAsync(h->tickets, 0, sizeof(unsigned) * iblocks, h->stream));
+    CK(h, cudaMalloc(&h->done, sizeof(unsigned)));
+    CK(h, cudaMemsetAsync(h->done, 0, sizeof(unsigned), h->stream));
+    CK(h, cudaMalloc(&h->step, sizeof(int64_t)));
+    CK(h, cudaMemsetAsync(h->step, 0, sizeof(int64_t), h->stream));
+    CK(h, cudaMalloc(&h->flags, sizeof(int)));
+    CK(h, cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
+    CK(h, cudaMalloc(&h->Racc, sizeof(double) * 3 * h->S));
+    // passive start: lambda = 0, phi = 0 (sin 0 = 0, cos 0 = 1)
+    std::vector<double> zeros(h->S, 0.0), ones(h->S, 1.0);
+    CK(h, cudaMemcpy(h->lam, zeros.data(), sizeof(double) * h->S, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->sinphi, zeros.data(), sizeof(double) * h->S, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->cosphi, ones.data(), sizeof(double) * h->S, cudaMemcpyHostToDevice));
+    return DBS_OK;
+}
+
+static void free_all(dbs_suspension *h)
+{
+    drop_graph(h);
+    void *bufs[] = {h->x, h->v0, h->Fd, h->Fext, h->lam, h->sinphi, h->cosphi, h->vout, h->Ftmp, h->packA,
+                    h->packB, h->packT, h->trig, h->part, h->tickets, h->done, h->step, h->flags,
+                    h->Racc, h->Rbar};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+}
+
+static void set_centre(dbs_suspension *h, const double *x)
+{
+    double lo[3] = {x[0], x[1], x[2]}, hi[3] = {x[0], x[1], x[2]};
+    for (int64_t i = 0; i < h->N; ++i)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = std::min(lo[k], x[3 * i + k]);
+            hi[k] = std::max(hi[k], x[3 * i + k]);
+        }
+    h->cx = 0.5 * (lo[0] + hi[0]);
+    h->cy = 0.5 * (lo[1] + hi[1]);
+    h->cz = 0.5 * (lo[2] + hi[2]);
+}
+
+static int check_flags(dbs_suspension *h)
+{
+    CK(h, cudaStreamSynchronize(h->stream));
+    int f = 0;
+    CK(h, cudaMemcpy(&f, h->flags, sizeof(int), cudaMemcpyDeviceToHost));
+    if (f & FLAG_OVERLAP)
+        return fail(h, DBS_E_OVERLAP, "two spheres closer than 2a (RPY) or coincident");
+    if (f & FLAG_NONFINITE) return fail(h, DBS_E_NONFINITE, "non-finite velocity or position");
+    if (f & FLAG_TIMEOUT) return fail(h, DBS_E_TIMEOUT, "device-side wait timed out");
+    return DBS_OK;
+}
+
+// one Heun step: predictor packA -> packB, corrector packB -> packA
+static void enqueue_heun(dbs_suspension *h)
+{
+    EvalArgs A = base_args(h);
+    A.pack_in = h->packA;
+    A.pack_out = h->packB;
+    launch_eval(h, PHASE_PREDICT, A);
+    A.pack_in = h->packB;
+    A.pack_out = h->packA;
+    launch_eval(h, PHASE_CORRECT, A);
+}
+
+static int build_graph(dbs_suspension *h)
+{
+    cudaGraph_t g = nullptr;
+    CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < GRAPH_STEPS; ++k) enqueue_heun(h);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (e != cudaSuccess) return fail(h, DBS_E_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->graph = nullptr;
+        return fail(h, DBS_E_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    return DBS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C-ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *dbs_version(void) { return "dbs 0.1 (sm_103a)"; }
+
+const char *dbs_status_string(int s)
+{
+    switch (s) {
+    case DBS_OK: return "DBS_OK";
+    case DBS_E_ARG: return "DBS_E_ARG";
+    case DBS_E_NOMEM: return "DBS_E_NOMEM";
+    case DBS_E_CUDA: return "DBS_E_CUDA";
+    case DBS_E_OVERLAP: return "DBS_E_OVERLAP";
+    case DBS_E_NONFINITE: return "DBS_E_NONFINITE";
+    case DBS_E_TIMEOUT: return "DBS_E_TIMEOUT";
+    case DBS_E_STATE: return "DBS_E_STATE";
+    default: return "DBS_E_UNKNOWN";
+    }
+}
+
+const char *dbs_last_error(const dbs_suspension *h) { return h ? h->msg : g_create_error; }
+
+int dbs_create_suspension(const dbs_params *p, const double *x0, dbs_suspension **out)
+{
+    if (!out) return fail(nullptr, DBS_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (!p || !x0) return fail(nullptr, DBS_E_ARG, "params or x0 is NULL");
+    if (p->S < 1 || p->S > (int64_t(1) << 29)) return fail(nullptr, DBS_E_ARG, "S out of range (1 .. 2^29)");
+    const double vals[] = {p->a, p->mu, p->k0, p->ell, p->omega, p->dt};
+    if (!all_finite(vals, 6)) return fail(nullptr, DBS_E_ARG, "non-finite parameter");
+    if (!(p->a > 0 && p->mu > 0 && p->omega > 0 && p->dt > 0 && p->k0 >= 0))
+        return fail(nullptr, DBS_E_ARG, "a, mu, omega, dt must be > 0 and k0 >= 0");
+    if (!(p->ell > 2 * p->a)) return fail(nullptr, DBS_E_ARG, "ell must exceed 2a (Sec. II)");
+    if (p->mobility != DBS_OSEEN && p->mobility != DBS_RPY)
+        return fail(nullptr, DBS_E_ARG, "mobility must be DBS_OSEEN or DBS_RPY");
+    if (p->precision != DBS_FP32C && p->precision != DBS_FP64)
+        return fail(nullptr, DBS_E_ARG, "precision must be DBS_FP32C or DBS_FP64");
+    if (p->flags != 0) return fail(nullptr, DBS_E_ARG, "flags must be 0");
+    if (!all_finite(x0, 6 * p->S)) return fail(nullptr, DBS_E_ARG, "non-finite x0");
+
+    dbs_suspension *h = new (std::nothrow) dbs_suspension();
+    if (!h) return fail(nullptr, DBS_E_NOMEM, "host allocation failed");
+    h->p = *p;
+    h->S = p->S;
+    h->N = 2 * p->S;
+    int dev = p->device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    h->device = dev;
+    int rc = DBS_OK;
+    auto bail = [&](int r) {
+        snprintf(g_create_error, sizeof(g_create_error), "%s", h->msg);
+        free_all(h);
+        if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+        delete h;
+        return r;
+    };
+    if (cudaSetDevice(dev) != cudaSuccess) {
+        fail(h, DBS_E_CUDA, "cudaSetDevice(%d) failed", dev);
+        return bail(DBS_E_CUDA);
+    }
+    if (p->stream) {
+        h->stream = (cudaStream_t)p->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            fail(h, DBS_E_CUDA, "stream creation failed");
+            return bail(DBS_E_CUDA);
+        }
+        h->own_stream = true;
+    }
+    choose_launch(h);
+    if ((rc = alloc_all(h)) != DBS_OK) return bail(rc);
+    set_centre(h, x0);
+    if ((rc = reset_trig(h, 0)) != DBS_OK) return bail(rc);
+    if (cudaMemcpyAsync(h->x, x0, sizeof(double) * 3 * h->N, cudaMemcpyHostToDevice, h->stream) !=
+        cudaSuccess) {
+        fail(h, DBS_E_CUDA, "upload of x0 failed");
+        return bail(DBS_E_CUDA);
+    }
+    if ((rc = repack(h)) != DBS_OK) return bail(rc);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        fail(h, DBS_E_CUDA, "create: %s", cudaGetErrorString(cudaGetLastError()));
+        return bail(DBS_E_CUDA);
+    }
+    *out = h;
+    return DBS_OK;
+}
+
+int dbs_destroy(dbs_suspension *h)
+{
+    if (!h) return DBS_OK;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_all(h);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return DBS_OK;
+}
+
+int dbs_set_stroke(dbs_suspension *h, const double *lambda, const double *phase)
+{
+    GUARD(h);
+    if (!lambda || !phase) return DBS_E_ARG;
+    if (!all_finite(lambda, h->S) || !all_finite(phase, h->S)) return DBS_E_ARG;
+    double lmax = 0;
+    for (int64_t s = 0; s < h->S; ++s) lmax = std::max(lmax, std::fabs(lambda[s]));
+    if (!(h->p.ell > 2 * h->p.a + lmax)) return DBS_E_ARG;  // Sec. II: ell > 2a + lambda
+    h->lam_max = lmax;
+    std::vector<double> sp(h->S), cp(h->S);
+    for (int64_t s = 0; s < h->S; ++s) {
+        sp[s] = std::sin(phase[s]);
+        cp[s] = std::cos(phase[s]);
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(h->lam, lambda, sizeof(double) * h->S, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->sinphi, sp.data(), sizeof(double) * h->S, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->cosphi, cp.data(), sizeof(double) * h->S, cudaMemcpyHostToDevice));
+    int rc = repack(h);
+    if (rc) return rc;
+    CK(h, cudaStreamSynchronize(h->stream));
+    return DBS_OK;
+}
+
+int dbs_set_external_force(dbs_suspension *h, const double *F)
+{
+    GUARD(h);
+    if (F && !all_finite(F, 3 * h->N)) return DBS_E_ARG;
+    drop_graph(h);
+    if (!F) {
+        if (h->Fext) {
+            CK(h, cudaStreamSynchronize(h->stream));
+            cudaFree(h->Fext);
+            h->Fext = nullptr;
+        }
+    } else {
+        if (!h->Fext) CK(h, cudaMalloc(&h->Fext, sizeof(double) * 3 * h->N));
+        CK(h, cudaMemcpyAsync(h->Fext, F, sizeof(double) * 3 * h->N, cudaMemcpyHostToDevice, h->stream));
+    }
+    int rc = repack(h);
+    if (rc) return rc;
+    CK(h, cudaStreamSynchronize(h->stream));
+    return DBS_OK;
+}
+
+int dbs_step(dbs_suspension *h, int64_t n)
+{
+    GUARD(h);
+    if (n < 0) return DBS_E_ARG;
+    int64_t left = n, k = h->n_host;
+    int rc;
+    if (left >= GRAPH_STEPS) {
+        if (!h->graph && (rc = build_graph(h)) != DBS_OK) return rc;
+        while (left >= GRAPH_STEPS) {
+            if ((rc = ensure_trig(h, k + GRAPH_STEPS)) != DBS_OK) return rc;
+            CK(h, cudaGraphLaunch(h->graph, h->stream));
+            left -= GRAPH_STEPS;
+            k += GRAPH_STEPS;
+        }
+    }
+    for (; left > 0; --left, ++k) {
+        if ((rc = ensure_trig(h, k + 1)) != DBS_OK) return rc;
+        enqueue_heun(h);
+    }
+    CK(h, cudaGetLastError());
+    h->n_host += n;
+    return DBS_OK;
+}
+
+int dbs_sync(dbs_suspension *h)
+{
+    GUARD(h);
+    return check_flags(h);
+}
+
+static int apply_to_host(dbs_suspension *h, const void *pack, double *Fd, int self, double *out)
+{
+    EvalArgs A = base_args(h);
+    A.pack_in = pack;
+    A.Fd = Fd;
+    A.apply_self = self;
+    launch_eval(h, PHASE_APPLY, A);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpyAsync(out, h->vout, sizeof(double) * 3 * h->N, cudaMemcpyDeviceToHost, h->stream));
+    return check_flags(h);
+}
+
+int dbs_velocities(dbs_suspension *h, double *v)
+{
+    GUARD(h);
+    if (!v) return DBS_E_ARG;
+    return apply_to_host(h, h->packA, h->Fd, 1, v);
+}
+
+int dbs_interaction(dbs_suspension *h, double *u)
+{
+    GUARD(h);
+    if (!u) return DBS_E_ARG;
+    return apply_to_host(h, h->packA, h->Fd, 0, u);
+}
+
+int dbs_mobility_apply(dbs_suspension *h, const double *F, double *v)
+{
+    GUARD(h);
+    if (!F || !v) return DBS_E_ARG;
+    if (!all_finite(F, 3 * h->N)) return DBS_E_ARG;
+    CK(h, cudaMemcpyAsync(h->Ftmp, F, sizeof(double) * 3 * h->N, cudaMemcpyHostToDevice, h->stream));
+    EvalArgs A = base_args(h);
+    const int thr = 128, blocks = (int)((h->S + thr - 1) / thr);
+    if (is_f64(h)) pack_kernel<double><<<blocks, thr, 0, h->stream>>>(A, h->Ftmp, nullptr, h->packT);
+    else pack_kernel<float><<<blocks, thr, 0, h->stream>>>(A, h->Ftmp, nullptr, h->packT);
+    CK(h, cudaGetLastError());
+    return apply_to_host(h, h->packT, h->Ftmp, 1, v);
+}
+
+int dbs_velocities_device(dbs_suspension *h, double *v_dev)
+{
+    GUARD(h);
+    if (!v_dev) return DBS_E_ARG;
+    EvalArgs A = base_args(h);
+    A.pack_in = h->packA;
+    A.vout = v_dev;
+    launch_eval(h, PHASE_APPLY, A);
+    CK(h, cudaGetLastError());
+    return DBS_OK;
+}
+
+int dbs_step_timed(dbs_suspension *h, int64_t n, double *mean_ms)
+{
+    GUARD(h);
+    if (n < 1 || !mean_ms) return DBS_E_ARG;
+    cudaEvent_t ev[4];
+    for (auto &e : ev) CK(h, cudaEventCreate(&e));
+    double total = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        int rc = ensure_trig(h, h->n_host + k + 1);
+        if (rc) return rc;
+        EvalArgs A = base_args(h);
+        A.pack_in = h->packA;
+        A.pack_out = h->packB;
+        CK(h, cudaEventRecord(ev[0], h->stream));
+        launch_eval(h, PHASE_PREDICT, A);
+        CK(h, cudaEventRecord(ev[1], h->stream));
+        A.pack_in = h->packB;
+        A.pack_out = h->packA;
+        CK(h, cudaEventRecord(ev[2], h->stream));
+        launch_eval(h, PHASE_CORRECT, A);
+        CK(h, cudaEventRecord(ev[3], h->stream));
+        CK(h, cudaEventSynchronize(ev[3]));
+        float a = 0, b = 0;
+        CK(h, cudaEventElapsedTime(&a, ev[0], ev[1]));
+        CK(h, cudaEventElapsedTime(&b, ev[2], ev[3]));
+        total += a + b;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    h->n_host += n;
+    *mean_ms = total / (2.0 * n);
+    return check_flags(h);
+}
+
+int dbs_positions(dbs_suspension *h, double *x)
+{
+    GUARD(h);
+    if (!x) return DBS_E_ARG;
+    CK(h, cudaMemcpyAsync(x, h->x, sizeof(double) * 3 * h->N, cudaMemcpyDeviceToHost, h->stream));
+    return check_flags(h);
+}
+
+int dbs_positions_device(dbs_suspension *h, double *x_dev)
+{
+    GUARD(h);
+    if (!x_dev) return DBS_E_ARG;
+    CK(h, cudaMemcpyAsync(x_dev, h->x, sizeof(double) * 3 * h->N, cudaMemcpyDeviceToDevice, h->stream));
+    return DBS_OK;
+}
+
+int dbs_get_time(dbs_suspension *h, int64_t *n, double *t)
+{
+    GUARD(h);
+    if (n) *n = h->n_host;
+    if (t) *t = (double)h->n_host * h->p.dt;
+    return DBS_OK;
+}
+
+int dbs_get_state(dbs_suspension *h, double *x, int64_t *n)
+{
+    GUARD(h);
+    if (n) *n = h->n_host;
+    if (x) return dbs_positions(h, x);
+    return DBS_OK;
+}
+
+int dbs_set_state(dbs_suspension *h, const double *x, int64_t n)
+{
+    GUARD(h);
+    if (!x || n < 0 || !all_finite(x, 3 * h->N)) return DBS_E_ARG;
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpyAsync(h->x, x, sizeof(double) * 3 * h->N, cudaMemcpyHostToDevice, h->stream));
+    set_step_kernel<<<1, 1, 0, h->stream>>>(h->step, n);
+    CK(h, cudaGetLastError());
+    h->n_host = n;
+    int rc = reset_trig(h, n);
+    if (rc) return rc;
+    rc = repack(h);
+    if (rc) return rc;
+    CK(h, cudaStreamSynchronize(h->stream));
+    return DBS_OK;
+}
+
+int dbs_enable_period_average(dbs_suspension *h, int64_t m, int64_t max_periods)
+{
+    GUARD(h);
+    if (m < 0 || (m > 0 && max_periods < 1)) return DBS_E_ARG;
+    drop_graph(h);
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (h->Rbar) {
+        cudaFree(h->Rbar);
+        h->Rbar = nullptr;
+    }
+    h->avg_m = m;
+    h->avg_maxk = m > 0 ? max_periods : 0;
+    h->avg_n0 = h->n_host;
+    if (m > 0) {
+        CK(h, cudaMalloc(&h->Rbar, sizeof(double) * 3 * h->S * max_periods));
+        EvalArgs A = base_args(h);
+        const int thr = 128, blocks = (int)((h->S + thr - 1) / thr);
+        avg_start_kernel<<<blocks, thr, 0, h->stream>>>(A);
+        CK(h, cudaGetLastError());
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
+    return DBS_OK;
+}
+
+int dbs_period_count(dbs_suspension *h, int64_t *count)
+{
+    GUARD(h);
+    if (!count) return DBS_E_ARG;
+    *count = h->avg_m > 0 ? std::min(h->avg_maxk, (h->n_host - h->avg_n0) / h->avg_m) : 0;
+    return DBS_OK;
+}
+
+int dbs_period_averages(dbs_suspension *h, int64_t k0, int64_t count, double *Rbar)
+{
+    GUARD(h);
+    int64_t have = 0;
+    dbs_period_count(h, &have);
+    if (!Rbar || k0 < 0 || count < 0 || k0 + count > have) return DBS_E_ARG;
+    CK(h, cudaMemcpyAsync(Rbar, h->Rbar + 3 * h->S * k0, sizeof(double) * 3 * h->S * count,
+                          cudaMemcpyDeviceToHost, h->stream));
+    return check_flags(h);
+}
+
+int dbs_period_average_device(dbs_suspension *h, int64_t k, const double **Rbar_dev)
+{
+    GUARD(h);
+    int64_t have = 0;
+    dbs_period_count(h, &have);
+    if (!Rbar_dev || k < 0 || k >= have) return DBS_E_ARG;
+    *Rbar_dev = h->Rbar + 3 * h->S * k;
+    return DBS_OK;
+}
+
+}  // extern "C"

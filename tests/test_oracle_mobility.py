@@ -142,3 +142,13 @@ def test_interaction_is_velocity_minus_stokes_drag():
         u = oracle.interaction(x, F, A, MU, mob)
         v = oracle.mobility_apply(x, F, A, MU, mob)
         np.testing.assert_allclose(u + F / (6 * math.pi * MU * A), v, rtol=1e-13, atol=1e-14)
+
+
+def test_rows_match_full_apply():
+    rng = np.random.default_rng(11)
+    x = rng.uniform(-5, 5, size=(40, 3))
+    F = rng.normal(size=(40, 3))
+    rows = np.array([0, 7, 39, 13])
+    for mob in (oracle.OSEEN, oracle.RPY):
+        full = oracle.mobility_apply(x, F, A, MU, mob)
+        np.testing.assert_array_equal(oracle.mobility_rows(x, F, rows, A, MU, mob), full[rows])
