@@ -262,6 +262,44 @@ DBS_API int dbs_pair_distance_error(int64_t S, const double *A0_dev, const doubl
                             const double *B0_dev, const double *B1_dev, double *out,
                             void *stream);
 
+/* ======================================================================== */
+/* Allocation-free mobility product                                         */
+/* ======================================================================== */
+
+/*
+ * Largest number of dumbbells dbs_mobility_apply_noalloc accepts (N = 2S
+ * spheres).  Its scratch memory, about 3.3 MB, is a fixed array inside the
+ * library, held on every GPU that loads the library until the process exits.
+ */
+#define DBS_NOALLOC_MAX_S 4096
+
+/*
+ * v = H F (Eq. (3): self term plus the FP32 compensated pair sum) for S
+ * dumbbells whose positions x_dev [2S][3], forces F_dev [2S][3] and output
+ * v_dev [2S][3] are caller-owned device buffers (doubles) on the current
+ * device; mobility is DBS_OSEEN or DBS_RPY.  Work is enqueued on `stream`
+ * (NULL = legacy default stream) and the call waits for it, returning
+ * DBS_E_OVERLAP / DBS_E_NONFINITE for geometry faults.
+ *
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate device memory while they run -- code inside a framework that
+ * owns all device memory through its own capped pool, or a latency-critical
+ * loop where cudaMalloc/cudaFree would stall the device.  It needs no handle
+ * and calls no allocator: its scratch (packed j-data, chunk partial sums,
+ * arrival counters) lives in one static device array that every call shares.
+ *  - S > DBS_NOALLOC_MAX_S (or S < 1) is rejected with DBS_E_ARG.
+ *  - The array keeps the last call's contents; the counters that must start
+ *    at zero are cleared at the start of every call.
+ *  - Calls that overlap on the GPU (two streams, two host threads) race on
+ *    the array: serialise them.
+ *  - The first call on each device performs a one-time set-up (it looks up
+ *    the array's device address); make that first call before any stream
+ *    capture.
+ */
+DBS_API int dbs_mobility_apply_noalloc(int64_t S, const double *x_dev, const double *F_dev,
+                                       double a, double mu, int32_t mobility, double *v_dev,
+                                       void *stream);
+
 /* Library version string. */
 DBS_API const char *dbs_version(void);
 

@@ -322,6 +322,23 @@ def pair_distance_error(S, A0, A1, B0, B1, stream=None):
             "ref_rms": float(np.sqrt(out[2] / out[3])), "pairs": int(out[3])}
 
 
+NOALLOC_MAX_S = 4096
+
+
+def mobility_apply_noalloc(S, x_dev, F_dev, *, a, mu, mobility="rpy", v_dev, stream=None):
+    """v = H F on caller-owned device buffers without any allocation
+    (``dbs_mobility_apply_noalloc``): for callers that may not allocate device
+    memory while they run.  Shares one static scratch array per GPU; serialise
+    overlapping calls."""
+    rc = load().dbs_mobility_apply_noalloc(
+        _i64(int(S)), ctypes.c_void_p(_devptr(x_dev)), ctypes.c_void_p(_devptr(F_dev)),
+        ctypes.c_double(a), ctypes.c_double(mu), ctypes.c_int32(_mob(mobility)),
+        ctypes.c_void_p(_devptr(v_dev)),
+        None if stream is None else ctypes.c_void_p(_devptr_stream(stream)))
+    if rc != OK:
+        raise DbsError(rc, "dbs_mobility_apply_noalloc")
+
+
 class DeviceView:
     """Zero-copy view of library-owned device memory for torch (``torch.as_tensor``)."""
 
