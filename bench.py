@@ -50,6 +50,7 @@ def _args():
     p.add_argument("--S", type=int, default=512)
     p.add_argument("--mobility", default="rpy", choices=["rpy", "oseen"])
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-large", action="store_true", help="skip the N=65536 kernel measurement")
     p.add_argument("--cpu-sample-steps", type=int, default=400,
                    help="Heun steps of the oracle timed for the CPU baseline")
     return p.parse_args()
@@ -262,6 +263,21 @@ def run_ours(args):
     h.close()
     sa.close()
 
+    # ---- the same kernel on the large single system (S=32768, N=65536) --------
+    large = None
+    if not args.no_large:
+        sl = inputs.paper_scale(32768, seed=rank, mobility=args.mobility)
+        hl = dbs.Suspension.from_inputs(sl, precision="fp32c", stream=stream, device=local)
+        hl.step_timed(2)
+        ms_l = hl.step_timed(6)
+        hl.close()
+        Nl = 2 * 32768
+        ach_l = Nl * (Nl - 1) * FLOPS_PER_PAIR[args.mobility] / (ms_l / 1e3) / 1e12
+        large = {"workload": "single suspension S=32768 (N=65536), density 0.002, same kernel",
+                 "launch_ms": ms_l, "achieved": ach_l, "peak": peak, "unit": "TFLOP/s",
+                 "frac": ach_l / peak,
+                 "pairs_per_s": 2 * Nl * (Nl - 1) / (2 * ms_l / 1e3)}
+
     # ---- end to end through the C-ABI with host buffers -----------------------
     e2e = None
     if not args.no_e2e:
@@ -317,6 +333,7 @@ def run_ours(args):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
         "sa_comparison": last_err,
+        "large_system_kernel": large,
     }
     print(json.dumps(line), flush=True)
 

@@ -65,7 +65,8 @@ int setup_device(int dev)
     if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return DBS_E_CUDA;
     int occ = 0, sms = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &occ, eval_kernel<float, DBS_RPY, PHASE_APPLY, NA_BT, NA_TDB>, NA_BT, 0) != cudaSuccess)
+            &occ, eval_kernel<float, DBS_RPY, PHASE_APPLY, NA_BT, NA_TDB>, NA_BT,
+            eval_smem_bytes<float>(NA_BT, NA_TDB, NA_MAX_CHUNKS)) != cudaSuccess)
         return DBS_E_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return DBS_E_CUDA;
@@ -152,10 +153,11 @@ extern "C" DBS_API int dbs_mobility_apply_noalloc(int64_t S, const double *x_dev
         return DBS_E_CUDA;
     noalloc_pack_kernel<<<(int)((S + 127) / 128), 128, 0, st>>>(A, F_dev);
     const int grid = (int)std::min<int64_t>(gfull, iblocks * C);
+    const size_t smem = eval_smem_bytes<float>(NA_BT, NA_TDB, (int)C);
     if (mobility == DBS_RPY)
-        eval_kernel<float, DBS_RPY, PHASE_APPLY, NA_BT, NA_TDB><<<grid, NA_BT, 0, st>>>(A);
+        eval_kernel<float, DBS_RPY, PHASE_APPLY, NA_BT, NA_TDB><<<grid, NA_BT, smem, st>>>(A);
     else
-        eval_kernel<float, DBS_OSEEN, PHASE_APPLY, NA_BT, NA_TDB><<<grid, NA_BT, 0, st>>>(A);
+        eval_kernel<float, DBS_OSEEN, PHASE_APPLY, NA_BT, NA_TDB><<<grid, NA_BT, smem, st>>>(A);
     if (cudaGetLastError() != cudaSuccess) return DBS_E_CUDA;
     int flags = 0;
     if (cudaMemcpyAsync(&flags, base + OFF_MISC, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)

@@ -155,15 +155,42 @@ static EvalArgs base_args(const dbs_suspension *h)
     return A;
 }
 
+// Launch with programmatic stream serialisation (PDL): the grid may be scheduled
+// while the previous kernel on the stream is still running; the kernel waits
+// for it with griddepcontrol.wait before reading its results.
+template <typename K>
+static void launch_pdl(K kern, int grid, int bt, size_t smem, cudaStream_t st, const EvalArgs &A)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(bt);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, A);
+}
+
 template <typename Real, int MOB, int PHASE>
 static void launch_eval_t(const EvalArgs &A, int grid, int bt, cudaStream_t st)
 {
     if constexpr (sizeof(Real) == 4) {
-        if (bt == BT32S) eval_kernel<float, MOB, PHASE, BT32S, TILE32S><<<grid, BT32S, 0, st>>>(A);
-        else eval_kernel<float, MOB, PHASE, BT32, TILE32><<<grid, BT32, 0, st>>>(A);
+        if (bt == BT32S)
+            launch_pdl(eval_kernel<float, MOB, PHASE, BT32S, TILE32S>, grid, BT32S,
+                       eval_smem_bytes<float>(BT32S, TILE32S, A.chunks), st, A);
+        else
+            launch_pdl(eval_kernel<float, MOB, PHASE, BT32, TILE32>, grid, BT32,
+                       eval_smem_bytes<float>(BT32, TILE32, A.chunks), st, A);
     } else {
-        if (bt == BT64S) eval_kernel<double, MOB, PHASE, BT64S, TILE64S><<<grid, BT64S, 0, st>>>(A);
-        else eval_kernel<double, MOB, PHASE, BT64, TILE64><<<grid, BT64, 0, st>>>(A);
+        if (bt == BT64S)
+            launch_pdl(eval_kernel<double, MOB, PHASE, BT64S, TILE64S>, grid, BT64S,
+                       eval_smem_bytes<double>(BT64S, TILE64S, A.chunks), st, A);
+        else
+            launch_pdl(eval_kernel<double, MOB, PHASE, BT64, TILE64>, grid, BT64,
+                       eval_smem_bytes<double>(BT64, TILE64, A.chunks), st, A);
     }
 }
 
@@ -291,35 +318,47 @@ static void choose_launch(dbs_suspension *h)
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     const bool small = h->S <= SMALL_S;
-    int bt, occ;
-    if (is_f64(h)) {
-        bt = small ? BT64S : BT64;
-        occ = small ? occupancy(eval_kernel<double, 1, PHASE_CORRECT, BT64S, TILE64S>, bt)
-                    : occupancy(eval_kernel<double, 1, PHASE_CORRECT, BT64, TILE64>, bt);
-    } else {
-        bt = small ? BT32S : BT32;
-        occ = small ? occupancy(eval_kernel<float, 1, PHASE_CORRECT, BT32S, TILE32S>, bt)
-                    : occupancy(eval_kernel<float, 1, PHASE_CORRECT, BT32, TILE32>, bt);
-    }
+    const bool f64 = is_f64(h);
+    const int bt = f64 ? (small ? BT64S : BT64) : (small ? BT32S : BT32);
+    const int tdb = f64 ? (small ? TILE64S : TILE64) : (small ? TILE32S : TILE32);
     h->bt = bt;
-    const int64_t gfull = (int64_t)sms * occ;
+    auto occ_for = [&](int64_t c) {
+        int occ = 0;
+        const size_t smem = f64 ? eval_smem_bytes<double>(bt, tdb, (int)c)
+                                : eval_smem_bytes<float>(bt, tdb, (int)c);
+        cudaError_t e;
+        if (f64)
+            e = small ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                            &occ, eval_kernel<double, 1, PHASE_CORRECT, BT64S, TILE64S>, bt, smem)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                            &occ, eval_kernel<double, 1, PHASE_CORRECT, BT64, TILE64>, bt, smem);
+        else
+            e = small ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                            &occ, eval_kernel<float, 1, PHASE_CORRECT, BT32S, TILE32S>, bt, smem)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                            &occ, eval_kernel<float, 1, PHASE_CORRECT, BT32, TILE32>, bt, smem);
+        return (e == cudaSuccess && occ > 0) ? occ : 1;
+    };
     const int64_t iblocks = (h->S + bt - 1) / bt;
-    const int64_t max_chunks = std::max<int64_t>(1, h->S / (small ? 16 : 32));
-    auto waste = [&](int64_t c) {
+    // chunks of at least 16 (small systems) / 32 dumbbell records; small systems
+    // also keep C x BT within the shared-memory staging of the partials
+    const int64_t max_chunks = std::max<int64_t>(
+        1, small ? std::min<int64_t>(h->S / 16, STAGE_MAX / bt) : h->S / 32);
+    double best = 1e300;
+    int64_t C = 1;
+    for (int64_t c = 1; c <= max_chunks; ++c) {
+        const int64_t gfull = (int64_t)sms * occ_for(c);
         const int64_t u = iblocks * c;
         const int64_t waves = (u + gfull - 1) / gfull;
-        return (double)(waves * gfull) / (double)u;
-    };
-    double best = 1e300;
-    for (int64_t c = 1; c <= max_chunks; ++c) best = std::min(best, waste(c));
-    int64_t C = 1;
-    for (int64_t c = 1; c <= max_chunks; ++c)
-        if (waste(c) <= best * 1.01) {
+        // time ~ waves * (work per unit ~ 1/c); choose the smallest time, ties to smaller c
+        const double t = (double)waves / (double)c;
+        if (t < best * 0.99) {
+            best = t;
             C = c;
-            break;
         }
+    }
     h->chunks = (int)C;
-    h->grid = (int)std::min<int64_t>(gfull, iblocks * C);
+    h->grid = (int)std::min<int64_t>((int64_t)sms * occ_for(C), iblocks * C);
 }
 
 static int alloc_all(dbs_suspension *h)

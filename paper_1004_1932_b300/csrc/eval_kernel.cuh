@@ -193,9 +193,9 @@ __device__ __forceinline__ void sweep_f32(const DbF32 *__restrict__ pin, DbF32 *
         const bool diag = (t0 < blk_hi) && (t0 + len > blk_lo);
         float2 qa[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         float2 qb[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        if (!diag && len == TDB) {
+        if (!diag) {
 #pragma unroll 2
-            for (int k = 0; k < TDB; ++k) {
+            for (int k = 0; k < len; ++k) {
                 const float4 ra = tile[k].a, rb = tile[k].b, rc = tile[k].c;
                 const float2 jx = make_float2(ra.x, ra.y), jy = make_float2(ra.z, ra.w);
                 const float2 jz = make_float2(rb.x, rb.y), gx = make_float2(rb.z, rb.w);
@@ -264,18 +264,47 @@ __device__ __forceinline__ void sweep_f64(const DbF64 *__restrict__ pin, DbF64 *
 // (the host limits S to 2^29).
 //
 // FP32: at most 85 registers per thread (768 / BT resident CTAs of BT threads,
-// 24 warps per SM).  FP64 keeps the compiler's choice.
+// 24 warps per SM).  FP64 keeps the compiler's choice.  Dynamic shared memory:
+// eval_smem_bytes(BT, TDB, C).
 template <typename Real, int BT>
 struct MinBlocks { static constexpr int value = sizeof(Real) == 4 ? 768 / BT : 1; };
+
+// FP32C partials are staged through shared memory when C x BT <= STAGE_MAX
+// (24 KB); larger splits (large systems, where the fixup is a negligible part
+// of the launch) read them from L2 directly.
+constexpr int STAGE_MAX = 512;
+__host__ __device__ inline bool staged_fixup(int bt, int chunks)
+{
+    return chunks > 1 && chunks * bt <= STAGE_MAX;
+}
+
+template <typename Real>
+inline size_t eval_smem_bytes(int bt, int tdb, int chunks)
+{
+    const size_t t = (size_t)tdb * sizeof(typename RecOf<Real>::type);
+    const size_t st = (sizeof(Real) == 4 && staged_fixup(bt, chunks))
+                          ? (size_t)chunks * bt * 3 * sizeof(float4) : 0;
+    return t > st ? t : st;
+}
 
 template <typename Real, int MOB, int PHASE, int BT, int TDB>
 __global__ void __launch_bounds__(BT, (MinBlocks<Real, BT>::value)) eval_kernel(const EvalArgs A)
 {
     using Rec = typename RecOf<Real>::type;
-    __shared__ Rec tile[TDB];
+    // dynamic shared memory, max(TDB records, C x BT x 48 B): the j-tile during
+    // the sweep, then (FP32C, last CTA of an i-block) the staged chunk partials
+    extern __shared__ float4 smem_dyn[];
+    Rec *tile = (Rec *)smem_dyn;
+    float4 *stage = smem_dyn;
     __shared__ int s_last;
 
     const int tid = threadIdx.x;
+    // Programmatic dependent launch: this grid may have been scheduled before the
+    // previous evaluation finished; wait for it (and its memory) before reading
+    // anything it wrote, then allow the next evaluation to be scheduled.  Both
+    // are no-ops for an ordinary launch.
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     const int64_t n = *A.step;
     const Rec *pin = (const Rec *)A.pack_in;
     const int S = (int)A.S, C = A.chunks;
@@ -341,21 +370,42 @@ __global__ void __launch_bounds__(BT, (MinBlocks<Real, BT>::value)) eval_kernel(
             do_epi = s_last;
             if (do_epi) {
                 __threadfence();
+                const bool staged = staged_fixup(BT, C);
+                if (sizeof(Real) == 4 && staged) {
+                    // stage the i-block's C x BT partial records (48 B each) into shared
+                    // memory with asynchronous 16-byte copies, all in flight together
+                    const int nb = blk_hi - blk_lo;      // dumbbells in this i-block
+                    const int per_chunk = 3 * nb;        // float4 per chunk
+                    const float4 *g = (const float4 *)A.part + (int64_t)blk_lo * 3;
+                    for (int f = tid; f < C * per_chunk; f += BT) {
+                        const int cc = f / per_chunk, rem = f - cc * per_chunk;
+                        const unsigned sa = (unsigned)__cvta_generic_to_shared(stage + cc * 3 * BT + rem);
+                        const float4 *ga = g + (int64_t)cc * S * 3 + rem;
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(ga));
+                    }
+                    asm volatile("cp.async.commit_group;\n" ::);
+                    asm volatile("cp.async.wait_group 0;\n" ::);
+                    __syncthreads();
+                }
                 if (active) {
                     if constexpr (sizeof(Real) == 4) {
-                        // the C partials combined in chunk order with FP32 two-sum; the
-                        // next chunk's loads are issued before the current one is added
-                        const float4 *src = (const float4 *)(A.part + (int64_t)s * 12);
-                        const int64_t stride = (int64_t)S * 3;  // float4 per chunk
+                        // the C partials combined in chunk order with FP32 two-sum, from
+                        // shared memory (staged above) or, for large splits, from L2 with
+                        // the next chunk's loads issued before the current one is added
                         float S_[6], C_[6];
-                        float4 w0 = __ldcg(src), w1 = __ldcg(src + 1), w2 = __ldcg(src + 2);
+                        const float4 *src = staged ? stage + tid * 3
+                                                   : (const float4 *)(A.part + (int64_t)s * 12);
+                        const int64_t stride = staged ? 3 * BT : (int64_t)S * 3;
+                        float4 w0 = staged ? src[0] : __ldcg(src);
+                        float4 w1 = staged ? src[1] : __ldcg(src + 1);
+                        float4 w2 = staged ? src[2] : __ldcg(src + 2);
                         for (int cc = 0; cc < C; ++cc) {
                             float4 n0 = w0, n1 = w1, n2 = w2;
                             if (cc + 1 < C) {
                                 const float4 *nx = src + (cc + 1) * stride;
-                                n0 = __ldcg(nx);
-                                n1 = __ldcg(nx + 1);
-                                n2 = __ldcg(nx + 2);
+                                n0 = staged ? nx[0] : __ldcg(nx);
+                                n1 = staged ? nx[1] : __ldcg(nx + 1);
+                                n2 = staged ? nx[2] : __ldcg(nx + 2);
                             }
                             // layout: a: s0 s1 s2 c0 c1 c2, b: s0 s1 s2 c0 c1 c2
                             const float ps[6] = {w0.x, w0.y, w0.z, w1.z, w1.w, w2.x};
