@@ -159,6 +159,15 @@ DBS_API int dbs_velocities_device(dbs_suspension *h, double *v_dev);
  */
 DBS_API int dbs_step_timed(dbs_suspension *h, int64_t n, double *mean_ms);
 
+/*
+ * Launch tuning of the pair-sum kernel (used by the autotuner): split the
+ * j-range into `chunks` pieces (1 <= chunks <= max(1, S/8); 0 restores the
+ * built-in choice).  Results change only in the rounding of the j-sum order.
+ * dbs_get_launch reports dumbbells per CTA, chunks and grid size.
+ */
+DBS_API int dbs_set_chunks(dbs_suspension *h, int32_t chunks);
+DBS_API int dbs_get_launch(dbs_suspension *h, int32_t *bt, int32_t *chunks, int32_t *grid);
+
 /* Current positions x [2S][3] (host).  Synchronising. */
 DBS_API int dbs_positions(dbs_suspension *h, double *x);
 

@@ -61,7 +61,7 @@ struct dbs_suspension {
     double cx = 0, cy = 0, cz = 0;
     double lam_max = 0;
     // launch configuration
-    int grid = 1, chunks = 1, bt = 128;
+    int grid = 1, chunks = 1, bt = 128, sms = 148;
     // captured block of GRAPH_STEPS Heun steps
     cudaGraphExec_t graph = nullptr;
 };
@@ -359,6 +359,29 @@ static void choose_launch(dbs_suspension *h)
     }
     h->chunks = (int)C;
     h->grid = (int)std::min<int64_t>((int64_t)sms * occ_for(C), iblocks * C);
+    h->sms = sms;
+}
+
+// grid for a given chunk count (same occupancy rule as choose_launch)
+static int grid_for(dbs_suspension *h, int C)
+{
+    const bool f64 = is_f64(h);
+    const bool small = h->S <= SMALL_S;
+    const int bt = h->bt;
+    const int tdb = f64 ? (small ? TILE64S : TILE64) : (small ? TILE32S : TILE32);
+    const size_t smem = f64 ? eval_smem_bytes<double>(bt, tdb, C) : eval_smem_bytes<float>(bt, tdb, C);
+    int occ = 0;
+    if (f64)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &occ, small ? (const void *)eval_kernel<double, 1, PHASE_CORRECT, BT64S, TILE64S>
+                        : (const void *)eval_kernel<double, 1, PHASE_CORRECT, BT64, TILE64>, bt, smem);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &occ, small ? (const void *)eval_kernel<float, 1, PHASE_CORRECT, BT32S, TILE32S>
+                        : (const void *)eval_kernel<float, 1, PHASE_CORRECT, BT32, TILE32>, bt, smem);
+    occ = std::max(1, occ);
+    const int64_t iblocks = (h->S + bt - 1) / bt;
+    return (int)std::min<int64_t>((int64_t)h->sms * occ, iblocks * C);
 }
 
 static int alloc_all(dbs_suspension *h)
@@ -674,6 +697,39 @@ int dbs_mobility_apply(dbs_suspension *h, const double *F, double *v)
     else pack_kernel<float><<<blocks, thr, 0, h->stream>>>(A, h->Ftmp, nullptr, h->packT);
     CK(h, cudaGetLastError());
     return apply_to_host(h, h->packT, h->Ftmp, 1, v);
+}
+
+int dbs_set_chunks(dbs_suspension *h, int32_t chunks)
+{
+    GUARD(h);
+    const int64_t cmax = std::max<int64_t>(1, h->S / 8);
+    if (chunks < 0 || chunks > cmax) return DBS_E_ARG;
+    CK(h, cudaStreamSynchronize(h->stream));
+    drop_graph(h);
+    if (chunks == 0) {
+        choose_launch(h);
+    } else {
+        h->chunks = chunks;
+        h->grid = grid_for(h, chunks);
+    }
+    if (h->part) {
+        cudaFree(h->part);
+        h->part = nullptr;
+    }
+    if (h->chunks > 1) {
+        const size_t pb = (size_t)h->chunks * h->S * (is_f64(h) ? 6 * sizeof(double) : 12 * sizeof(float));
+        CK(h, cudaMalloc(&h->part, pb));
+    }
+    return DBS_OK;
+}
+
+int dbs_get_launch(dbs_suspension *h, int32_t *bt, int32_t *chunks, int32_t *grid)
+{
+    GUARD(h);
+    if (bt) *bt = h->bt;
+    if (chunks) *chunks = h->chunks;
+    if (grid) *grid = h->grid;
+    return DBS_OK;
 }
 
 int dbs_velocities_device(dbs_suspension *h, double *v_dev)

@@ -199,6 +199,15 @@ class Suspension:
         self._check(load().dbs_step_timed(self._h, _i64(int(n)), ctypes.byref(ms)))
         return ms.value
 
+    def set_chunks(self, chunks: int):
+        """j-split of the pair sum (0 = built-in choice); used by the autotuner."""
+        self._check(load().dbs_set_chunks(self._h, ctypes.c_int32(int(chunks))))
+
+    def get_launch(self):
+        bt, c, g = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        self._check(load().dbs_get_launch(self._h, ctypes.byref(bt), ctypes.byref(c), ctypes.byref(g)))
+        return {"bt": bt.value, "chunks": c.value, "grid": g.value}
+
     def positions(self):
         x = np.empty((self.N, 3))
         self._check(load().dbs_positions(self._h, _p(x)))
