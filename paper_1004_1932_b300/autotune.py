@@ -1,0 +1,87 @@
+"""Autotuner for the pair-sum launch: picks the j-split (chunks) of a suspension
+by timing candidate splits on the device and caches the winner.
+
+The kernel's work units are (i-block of dumbbells) x (j-chunk); how many
+chunks fill the 148 SMs best depends on S, precision, mobility and occupancy
+in ways a closed-form rule only approximates (see ``choose_launch`` in the
+library).  ``tune()`` times the library's own choice and a candidate set
+around whole waves of the persistent grid with ``dbs_step_timed`` (CUDA events
+around every launch) and keeps the fastest.  Results are cached per device
+name, precision, mobility and S in a JSON file.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+from . import dbs
+
+CACHE = os.environ.get("DBS_TUNE_CACHE",
+                       os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_chunks.json"))
+
+
+def _key(h: "dbs.Suspension", device_name: str, precision: str, mobility: str) -> str:
+    return f"{device_name}|{precision}|{mobility}|S={h.S}"
+
+
+def _load():
+    try:
+        return json.load(open(CACHE))
+    except (OSError, ValueError):
+        return {}
+
+
+def candidates(S: int, launch: dict, sms: int = 148) -> list[int]:
+    """Chunk counts worth timing: the built-in choice, powers of two, and the
+    splits that make the unit count a small multiple of the resident grid."""
+    bt = launch["bt"]
+    iblocks = (S + bt - 1) // bt
+    cmax = max(1, S // 8)
+    out = {launch["chunks"], 1}
+    c = 2
+    while c <= cmax:
+        out.add(c)
+        c *= 2
+    grid = max(launch["grid"], 1)
+    for waves in (1, 2, 3, 4, 6, 8):
+        c = (waves * grid) // iblocks
+        for d in (-1, 0, 1):
+            if 1 <= c + d <= cmax:
+                out.add(c + d)
+    return sorted(x for x in out if 1 <= x <= cmax)
+
+
+def tune(h: "dbs.Suspension", *, device_name: str = "cuda", precision: str = "fp32c",
+         mobility: str = "rpy", reps: int | None = None, use_cache: bool = True,
+         write_cache: bool = True) -> dict:
+    """Choose and apply the fastest chunk count for handle ``h``.
+
+    Advances the suspension by the timing steps (the caller restores its state
+    if that matters, e.g. with get_state/set_state)."""
+    key = _key(h, device_name, precision, mobility)
+    cache = _load() if use_cache else {}
+    if key in cache:
+        h.set_chunks(int(cache[key]["chunks"]))
+        return {"chunks": int(cache[key]["chunks"]), "cached": True}
+    base = h.get_launch()
+    if reps is None:
+        reps = max(4, min(200, int(2e9 / max(1, h.N) ** 2)))
+    results = {}
+    for c in candidates(h.S, base):
+        h.set_chunks(c)
+        h.step_timed(2)
+        results[c] = h.step_timed(reps)
+    best = min(results, key=results.get)
+    h.set_chunks(best)
+    entry = {"chunks": best, "ms_per_launch": results[best],
+             "builtin": {"chunks": base["chunks"], "ms_per_launch": results.get(base["chunks"])}}
+    if write_cache:
+        cache = _load()
+        cache[key] = entry
+        try:
+            with open(CACHE + ".tmp", "w") as f:
+                json.dump(cache, f, indent=1, sort_keys=True)
+            os.replace(CACHE + ".tmp", CACHE)
+        except OSError:
+            pass
+    return {**entry, "cached": False, "timed": results}

@@ -344,19 +344,26 @@ static void choose_launch(dbs_suspension *h)
     // also keep C x BT within the shared-memory staging of the partials
     const int64_t max_chunks = std::max<int64_t>(
         1, small ? std::min<int64_t>(h->S / 16, STAGE_MAX / bt) : h->S / 32);
-    double best = 1e300;
-    int64_t C = 1;
-    for (int64_t c = 1; c <= max_chunks; ++c) {
-        const int64_t gfull = (int64_t)sms * occ_for(c);
-        const int64_t u = iblocks * c;
-        const int64_t waves = (u + gfull - 1) / gfull;
-        // time ~ waves * (work per unit ~ 1/c); choose the smallest time, ties to smaller c
-        const double t = (double)waves / (double)c;
-        if (t < best * 0.99) {
-            best = t;
-            C = c;
+    // Single pass when it leaves at least 4 chunks: every CTA takes at most one
+    // unit, and the fixup of each i-block reads few partials.  Otherwise (large
+    // systems) many equal units over the persistent grid, C minimising
+    // waves / C (the unit time scales as 1/C; ties within 1% to the smaller C).
+    int64_t C = std::min<int64_t>(max_chunks, ((int64_t)sms * occ_for(max_chunks)) / iblocks);
+    if (C < 4) {
+        double best = 1e300;
+        C = 1;
+        for (int64_t c = 1; c <= max_chunks; ++c) {
+            const int64_t gfull = (int64_t)sms * occ_for(c);
+            const int64_t u = iblocks * c;
+            const int64_t waves = (u + gfull - 1) / gfull;
+            const double t = (double)waves / (double)c;
+            if (t < best * 0.99) {
+                best = t;
+                C = c;
+            }
         }
     }
+    C = std::max<int64_t>(1, C);
     h->chunks = (int)C;
     h->grid = (int)std::min<int64_t>((int64_t)sms * occ_for(C), iblocks * C);
     h->sms = sms;
