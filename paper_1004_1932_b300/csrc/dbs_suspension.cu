@@ -19,8 +19,14 @@ using namespace dbs;
 
 namespace {
 
-constexpr int BT32 = 128;    // dumbbells per CTA (FP32C, large systems)
-constexpr int TILE32 = 128;  // dumbbell records per shared-memory tile (FP32C, 6 KB)
+#ifndef DBS_BT_LARGE
+#define DBS_BT_LARGE 128
+#endif
+#ifndef DBS_TILE_LARGE
+#define DBS_TILE_LARGE 256
+#endif
+constexpr int BT32 = DBS_BT_LARGE;      // dumbbells per CTA (FP32C, large systems)
+constexpr int TILE32 = DBS_TILE_LARGE;  // dumbbell records per shared-memory tile (FP32C)
 constexpr int BT32S = 32;    // dumbbells per CTA (FP32C, S <= SMALL_S): more CTAs, spread epilogue
 constexpr int TILE32S = 64;
 constexpr int BT64 = 128;    // dumbbells per CTA (FP64)

@@ -24,6 +24,28 @@
 #pragma once
 #include "dbs_common.cuh"
 
+// Tuning macros (defaults measured on B300 at N = 65536, see profiles/):
+//   DBS_RPY_W35           RPY coefficients as A = w + c2 w^3, B = (r.G)(w^3 + c3 w^5)
+//   DBS_UNROLL            unroll of the fast j-loop
+//   DBS_FP32_WARPS_PER_SM resident warps the FP32 kernels are register-capped for
+//   DBS_W2_RCP            w^2 from rcp.approx instead of w*w (slower on B300; off)
+#ifndef DBS_RPY_W35
+#define DBS_RPY_W35 1
+#endif
+#ifndef DBS_UNROLL
+#define DBS_UNROLL 2
+#endif
+#ifndef DBS_FP32_WARPS_PER_SM
+#define DBS_FP32_WARPS_PER_SM 20
+#endif
+#ifndef DBS_W2_RCP
+#define DBS_W2_RCP 0
+#endif
+
+namespace dbs {
+constexpr int kPairUnroll = DBS_UNROLL;  // unroll of the fast j-loop
+}
+
 namespace dbs {
 
 // ---- FP32 pair terms, two j-spheres per call ----------------------------------
@@ -49,7 +71,19 @@ __device__ __forceinline__ void pair2(const float2 px, const float2 py, const fl
         if (skip_x) w.x = 0.f;
         if (skip_y) w.y = 0.f;
     }
+#if DBS_W2_RCP
+    // w^2 = 1/r^2 from the special-function unit (approximate reciprocal, like the
+    // approximate rsqrt): moves one paired multiply off the FP32 pipe
+    float2 w2;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(w2.x) : "f"(r2.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(w2.y) : "f"(r2.y));
+    if (GUARD) {
+        if (skip_x) w2.x = 0.f;
+        if (skip_y) w2.y = 0.f;
+    }
+#else
     const float2 w2 = __fmul2_rn(w, w);
+#endif
     float2 dot = __fmul2_rn(rx, gx);
     dot = __ffma2_rn(ry, gy, dot);
     dot = __ffma2_rn(rz, gz, dot);
@@ -59,8 +93,15 @@ __device__ __forceinline__ void pair2(const float2 px, const float2 py, const fl
         uy = __ffma2_rn(w, __ffma2_rn(ry, t, gy), uy);
         uz = __ffma2_rn(w, __ffma2_rn(rz, t, gz), uz);
     } else {
+#if DBS_RPY_W35
+        // A = w + c2 w^3, B = (r.G)(w^3 + c3 w^5): one paired op fewer than via t
+        const float2 w3 = __fmul2_rn(w, w2);
+        const float2 Af = __ffma2_rn(c2, w3, w);
+        const float2 Bf = __fmul2_rn(dot, __ffma2_rn(c3, __fmul2_rn(w3, w2), w3));
+#else
         const float2 Af = __ffma2_rn(w, __fmul2_rn(c2, w2), w);
         const float2 Bf = __fmul2_rn(t, __ffma2_rn(w, __fmul2_rn(c3, w2), w));
+#endif
         ux = __ffma2_rn(Bf, rx, __ffma2_rn(Af, gx, ux));
         uy = __ffma2_rn(Bf, ry, __ffma2_rn(Af, gy, uy));
         uz = __ffma2_rn(Bf, rz, __ffma2_rn(Af, gz, uz));
@@ -194,7 +235,7 @@ __device__ __forceinline__ void sweep_f32(const DbF32 *__restrict__ pin, DbF32 *
         float2 qa[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         float2 qb[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         if (!diag) {
-#pragma unroll 2
+#pragma unroll kPairUnroll
             for (int k = 0; k < len; ++k) {
                 const float4 ra = tile[k].a, rb = tile[k].b, rc = tile[k].c;
                 const float2 jx = make_float2(ra.x, ra.y), jy = make_float2(ra.z, ra.w);
@@ -263,11 +304,11 @@ __device__ __forceinline__ void sweep_f64(const DbF64 *__restrict__ pin, DbF64 *
 // that the units fill whole waves of the resident grid.  Indices are 32-bit
 // (the host limits S to 2^29).
 //
-// FP32: at most 85 registers per thread (768 / BT resident CTAs of BT threads,
-// 24 warps per SM).  FP64 keeps the compiler's choice.  Dynamic shared memory:
+// FP32: registers capped so that DBS_FP32_WARPS_PER_SM warps stay resident
+// (20 warps: at most 102 registers).  FP64 keeps the compiler's choice.  Dynamic shared memory:
 // eval_smem_bytes(BT, TDB, C).
 template <typename Real, int BT>
-struct MinBlocks { static constexpr int value = sizeof(Real) == 4 ? 768 / BT : 1; };
+struct MinBlocks { static constexpr int value = sizeof(Real) == 4 ? 32 * DBS_FP32_WARPS_PER_SM / BT : 1; };
 
 // FP32C partials are staged through shared memory when C x BT <= STAGE_MAX
 // (24 KB); larger splits (large systems, where the fixup is a negligible part
