@@ -272,6 +272,61 @@ DBS_API int dbs_pair_distance_error(int64_t S, const double *A0_dev, const doubl
                             void *stream);
 
 /* ======================================================================== */
+/* Cluster-resident execution: one system or an ensemble of independent ones */
+/* ======================================================================== */
+
+/*
+ * Execution path of dbs_step for one FP32C suspension.
+ *  DBS_PATH_GRID     every evaluation of Eq. (3) is one launch over all SMs
+ *                    (default; any size).
+ *  DBS_PATH_CLUSTER  a thread-block cluster of cluster_size CTAs (1, 2, 4, 8 or
+ *                    16; 0 = largest useful) holds the whole suspension in
+ *                    shared memory and advances up to 1024 Heun steps per
+ *                    launch, exchanging j-data through distributed shared
+ *                    memory with hardware cluster barriers.  Needs
+ *                    2 S x 48 B + partial sums <= 227 KB per CTA (S <= ~2200)
+ *                    and S / cluster_size <= 512.
+ * Both paths compute the same quantities (Secs. II and IV); the rounding of
+ * the j-sums differs.  Errors: DBS_E_ARG for FP64 handles or sizes the path
+ * cannot hold.
+ */
+#define DBS_PATH_GRID 0
+#define DBS_PATH_CLUSTER 1
+DBS_API int dbs_set_path(dbs_suspension *h, int32_t path, int32_t cluster_size);
+DBS_API int dbs_get_path(dbs_suspension *h, int32_t *path, int32_t *cluster_size);
+
+typedef struct dbs_ensemble dbs_ensemble;
+
+/*
+ * Group `count` independent FP32C suspensions (existing handles on one device,
+ * each listed once) so that dbs_ensemble_step advances all of them together:
+ * every member runs on its own thread-block cluster, members of equal cluster
+ * size and mobility share one launch, and the launches of one block of steps
+ * run concurrently.  The members stay valid handles: their state advances in
+ * place, and work issued on a member's own stream is ordered before and after
+ * the ensemble's.  stream: cudaStream_t of the ensemble, NULL = its own.
+ */
+DBS_API int dbs_ensemble_create(int32_t count, dbs_suspension *const *members, void *stream,
+                                dbs_ensemble **out);
+DBS_API int dbs_ensemble_destroy(dbs_ensemble *e);
+
+/* n Heun steps of every member (asynchronous). */
+DBS_API int dbs_ensemble_step(dbs_ensemble *e, int64_t n);
+
+/* Wait for the ensemble's work and report member faults. */
+DBS_API int dbs_ensemble_sync(dbs_ensemble *e);
+
+/*
+ * Cluster size of every member (1, 2, 4, 8 or 16, at least S/512 rounded up
+ * to a power of two).  G = NULL restores the built-in balance rule, which
+ * gives each member a cluster in proportion to its pair work S^2.  Used by the
+ * autotuner.
+ */
+DBS_API int dbs_ensemble_set_clusters(dbs_ensemble *e, const int32_t *G);
+DBS_API int dbs_ensemble_get_clusters(dbs_ensemble *e, int32_t *G);
+DBS_API const char *dbs_ensemble_last_error(const dbs_ensemble *e);
+
+/* ======================================================================== */
 /* Allocation-free mobility product                                         */
 /* ======================================================================== */
 

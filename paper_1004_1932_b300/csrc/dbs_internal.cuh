@@ -1,0 +1,52 @@
+// Internal view of a suspension handle, shared by the translation units of
+// libdbs (not part of the C-ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dbs.h"
+#include "dbs_common.cuh"
+
+struct dbs_ensemble;
+
+struct dbs_suspension {
+    dbs_ensemble *solo = nullptr;  // private one-member ensemble of the cluster path
+    dbs_params p{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int64_t S = 0, N = 0;
+    int64_t n_host = 0;
+    int status = DBS_OK;
+    char msg[256] = "";
+    // device state
+    double *x = nullptr, *v0 = nullptr, *Fd = nullptr, *Fext = nullptr, *lam = nullptr,
+           *sinphi = nullptr, *cosphi = nullptr, *vout = nullptr, *Ftmp = nullptr;
+    void *packA = nullptr, *packB = nullptr, *packT = nullptr;
+    double2 *trig = nullptr;
+    int64_t trig_hi = -1;  // ring holds (sin, cos)(omega t_k) for k <= trig_hi (last TRIG_RING/2 fills)
+    float *part = nullptr;
+    unsigned *tickets = nullptr, *done = nullptr;
+    int64_t *step = nullptr;
+    int *flags = nullptr;
+    double *Racc = nullptr, *Rbar = nullptr;
+    int64_t avg_m = 0, avg_n0 = 0, avg_maxk = 0;
+    double cx = 0, cy = 0, cz = 0;
+    double lam_max = 0;
+    // launch configuration
+    int grid = 1, chunks = 1, bt = 128, sms = 148;
+    // captured block of GRAPH_STEPS Heun steps
+    cudaGraphExec_t graph = nullptr;
+};
+
+
+// helpers defined in dbs_suspension.cu
+int fail(dbs_suspension *h, int status, const char *fmt, ...);
+dbs::EvalArgs base_args(const dbs_suspension *h);
+int ensure_trig(dbs_suspension *h, int64_t k_hi, cudaStream_t st = nullptr);  // st: h->stream if null
+int check_flags(dbs_suspension *h);
+void drop_graph(dbs_suspension *h);
+// defined in dbs_ensemble.cu
+int solo_step(dbs_suspension *h, int64_t n);
+constexpr int kTrigRing = 4096;  // entries of the per-handle clock ring
+void solo_destroy(dbs_suspension *h);

@@ -14,6 +14,7 @@
 #include "dbs.h"
 #include "dbs_common.cuh"
 #include "eval_kernel.cuh"
+#include "dbs_internal.cuh"
 
 using namespace dbs;
 
@@ -34,7 +35,7 @@ constexpr int TILE64 = 64;   // dumbbell records per tile (FP64, 6 KB)
 constexpr int BT64S = 32;
 constexpr int TILE64S = 32;
 constexpr int64_t SMALL_S = 2048;
-constexpr int TRIG_RING = 4096;  // entries of the (sin, cos)(omega t_k) ring (power of two)
+constexpr int TRIG_RING = kTrigRing;  // entries of the (sin, cos)(omega t_k) ring (power of two)
 constexpr int GRAPH_STEPS = 32;  // Heun steps per captured CUDA graph
 
 thread_local char g_create_error[256] = "";
@@ -43,39 +44,10 @@ const double PI = 3.14159265358979323846;
 
 }  // namespace
 
-struct dbs_suspension {
-    dbs_params p{};
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    int64_t S = 0, N = 0;
-    int64_t n_host = 0;
-    int status = DBS_OK;
-    char msg[256] = "";
-    // device state
-    double *x = nullptr, *v0 = nullptr, *Fd = nullptr, *Fext = nullptr, *lam = nullptr,
-           *sinphi = nullptr, *cosphi = nullptr, *vout = nullptr, *Ftmp = nullptr;
-    void *packA = nullptr, *packB = nullptr, *packT = nullptr;
-    double2 *trig = nullptr;
-    int64_t trig_hi = -1;  // ring holds (sin, cos)(omega t_k) for k <= trig_hi (last TRIG_RING/2 fills)
-    float *part = nullptr;
-    unsigned *tickets = nullptr, *done = nullptr;
-    int64_t *step = nullptr;
-    int *flags = nullptr;
-    double *Racc = nullptr, *Rbar = nullptr;
-    int64_t avg_m = 0, avg_n0 = 0, avg_maxk = 0;
-    double cx = 0, cy = 0, cz = 0;
-    double lam_max = 0;
-    // launch configuration
-    int grid = 1, chunks = 1, bt = 128, sms = 148;
-    // captured block of GRAPH_STEPS Heun steps
-    cudaGraphExec_t graph = nullptr;
-};
-
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
-static int fail(dbs_suspension *h, int status, const char *fmt, ...)
+int fail(dbs_suspension *h, int status, const char *fmt, ...)
 {
     char *buf = h ? h->msg : g_create_error;
     va_list ap;
@@ -117,7 +89,7 @@ static size_t pack_bytes(const dbs_suspension *h)
     return (size_t)h->S * (is_f64(h) ? sizeof(DbF64) : sizeof(DbF32));
 }
 
-static EvalArgs base_args(const dbs_suspension *h)
+EvalArgs base_args(const dbs_suspension *h)
 {
     EvalArgs A{};
     A.S = h->S;
@@ -269,11 +241,12 @@ __global__ void set_step_kernel(int64_t *step, int64_t n) { *step = n; }
 // Make the trig ring cover step indices up to k_hi.  Fills are stream-ordered
 // before the launches that read them and cover TRIG_RING/2 steps at a time, so
 // a fill never overwrites an entry that later-enqueued work still needs.
-static int ensure_trig(dbs_suspension *h, int64_t k_hi)
+int ensure_trig(dbs_suspension *h, int64_t k_hi, cudaStream_t st)
 {
+    if (!st) st = h->stream;
     while (h->trig_hi < k_hi) {
         const int count = TRIG_RING / 2;
-        trig_fill_kernel<<<(count + 127) / 128, 128, 0, h->stream>>>(
+        trig_fill_kernel<<<(count + 127) / 128, 128, 0, st>>>(
             h->trig, TRIG_RING - 1, h->trig_hi + 1, count, h->p.omega, h->p.dt);
         CK(h, cudaGetLastError());
         h->trig_hi += count;
@@ -298,7 +271,7 @@ static int repack(dbs_suspension *h)
     return DBS_OK;
 }
 
-static void drop_graph(dbs_suspension *h)
+void drop_graph(dbs_suspension *h)
 {
     if (h->graph) {
         cudaGraphExecDestroy(h->graph);
@@ -457,7 +430,7 @@ static void set_centre(dbs_suspension *h, const double *x)
     h->cz = 0.5 * (lo[2] + hi[2]);
 }
 
-static int check_flags(dbs_suspension *h)
+int check_flags(dbs_suspension *h)
 {
     CK(h, cudaStreamSynchronize(h->stream));
     int f = 0;
@@ -591,6 +564,7 @@ int dbs_destroy(dbs_suspension *h)
     if (!h) return DBS_OK;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->solo) solo_destroy(h);
     free_all(h);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -646,6 +620,7 @@ int dbs_step(dbs_suspension *h, int64_t n)
 {
     GUARD(h);
     if (n < 0) return DBS_E_ARG;
+    if (h->solo) return solo_step(h, n);
     int64_t left = n, k = h->n_host;
     int rc;
     if (left >= GRAPH_STEPS) {

@@ -22,6 +22,7 @@ OK = 0
 E_ARG, E_NOMEM, E_CUDA, E_OVERLAP, E_NONFINITE, E_TIMEOUT, E_STATE = -1, -2, -3, -4, -5, -6, -7
 OSEEN, RPY = 0, 1
 FP32C, FP64 = 0, 1
+PATH_GRID, PATH_CLUSTER = 0, 1
 K_PREFACTOR = 15.0 / 64.0  # Eq. (9d) as printed
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -62,10 +63,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
     if not os.path.exists(p):
         raise FileNotFoundError(f"{p} not built; run python -m paper_1004_1932_b300.build")
     lib = ctypes.CDLL(p)
-    for name in ("dbs_last_error", "dbs_status_string", "dbs_version", "dbs_sa_last_error"):
+    for name in ("dbs_last_error", "dbs_status_string", "dbs_version", "dbs_sa_last_error",
+                 "dbs_ensemble_last_error"):
         getattr(lib, name).restype = ctypes.c_char_p
     lib.dbs_last_error.argtypes = [_vp]
     lib.dbs_sa_last_error.argtypes = [_vp]
+    lib.dbs_ensemble_last_error.argtypes = [_vp]
     lib.dbs_status_string.argtypes = [ctypes.c_int]
     _lib = lib
     return lib
@@ -199,6 +202,16 @@ class Suspension:
         self._check(load().dbs_step_timed(self._h, _i64(int(n)), ctypes.byref(ms)))
         return ms.value
 
+    def set_path(self, path, cluster_size: int = 0):
+        """dbs_step path: "grid" (per-evaluation launches) or "cluster" (resident cluster)."""
+        p = {"grid": PATH_GRID, "cluster": PATH_CLUSTER}.get(path, path)
+        self._check(load().dbs_set_path(self._h, ctypes.c_int32(int(p)), ctypes.c_int32(int(cluster_size))))
+
+    def get_path(self):
+        p, g = ctypes.c_int32(), ctypes.c_int32()
+        self._check(load().dbs_get_path(self._h, ctypes.byref(p), ctypes.byref(g)))
+        return ("cluster" if p.value == PATH_CLUSTER else "grid"), g.value
+
     def set_chunks(self, chunks: int):
         """j-split of the pair sum (0 = built-in choice); used by the autotuner."""
         self._check(load().dbs_set_chunks(self._h, ctypes.c_int32(int(chunks))))
@@ -329,6 +342,62 @@ def pair_distance_error(S, A0, A1, B0, B1, stream=None):
         raise DbsError(rc, "dbs_pair_distance_error")
     return {"max": out[0], "rms": float(np.sqrt(out[1] / out[3])),
             "ref_rms": float(np.sqrt(out[2] / out[3])), "pairs": int(out[3])}
+
+
+class Ensemble:
+    """Independent suspensions advanced together on thread-block clusters
+    (``dbs_ensemble_*``).  Members stay usable as ordinary handles."""
+
+    def __init__(self, members, stream=None):
+        lib = load()
+        self.members = list(members)
+        arr = (ctypes.c_void_p * len(self.members))(*[m._h.value for m in self.members])
+        h = ctypes.c_void_p()
+        rc = lib.dbs_ensemble_create(ctypes.c_int32(len(self.members)), arr,
+                                     None if stream is None else ctypes.c_void_p(_devptr_stream(stream)),
+                                     ctypes.byref(h))
+        if rc != OK:
+            raise DbsError(rc, lib.dbs_ensemble_last_error(None).decode())
+        self._h = h
+
+    def _check(self, rc):
+        if rc != OK:
+            raise DbsError(rc, load().dbs_ensemble_last_error(self._h).decode())
+
+    def step(self, n: int = 1):
+        self._check(load().dbs_ensemble_step(self._h, _i64(int(n))))
+
+    def sync(self):
+        self._check(load().dbs_ensemble_sync(self._h))
+
+    def set_clusters(self, G=None):
+        if G is None:
+            self._check(load().dbs_ensemble_set_clusters(self._h, None))
+        else:
+            g = (ctypes.c_int32 * len(self.members))(*[int(x) for x in G])
+            self._check(load().dbs_ensemble_set_clusters(self._h, g))
+
+    def get_clusters(self):
+        g = (ctypes.c_int32 * len(self.members))()
+        self._check(load().dbs_ensemble_get_clusters(self._h, g))
+        return list(g)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().dbs_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 NOALLOC_MAX_S = 4096
