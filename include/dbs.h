@@ -327,6 +327,69 @@ DBS_API int dbs_ensemble_get_clusters(dbs_ensemble *e, int32_t *G);
 DBS_API const char *dbs_ensemble_last_error(const dbs_ensemble *e);
 
 /* ======================================================================== */
+/* Serving engine: requests admitted by device-memory budget, batched        */
+/* ======================================================================== */
+
+/*
+ * A request is one simulation: parameters, initial positions, stroke and a
+ * number of Heun steps; its result is the positions after those steps.  The
+ * engine keeps requests resident on the device as independent suspensions and
+ * advances all of them together on every dbs_engine_tick (continuous
+ * batching): requests that arrive while others run are admitted at the next
+ * tick as soon as the device-memory budget and the slot limit allow, members
+ * that fit the cluster path run as one ensemble and the others on the grid
+ * path concurrently, and finished requests are copied out and freed.
+ */
+typedef struct {
+    size_t hbm_budget_bytes; /* admission budget for resident request state, 0 = unlimited */
+    int32_t max_active;      /* resident requests at most, 0 = unlimited */
+    int32_t block_steps;     /* Heun steps per request per tick, >= 1 */
+    int32_t device;          /* -1 = current device */
+    int32_t reserved;        /* must be 0 */
+} dbs_engine_params;
+
+#define DBS_REQ_PENDING 0
+#define DBS_REQ_RUNNING 1
+#define DBS_REQ_DONE 2
+#define DBS_REQ_CANCELLED 3
+#define DBS_REQ_FAILED 4
+
+typedef struct dbs_engine dbs_engine;
+
+DBS_API int dbs_engine_create(const dbs_engine_params *p, dbs_engine **out);
+DBS_API int dbs_engine_destroy(dbs_engine *e);
+
+/*
+ * Queue a request (host arrays are copied): p->stream must be NULL, x0 [2S][3],
+ * lambda [S], phase [S] (NULL = passive), steps >= 0.  *id identifies it.
+ * Parameters are validated when the request is admitted (invalid ones end in
+ * DBS_REQ_FAILED).
+ */
+DBS_API int dbs_engine_submit(dbs_engine *e, const dbs_params *p, const double *x0,
+                              const double *lambda, const double *phase, int64_t steps,
+                              int64_t *id);
+
+/* Admit, advance every resident request by up to block_steps, retire finished ones.
+ * Reports the numbers of resident and queued requests afterwards. */
+DBS_API int dbs_engine_tick(dbs_engine *e, int32_t *active, int32_t *pending);
+
+/*
+ * State of a request; for DBS_REQ_DONE, x_out [2S][3] (host, may be NULL)
+ * receives the final positions and *latency_s (may be NULL) the time from
+ * submission to completion on the host clock.
+ */
+DBS_API int dbs_engine_poll(dbs_engine *e, int64_t id, int32_t *state, double *x_out,
+                            double *latency_s);
+
+/* Cancel a queued or resident request (its device memory is freed). */
+DBS_API int dbs_engine_cancel(dbs_engine *e, int64_t id);
+
+/* Device bytes the engine charges against the budget for a request of S dumbbells. */
+DBS_API int dbs_engine_request_bytes(int64_t S, int32_t precision, size_t *bytes);
+
+DBS_API const char *dbs_engine_last_error(const dbs_engine *e);
+
+/* ======================================================================== */
 /* Allocation-free mobility product                                         */
 /* ======================================================================== */
 

@@ -199,9 +199,11 @@ static ResSys make_sys(const dbs_suspension *h, int G)
     return P;
 }
 
-// Advance every member n steps; all work ordered after the members' pending work
-// and before their later work.
-static int ensemble_step(dbs_ensemble *e, int64_t n)
+// Advance member i by steps[i] Heun steps (all members by n when steps is
+// null); all work is ordered after the members' pending work and before their
+// later work.  Blocks of at most K_BLOCK steps; a member whose count is used up
+// sits out the remaining blocks (K = 0 launches nothing for it).
+static int ensemble_step_v(dbs_ensemble *e, int64_t n, const int64_t *steps)
 {
     if (e->status != DBS_OK) return e->status;
     ECK(e, cudaSetDevice(e->device));
@@ -209,24 +211,30 @@ static int ensemble_step(dbs_ensemble *e, int64_t n)
         int rc = build_classes(e);
         if (rc) return rc;
     }
+    const size_t M = e->m.size();
+    std::vector<int64_t> left(M);
+    for (size_t i = 0; i < M; ++i) left[i] = steps ? steps[i] : n;
     // the ensemble stream waits for each member's stream
     for (auto *h : e->m) {
         ECK(e, cudaEventRecord(e->joined, h->stream));
         ECK(e, cudaStreamWaitEvent(e->stream, e->joined, 0));
     }
-    std::vector<ResSys> sys(e->m.size());
-    int64_t left = n;
-    while (left > 0) {
-        const int K = (int)std::min<int64_t>(left, K_BLOCK);
-        for (size_t i = 0; i < e->m.size(); ++i) {
+    std::vector<ResSys> sys(M);
+    for (;;) {
+        int64_t kmax = 0;
+        for (size_t i = 0; i < M; ++i) kmax = std::max(kmax, std::min<int64_t>(left[i], K_BLOCK));
+        if (kmax == 0) break;
+        for (size_t i = 0; i < M; ++i) {
             dbs_suspension *h = e->m[i];
             if (h->status != DBS_OK) return efail(e, h->status, "member %zu is in an error state", i);
+            const int K = (int)std::min<int64_t>(left[i], K_BLOCK);
             int rc = ensure_trig(h, h->n_host + K + 1, e->stream);
             if (rc) return efail(e, rc, "member %zu: %s", i, h->msg);
             sys[i] = make_sys(h, e->G[i]);
+            sys[i].K = K;
         }
-        if (!e->d_sys) ECK(e, cudaMalloc(&e->d_sys, sizeof(ResSys) * e->m.size()));
-        ECK(e, cudaMemcpyAsync(e->d_sys, sys.data(), sizeof(ResSys) * sys.size(), cudaMemcpyHostToDevice,
+        if (!e->d_sys) ECK(e, cudaMalloc(&e->d_sys, sizeof(ResSys) * M));
+        ECK(e, cudaMemcpyAsync(e->d_sys, sys.data(), sizeof(ResSys) * M, cudaMemcpyHostToDevice,
                                e->stream));
         ECK(e, cudaEventRecord(e->fork, e->stream));
         for (auto &kv : e->classes) {
@@ -248,25 +256,30 @@ static int ensemble_step(dbs_ensemble *e, int64_t n)
             const int *cs = c.csys;
             cudaError_t err;
             if (kv.first.mob == DBS_OSEEN)
-                err = kv.first.nt == NT_BIG ? cudaLaunchKernelEx(&cfg, resident_kernel<0, NT_BIG>, ds, cs, K)
-                                            : cudaLaunchKernelEx(&cfg, resident_kernel<0, NT_SMALL>, ds, cs, K);
+                err = kv.first.nt == NT_BIG ? cudaLaunchKernelEx(&cfg, resident_kernel<0, NT_BIG>, ds, cs)
+                                            : cudaLaunchKernelEx(&cfg, resident_kernel<0, NT_SMALL>, ds, cs);
             else
-                err = kv.first.nt == NT_BIG ? cudaLaunchKernelEx(&cfg, resident_kernel<1, NT_BIG>, ds, cs, K)
-                                            : cudaLaunchKernelEx(&cfg, resident_kernel<1, NT_SMALL>, ds, cs, K);
+                err = kv.first.nt == NT_BIG ? cudaLaunchKernelEx(&cfg, resident_kernel<1, NT_BIG>, ds, cs)
+                                            : cudaLaunchKernelEx(&cfg, resident_kernel<1, NT_SMALL>, ds, cs);
             if (err != cudaSuccess)
                 return efail(e, DBS_E_CUDA, "resident launch (G=%d, %zu members): %s", kv.first.G,
                              c.members.size(), cudaGetErrorString(err));
             ECK(e, cudaEventRecord(c.done, c.stream));
             ECK(e, cudaStreamWaitEvent(e->stream, c.done, 0));
         }
-        for (auto *h : e->m) h->n_host += K;
-        left -= K;
+        for (size_t i = 0; i < M; ++i) {
+            const int K = (int)std::min<int64_t>(left[i], K_BLOCK);
+            e->m[i]->n_host += K;
+            left[i] -= K;
+        }
     }
     // members' later work waits for the ensemble
     ECK(e, cudaEventRecord(e->joined, e->stream));
     for (auto *h : e->m) ECK(e, cudaStreamWaitEvent(h->stream, e->joined, 0));
     return DBS_OK;
 }
+
+static int ensemble_step(dbs_ensemble *e, int64_t n) { return ensemble_step_v(e, n, nullptr); }
 
 static int ensemble_create(int32_t count, dbs_suspension *const *members, void *stream,
                            dbs_ensemble **out)
@@ -323,6 +336,16 @@ static void ensemble_destroy(dbs_ensemble *e)
     if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
     delete e;
 }
+
+// ---- internal entry points (serving engine) ------------------------------------
+bool ens_member_ok(const dbs_suspension *h) { return member_ok(h); }
+int ens_create(int32_t count, dbs_suspension *const *members, void *stream, dbs_ensemble **out)
+{
+    return ensemble_create(count, members, stream, out);
+}
+int ens_step_v(dbs_ensemble *e, const int64_t *steps) { return ensemble_step_v(e, 0, steps); }
+void ens_destroy(dbs_ensemble *e) { ensemble_destroy(e); }
+const char *ens_error(const dbs_ensemble *e) { return e ? e->msg : g_ens_error; }
 
 // ---- single-system cluster path -------------------------------------------------
 int solo_step(dbs_suspension *h, int64_t n)

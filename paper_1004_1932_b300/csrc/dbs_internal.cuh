@@ -48,5 +48,10 @@ int check_flags(dbs_suspension *h);
 void drop_graph(dbs_suspension *h);
 // defined in dbs_ensemble.cu
 int solo_step(dbs_suspension *h, int64_t n);
+bool ens_member_ok(const dbs_suspension *h);               // can run on the cluster path
+int ens_create(int32_t count, dbs_suspension *const *members, void *stream, dbs_ensemble **out);
+int ens_step_v(dbs_ensemble *e, const int64_t *steps);     // member i advances steps[i]
+void ens_destroy(dbs_ensemble *e);
+const char *ens_error(const dbs_ensemble *e);
 constexpr int kTrigRing = 4096;  // entries of the per-handle clock ring
 void solo_destroy(dbs_suspension *h);

@@ -29,6 +29,7 @@ namespace cg = cooperative_groups;
 struct ResSys {
     int S;            // dumbbells
     int G;            // cluster size of this member
+    int K;            // Heun steps of this member in this launch (<= the launch's K)
     double inv6pimua, k0, ell, dt;
     float c2, c3, overlap_r2;
     double *x, *v0, *Fd;        // [2S][3] FP64 state (read at start, written at end)
@@ -101,12 +102,13 @@ __device__ __forceinline__ void res_sweep(const DbF32 *rec, int db, int de, int 
     }
 }
 
-// K Heun steps of the cluster's suspension.  Grid = sum over members of G_m
-// CTAs in clusters of G (all members of a launch share G); csys[cluster] is
-// the member index.  NT threads per CTA.
+// P.K Heun steps of the cluster's suspension (members of one launch may take
+// different step counts).  Grid = sum over members of G_m CTAs in clusters of G
+// (all members of a launch share G); csys[cluster] is the member index.  NT
+// threads per CTA.
 template <int MOB, int NT>
 __global__ void __launch_bounds__(NT, 1)
-resident_kernel(const ResSys *__restrict__ systems, const int *__restrict__ csys, int K)
+resident_kernel(const ResSys *__restrict__ systems, const int *__restrict__ csys)
 {
     cg::cluster_group cluster = cg::this_cluster();
     const int G = (int)cluster.num_blocks();
@@ -114,6 +116,8 @@ resident_kernel(const ResSys *__restrict__ systems, const int *__restrict__ csys
     const int cid = blockIdx.x / G;
     const ResSys &P = systems[csys[cid]];
     const int S = P.S;
+    const int K = P.K;
+    if (K <= 0) return;  // the whole cluster sits out this launch
     const int t0 = (int)(((int64_t)S * r) / G), t1 = (int)(((int64_t)S * (r + 1)) / G);
     const int TP = t1 - t0;
     const int tp_max = (S + G - 1) / G;

@@ -64,11 +64,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
         raise FileNotFoundError(f"{p} not built; run python -m paper_1004_1932_b300.build")
     lib = ctypes.CDLL(p)
     for name in ("dbs_last_error", "dbs_status_string", "dbs_version", "dbs_sa_last_error",
-                 "dbs_ensemble_last_error"):
+                 "dbs_ensemble_last_error", "dbs_engine_last_error"):
         getattr(lib, name).restype = ctypes.c_char_p
     lib.dbs_last_error.argtypes = [_vp]
     lib.dbs_sa_last_error.argtypes = [_vp]
     lib.dbs_ensemble_last_error.argtypes = [_vp]
+    lib.dbs_engine_last_error.argtypes = [_vp]
     lib.dbs_status_string.argtypes = [ctypes.c_int]
     _lib = lib
     return lib
@@ -398,6 +399,96 @@ class Ensemble:
 
     def __exit__(self, *exc):
         self.close()
+
+
+REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_CANCELLED, REQ_FAILED = 0, 1, 2, 3, 4
+
+
+class EngineParams(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_active", ctypes.c_int32),
+                ("block_steps", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Engine:
+    """Serving engine (``dbs_engine_*``): requests admitted by a device-memory
+    budget and advanced together on every ``tick()`` (continuous batching)."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, max_active: int = 0, block_steps: int = 256,
+                 device: int = -1):
+        lib = load()
+        self._p = EngineParams(int(hbm_budget_bytes), int(max_active), int(block_steps), int(device), 0)
+        h = ctypes.c_void_p()
+        rc = lib.dbs_engine_create(ctypes.byref(self._p), ctypes.byref(h))
+        if rc != OK:
+            raise DbsError(rc, lib.dbs_engine_last_error(None).decode())
+        self._h = h
+        self._S = {}
+
+    def _check(self, rc):
+        if rc != OK:
+            raise DbsError(rc, load().dbs_engine_last_error(self._h).decode())
+
+    def submit(self, x0, *, a, mu, k0, ell, omega, dt, steps, mobility="rpy", precision="fp32c",
+               lam=None, phi=None) -> int:
+        x0 = _arr(x0)
+        S = x0.shape[0] // 2
+        p = Params(S, a, mu, k0, ell, omega, dt, _mob(mobility), _prec(precision), None, -1, 0)
+        lam_a = None if lam is None else _arr(np.broadcast_to(np.asarray(lam, float), (S,)))
+        phi_a = None if phi is None else _arr(phi, (S,))
+        rid = ctypes.c_int64()
+        self._check(load().dbs_engine_submit(self._h, ctypes.byref(p), _p(x0),
+                                             None if lam_a is None else _p(lam_a),
+                                             None if phi_a is None else _p(phi_a),
+                                             _i64(int(steps)), ctypes.byref(rid)))
+        self._S[rid.value] = S
+        return rid.value
+
+    def submit_inputs(self, susp, steps, precision="fp32c") -> int:
+        return self.submit(susp.x0, a=susp.a, mu=susp.mu, k0=susp.k0, ell=susp.ell, omega=susp.omega,
+                           dt=susp.dt, steps=steps, mobility=susp.mobility, precision=precision,
+                           lam=susp.lam, phi=susp.phi)
+
+    def tick(self):
+        a, q = ctypes.c_int32(), ctypes.c_int32()
+        self._check(load().dbs_engine_tick(self._h, ctypes.byref(a), ctypes.byref(q)))
+        return a.value, q.value
+
+    def poll(self, rid: int):
+        st = ctypes.c_int32()
+        x = np.empty((2 * self._S[rid], 3))
+        lat = ctypes.c_double(float("nan"))
+        self._check(load().dbs_engine_poll(self._h, _i64(rid), ctypes.byref(st), _p(x),
+                                           ctypes.byref(lat)))
+        return st.value, (x if st.value == REQ_DONE else None), lat.value
+
+    def cancel(self, rid: int):
+        self._check(load().dbs_engine_cancel(self._h, _i64(rid)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().dbs_engine_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def request_bytes(S: int, precision="fp32c") -> int:
+    b = ctypes.c_size_t()
+    rc = load().dbs_engine_request_bytes(_i64(int(S)), ctypes.c_int32(_prec(precision)), ctypes.byref(b))
+    if rc != OK:
+        raise DbsError(rc, "dbs_engine_request_bytes")
+    return b.value
 
 
 NOALLOC_MAX_S = 4096

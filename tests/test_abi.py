@@ -107,3 +107,13 @@ def test_inputs_deterministic_and_separated():
     L0 = a.ell + a.lam * np.sin(a.phi)
     np.testing.assert_allclose(np.linalg.norm(a.x0[1::2] - a.x0[0::2], axis=1), L0, rtol=1e-13)
     assert a.side == pytest.approx((512 / 0.002) ** (1 / 3))
+
+
+def test_engine_host_validation(lib):
+    bad = dbs.EngineParams(0, 0, 0, -1, 0)            # block_steps must be >= 1
+    h = ctypes.c_void_p()
+    assert lib.dbs_engine_create(ctypes.byref(bad), ctypes.byref(h)) == dbs.E_ARG
+    b1, b2 = dbs.request_bytes(100), dbs.request_bytes(1000)
+    assert 0 < b1 < b2
+    with pytest.raises(dbs.DbsError):
+        dbs.request_bytes(0)
