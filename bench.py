@@ -51,6 +51,8 @@ def _args():
     p.add_argument("--mobility", default="rpy", choices=["rpy", "oseen"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-large", action="store_true", help="skip the N=65536 kernel measurement")
+    p.add_argument("--no-ensemble", action="store_true", help="skip the 256-system ensemble measurement")
+    p.add_argument("--no-serving", action="store_true", help="skip the serving-trace measurement")
     p.add_argument("--cpu-sample-steps", type=int, default=400,
                    help="Heun steps of the oracle timed for the CPU baseline")
     return p.parse_args()
@@ -138,6 +140,102 @@ def _cpu_baseline(S, mobility, nsteps):
             "kind": "oracle",
             "sample": f"{nsteps} Heun steps of the same S={S} suspension (FP64 C oracle, OpenMP over "
                       f"targets), {el:.2f} s"}
+
+
+def ensemble_measure(dbs, inputs, torch, stream, steps=1000, count=256):
+    """256 independent suspensions, S log-uniform in [8, 2048], lambda ~ U[0.1, 0.3],
+    seeds 0..255: batched on thread-block clusters vs one system per launch."""
+    systems = inputs.ensemble(count)
+    hs = [dbs.Suspension.from_inputs(s, precision="fp32c", stream=stream) for s in systems]
+    pairs = sum(2 * (2 * s.S) * (2 * s.S - 1) for s in systems)
+    ens = dbs.Ensemble(hs, stream=stream)
+    ens.step(16)
+    ens.sync()
+    t0 = time.perf_counter()
+    ens.step(steps)
+    ens.sync()
+    el_b = time.perf_counter() - t0
+    G = ens.get_clusters()
+    ens.close()
+    seq_steps = max(32, steps // 5)
+    for h in hs:
+        h.step(32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for h in hs:
+        h.step(seq_steps)
+    for h in hs:
+        h.sync()
+    el_s = time.perf_counter() - t0
+    for h in hs:
+        h.close()
+    b = count * steps / el_b
+    sq = count * seq_steps / el_s
+    return {"workload": f"{count} suspensions, S log-uniform in [8, 2048], lambda ~ U[0.1, 0.3], "
+                        f"seeds 0..{count - 1}, RPY, FP32C",
+            "batched": {"steps": steps, "seconds": el_b, "system_steps_per_s": b,
+                        "pairs_per_s": pairs * steps / el_b,
+                        "clusters": {str(g): G.count(g) for g in sorted(set(G))}},
+            "one_system_per_launch": {"steps": seq_steps, "seconds": el_s, "system_steps_per_s": sq,
+                                      "pairs_per_s": pairs * seq_steps / el_s},
+            "speedup": b / sq}
+
+
+def serving_measure(dbs, inputs, n_req=48, rate=200.0, steps_lo=1e3, steps_hi=1e4, block=256,
+                    budget=64 << 30):
+    """Poisson trace (mean `rate` req/s), S uniform over {16, 64, 256, 1024, 4096},
+    steps log-uniform in [steps_lo, steps_hi]: the engine (continuous batching under an
+    HBM budget) against serving the same requests one at a time in arrival order."""
+    trace = inputs.request_trace(n_req, rate, steps_lo=steps_lo, steps_hi=steps_hi)
+    susp = {rid: inputs.make_suspension(S, seed=1000 + rid, density=0.002) for _, S, _, rid in trace}
+    eng = dbs.Engine(hbm_budget_bytes=budget, block_steps=block)
+    t0 = time.perf_counter()
+    ids, sub_t, done = {}, {}, {}
+    k = 0
+    total_steps = sum(n for _, _, n, _ in trace)
+    while len(done) < len(trace):
+        now = time.perf_counter() - t0
+        while k < len(trace) and trace[k][0] <= now:
+            arr, S, n, rid = trace[k]
+            ids[rid] = eng.submit_inputs(susp[rid], n)
+            sub_t[rid] = (arr, time.perf_counter() - t0)
+            k += 1
+        a, q = eng.tick()
+        for rid, eid in ids.items():
+            if rid in done:
+                continue
+            st, _, lat = eng.poll(eid)
+            if st in (dbs.REQ_DONE, dbs.REQ_FAILED, dbs.REQ_CANCELLED):
+                arr, sub = sub_t[rid]
+                done[rid] = (st, (sub - arr) + lat)
+        if a == 0 and q == 0 and k < len(trace):
+            time.sleep(max(0.0, trace[k][0] - (time.perf_counter() - t0)))
+    makespan = time.perf_counter() - t0
+    eng.close()
+    lat = sorted(v[1] for v in done.values() if v[0] == dbs.REQ_DONE)
+    # one at a time in arrival order (grid path), measured run times, simulated queueing
+    t_free, lat_seq, busy = 0.0, [], 0.0
+    for arr, S, n, rid in trace:
+        with dbs.Suspension.from_inputs(susp[rid], precision="fp32c") as h:
+            h.sync()
+            ts = time.perf_counter()
+            h.step(n)
+            h.positions()
+            run = time.perf_counter() - ts
+        start = max(arr, t_free)
+        t_free = start + run
+        busy += run
+        lat_seq.append(t_free - arr)
+    lat_seq.sort()
+    q = lambda v, p: v[min(len(v) - 1, int(round(p * (len(v) - 1))))]
+    return {"trace": f"{n_req} requests, Poisson {rate:g}/s (seed 0), S in {{16,64,256,1024,4096}}, "
+                     f"steps log-uniform [{steps_lo:g}, {steps_hi:g}], HBM budget {budget >> 30} GB, "
+                     f"block {block} steps",
+            "completed": len(lat),
+            "engine": {"makespan_s": makespan, "system_steps_per_s": total_steps / makespan,
+                       "p50_latency_s": q(lat, 0.5), "p99_latency_s": q(lat, 0.99)},
+            "one_at_a_time": {"makespan_s": t_free, "system_steps_per_s": total_steps / busy,
+                              "p50_latency_s": q(lat_seq, 0.5), "p99_latency_s": q(lat_seq, 0.99)}}
 
 
 def run_reference(args):
@@ -312,6 +410,9 @@ def run_ours(args):
         h.close()
         sa.close()
 
+    ensemble = None if args.no_ensemble else ensemble_measure(dbs, inputs, torch, stream)
+    serving = None if args.no_serving else serving_measure(dbs, inputs)
+
     if rank != 0:
         return
     cpu = _cpu_baseline(S, args.mobility, args.cpu_sample_steps) if ws == 1 else None
@@ -334,6 +435,8 @@ def run_ours(args):
         "clocks": clk,
         "sa_comparison": last_err,
         "large_system_kernel": large,
+        "ensemble": ensemble,
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
 
