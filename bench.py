@@ -65,6 +65,22 @@ def _dist():
     return ws, rank, local
 
 
+def reduce_max(value: float, device=None) -> float:
+    """Max of a per-rank float over all ranks (identity without torch.distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_seed(rank: int) -> int:
+    """Each rank simulates its own independent suspension (weak scaling)."""
+    return int(rank)
+
+
 def _workload_config(S, mobility, flush):
     return {"workload": f"single suspension S={S} (N={2 * S}) density 0.002, lambda=0.2, "
                         f"{mobility.upper()}, FP32 pair math + FP64 state, dt=1e-3, one step = "
@@ -286,7 +302,7 @@ def run_ours(args):
     dbs.load()
 
     S, N = args.S, 2 * args.S
-    s = inputs.paper_scale(S, seed=rank, mobility=args.mobility)
+    s = inputs.paper_scale(S, seed=rank_seed(rank), mobility=args.mobility)
     stream = torch.cuda.Stream(device=dev)
     T = 2 * math.pi / s.omega
     m = STEPS_PER_PERIOD
@@ -296,8 +312,14 @@ def run_ours(args):
     l2_bytes = torch.cuda.get_device_properties(dev).L2_cache_size
     flush_buf = torch.empty(int(2 * l2_bytes) // 4, dtype=torch.float32, device=dev)
 
+    from paper_1004_1932_b300 import autotune
+    probe = dbs.Suspension.from_inputs(s, precision="fp32c", stream=stream, device=local)
+    path_choice = autotune.choose_path(probe)
+    probe.close()
+
     def make():
         h = dbs.Suspension.from_inputs(s, precision="fp32c", stream=stream, device=local)
+        h.set_path(path_choice["path"])
         sa = dbs.StrokeAveraged(s.R0, s.N0, s.phi, s.lam, a=s.a, ell=s.ell, omega=s.omega,
                                 dt=dt_sa, precision="fp32c", stream=stream, device=local)
         h.enable_period_average(m, max_periods=total_periods)
@@ -342,20 +364,38 @@ def run_ours(args):
     clk = clocks.stop()
     ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
     h.sync()
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ms, dev)
     pairs_per_step = 2 * N * (N - 1) * m
     value = ws * pairs_per_step * args.steps / (ms / 1e3)
-    launches_per_step = 2 * m + 2 * SA_STEPS_PER_PERIOD + 1
+    # our kernels per benchmark step: the microscopic model (grid: 2 per Heun step;
+    # cluster: one resident launch per <= 1024 steps), the clock-ring refills (one per
+    # 2048 steps), the stroke-averaged model (2 per step) and the comparison
+    model_launches = 2 * m if path_choice["path"] == "grid" else -(-m // 1024)
+    launches_per_step = model_launches + 2 * SA_STEPS_PER_PERIOD + 1
+    ring_fills = -(-(m * args.steps) // 2048)
 
-    # ---- live per-launch duration of the pair-sum kernel (CUDA events, its stream) ----
-    mean_ms = h.step_timed(200)
+    # ---- live per-launch duration of the dominant kernel (CUDA events, its stream) ----
     props = torch.cuda.get_device_properties(dev)
     mhz_max = clk.get("sm_max_mhz") or 2032.0
     peak = _fp32_peak_tflops(props.multi_processor_count, mhz_max)
-    flops_launch = N * (N - 1) * FLOPS_PER_PAIR[args.mobility]
+    if path_choice["path"] == "cluster":
+        # one resident launch advances 1024 Heun steps (2048 pair sums)
+        kname = "resident_kernel (cluster-resident pair sums + Heun, 1024 steps per launch)"
+        kev0, kev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        launches = []
+        for _ in range(3):
+            h.sync()
+            kev0.record(stream)
+            h.step(1024)
+            kev1.record(stream)
+            kev1.synchronize()
+            launches.append(kev0.elapsed_time(kev1))
+        mean_ms = sum(launches) / len(launches)
+        flops_launch = 2 * 1024 * N * (N - 1) * FLOPS_PER_PAIR[args.mobility]
+    else:
+        kname = "eval_kernel (pair sum + fused Heun epilogue)"
+        mean_ms = h.step_timed(200)
+        flops_launch = N * (N - 1) * FLOPS_PER_PAIR[args.mobility]
     achieved = flops_launch / (mean_ms / 1e3) / 1e12
     last_err = errs[-1] if errs else None
     h.close()
@@ -400,11 +440,7 @@ def run_ours(args):
             out_host.numpy()[:] = h.positions()     # device -> host: the step's result
             xs = out_host.numpy()
         barrier()
-        el = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([el], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            el = float(t.item())
+        el = reduce_max(time.perf_counter() - t0, dev)
         e2e = {"value": ws * pairs_per_step * args.steps / el, "unit": "pairs/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
         h.close()
@@ -423,7 +459,8 @@ def run_ours(args):
         "data": "synthetic (seeded random suspension, no dataset)",
         "config": _workload_config(S, args.mobility, "flushed between timed steps (2x L2 write)"),
         "heun_steps_per_s": ws * m * args.steps / (ms / 1e3),
-        "roofline": {"bound": "alu", "kernel": "eval_kernel (pair sum + fused Heun epilogue)",
+        "path": path_choice,
+        "roofline": {"bound": "alu", "kernel": kname,
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "launch_ms": mean_ms, "flops_per_launch": flops_launch,
@@ -431,7 +468,7 @@ def run_ours(args):
                                    f"{mhz_max:.0f} MHz (max SM clock)"},
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches": launches_per_step * args.steps + ring_fills,
         "clocks": clk,
         "sa_comparison": last_err,
         "large_system_kernel": large,

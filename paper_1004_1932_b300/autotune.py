@@ -85,3 +85,28 @@ def tune(h: "dbs.Suspension", *, device_name: str = "cuda", precision: str = "fp
         except OSError:
             pass
     return {**entry, "cached": False, "timed": results}
+
+
+def choose_path(h: "dbs.Suspension", steps: int = 1024) -> dict:
+    """Time ``steps`` Heun steps on the grid path and on the cluster path (when the
+    suspension fits it) and keep the faster.  The suspension's state is restored
+    to where it started, so the choice does not change the trajectory."""
+    import time
+    x0, n0 = h.get_state()
+    timings = {}
+    for path in ("grid", "cluster"):
+        try:
+            h.set_path(path)
+        except dbs.DbsError:
+            continue
+        h.step(64)
+        h.sync()
+        t = time.perf_counter()
+        h.step(steps)
+        h.sync()
+        timings[path] = (time.perf_counter() - t) / steps
+        h.set_state(x0, n0)
+    best = min(timings, key=timings.get)
+    h.set_path(best)
+    h.set_state(x0, n0)
+    return {"path": best, "s_per_step": timings}

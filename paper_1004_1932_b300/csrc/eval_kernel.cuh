@@ -362,6 +362,17 @@ __global__ void __launch_bounds__(BT, (MinBlocks<Real, BT>::value)) eval_kernel(
         const int blk_lo = ib_ * BT;
         const int blk_hi = min(blk_lo + BT, S);
 
+        if (PHASE != PHASE_APPLY && active) {
+            // warm L1 with what the epilogue of this dumbbell will read, in case this
+            // CTA turns out to be the last of its i-block
+            const int64_t o = 6 * (int64_t)s;
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(A.x + o));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(A.Fd + o));
+            if (PHASE == PHASE_CORRECT) asm volatile("prefetch.global.L1 [%0];" ::"l"(A.v0 + o));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(A.lam + s));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(A.sinphi + s));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(A.cosphi + s));
+        }
         double u[6];
         if constexpr (sizeof(Real) == 4) {
             float s_[6] = {0, 0, 0, 0, 0, 0}, c_[6] = {0, 0, 0, 0, 0, 0};
@@ -400,17 +411,23 @@ __global__ void __launch_bounds__(BT, (MinBlocks<Real, BT>::value)) eval_kernel(
 
         bool do_epi = true;
         if (C > 1) {
-            __threadfence();
+            // block-level release/acquire: the barrier orders every thread's partial
+            // writes before thread 0, whose fence makes them visible device-wide
+            // before its arrival ticket; the last arriver fences again before the
+            // CTA reads the other chunks' partials
             __syncthreads();
             if (tid == 0) {
+                __threadfence();
                 const unsigned prev = atomicAdd(&A.tickets[ib_], 1u);
                 s_last = (prev == (unsigned)C - 1u);
-                if (s_last) A.tickets[ib_] = 0u;
+                if (s_last) {
+                    A.tickets[ib_] = 0u;
+                    __threadfence();
+                }
             }
             __syncthreads();
             do_epi = s_last;
             if (do_epi) {
-                __threadfence();
                 const bool staged = staged_fixup(BT, C);
                 if (sizeof(Real) == 4 && staged) {
                     // stage the i-block's C x BT partial records (48 B each) into shared
