@@ -174,3 +174,54 @@ def request_trace(n: int = 500, rate: float = 200.0, sizes=(16, 64, 256, 1024, 4
     S = rng.choice(np.asarray(sizes), size=n)
     steps = np.round(np.exp(rng.uniform(math.log(steps_lo), math.log(steps_hi), size=n))).astype(int)
     return [(float(arr[i]), int(S[i]), int(steps[i]), int(i)) for i in range(n)]
+
+
+# ---------------------------------------------------------------------------
+# Workloads of the paper's other experiments
+# ---------------------------------------------------------------------------
+
+def colloids(N: int, *, seed: int = 0, density: float = 0.002, min_sep: float = 2.0, a: float = 0.05,
+             mu: float = 1.0, force=(0.0, 0.0, -1.0), dt: float = 1e-3,
+             mobility: str = "oseen") -> tuple[Suspension, np.ndarray]:
+    """N colloidal spheres under one constant force (Sec. IV speed-up test: colloids
+    moving under a constant applied force, Oseen interactions).  Spheres are
+    paired as spring-less dumbbells (k0 = 0, lambda = 0) so the dumbbell
+    machinery carries them; returns the suspension and the force [N, 3]."""
+    if N % 2:
+        raise ValueError("N must be even")
+    S = N // 2
+    side = (N / density) ** (1.0 / 3.0)
+    rng = np.random.default_rng(seed)
+    x = _centres(rng, N, side, min_sep)
+    s = Suspension(S=S, a=a, mu=mu, k0=0.0, ell=1.0, omega=2 * math.pi, dt=dt, mobility=mobility,
+                   lam=np.zeros(S), phi=np.zeros(S), R0=0.5 * (x[0::2] + x[1::2]),
+                   N0=np.tile([1.0, 0.0, 0.0], (S, 1)), x0=x, side=side, seed=seed)
+    F = np.tile(np.asarray(force, float), (N, 1))
+    return s, F
+
+
+def lattice(x: int, spacing: float, *, seed: int = 0, phases: str = "checkerboard",
+            ell: float = 5e-6, a_over_ell: float = 0.2, lam_over_ell: float = 0.1,
+            omega: float = 500.0, k0: float = 1e-3, mu: float = 1e-3, dt_over_T: float = 1e-4,
+            mobility: str = "rpy") -> Suspension:
+    """Dumbbell centres on an x*x*x cubic lattice of the given spacing (Sec. III.C),
+    orientations uniform on the sphere (seeded), phases either the 3d
+    checkerboard {0, pi/2} (alternating between nearest neighbours) or uniform
+    on [0, 2pi).  Default parameters are those of Fig. 1 (SI units)."""
+    rng = np.random.default_rng(seed)
+    idx = np.stack(np.meshgrid(np.arange(x), np.arange(x), np.arange(x), indexing="ij"), -1).reshape(-1, 3)
+    R = (idx - (x - 1) / 2.0) * spacing
+    S = R.shape[0]
+    Nv = _orientations(rng, S)
+    if phases == "checkerboard":
+        phi = np.where(idx.sum(1) % 2 == 0, 0.0, math.pi / 2)
+    elif phases == "random":
+        phi = rng.uniform(0.0, 2 * math.pi, size=S)
+    else:
+        raise ValueError(phases)
+    lam = np.full(S, lam_over_ell * ell)
+    x0 = spheres_at_rest(R, Nv, ell, lam, phi)
+    T = 2 * math.pi / omega
+    return Suspension(S=S, a=a_over_ell * ell, mu=mu, k0=k0, ell=ell, omega=omega,
+                      dt=dt_over_T * T, mobility=mobility, lam=lam, phi=phi, R0=R, N0=Nv, x0=x0,
+                      side=spacing * x, seed=seed, meta={"phases": phases, "spacing": spacing})
