@@ -368,8 +368,8 @@ def run_ours(args):
     pairs_per_step = 2 * N * (N - 1) * m
     value = ws * pairs_per_step * args.steps / (ms / 1e3)
     # our kernels per benchmark step: the microscopic model (grid: 2 per Heun step;
-    # cluster: one resident launch per <= 1024 steps), the clock-ring refills (one per
-    # 2048 steps), the stroke-averaged model (2 per step) and the comparison
+    # cluster and cooperative: one launch per <= 1024 steps), the clock-ring refills
+    # (one per 2048 steps), the stroke-averaged model (2 per step) and the comparison
     model_launches = 2 * m if path_choice["path"] == "grid" else -(-m // 1024)
     launches_per_step = model_launches + 2 * SA_STEPS_PER_PERIOD + 1
     ring_fills = -(-(m * args.steps) // 2048)
@@ -378,9 +378,12 @@ def run_ours(args):
     props = torch.cuda.get_device_properties(dev)
     mhz_max = clk.get("sm_max_mhz") or 2032.0
     peak = _fp32_peak_tflops(props.multi_processor_count, mhz_max)
-    if path_choice["path"] == "cluster":
-        # one resident launch advances 1024 Heun steps (2048 pair sums)
-        kname = "resident_kernel (cluster-resident pair sums + Heun, 1024 steps per launch)"
+    if path_choice["path"] in ("cluster", "coop"):
+        # one launch advances 1024 Heun steps (2048 pair sums)
+        kname = ("resident_kernel (cluster-resident pair sums + Heun, 1024 steps per launch)"
+                 if path_choice["path"] == "cluster" else
+                 "flow_kernel (cooperative dataflow: pair sums + Heun, tagged point-to-point "
+                 "exchange, 1024 steps per launch)")
         kev0, kev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         launches = []
         for _ in range(3):

@@ -292,6 +292,18 @@ DBS_API int dbs_pair_distance_error(int64_t S, const double *A0_dev, const doubl
  */
 #define DBS_PATH_GRID 0
 #define DBS_PATH_CLUSTER 1
+/*
+ *  DBS_PATH_COOP     one cooperative launch over all SMs advances up to 1024
+ *                    Heun steps.  CTAs exchange records and partial sums
+ *                    through flag-tagged words in device memory, point to
+ *                    point, with no grid-wide barrier.  Every wait is bounded
+ *                    (about one second): a launch whose exchange cannot
+ *                    complete ends with DBS_E_TIMEOUT instead of hanging.
+ *                    FP32C, S <= 2048.  dbs_set_chunks on this path sets the
+ *                    number of j-chunks (default 16, fewer if the grid would
+ *                    not be co-resident).
+ */
+#define DBS_PATH_COOP 2
 DBS_API int dbs_set_path(dbs_suspension *h, int32_t path, int32_t cluster_size);
 DBS_API int dbs_get_path(dbs_suspension *h, int32_t *path, int32_t *cluster_size);
 
@@ -426,6 +438,14 @@ DBS_API const char *dbs_engine_last_error(const dbs_engine *e);
 DBS_API int dbs_mobility_apply_noalloc(int64_t S, const double *x_dev, const double *F_dev,
                                        double a, double mu, int32_t mobility, double *v_dev,
                                        void *stream);
+
+/*
+ * Diagnostic of the bounded device-side wait used by the cooperative path:
+ * one warp polls a word that nothing writes, so that its wait must run out
+ * after timeout_ms (1..10000); *status receives the outcome (DBS_E_TIMEOUT
+ * expected) and the call returns DBS_OK if the device stayed usable.
+ */
+DBS_API int dbs_test_wait_timeout(int32_t timeout_ms, int32_t *status);
 
 /* Library version string. */
 DBS_API const char *dbs_version(void);

@@ -88,13 +88,13 @@ def tune(h: "dbs.Suspension", *, device_name: str = "cuda", precision: str = "fp
 
 
 def choose_path(h: "dbs.Suspension", steps: int = 1024) -> dict:
-    """Time ``steps`` Heun steps on the grid path and on the cluster path (when the
+    """Time ``steps`` Heun steps on the grid, cluster and cooperative paths (where the
     suspension fits it) and keep the faster.  The suspension's state is restored
     to where it started, so the choice does not change the trajectory."""
     import time
     x0, n0 = h.get_state()
     timings = {}
-    for path in ("grid", "cluster"):
+    for path in ("grid", "cluster", "coop"):
         try:
             h.set_path(path)
         except dbs.DbsError:

@@ -430,12 +430,21 @@ int dbs_set_path(dbs_suspension *h, int32_t path, int32_t cluster_size)
 {
     if (!h) return DBS_E_ARG;
     if (h->status != DBS_OK) return h->status;
-    if (path == DBS_PATH_GRID) {
-        if (h->solo) {
-            cudaSetDevice(h->device);
-            cudaStreamSynchronize(h->stream);
-            solo_destroy(h);
+    cudaSetDevice(h->device);
+    if (h->solo) {
+        cudaStreamSynchronize(h->stream);
+        solo_destroy(h);
+    }
+    h->path = DBS_PATH_GRID;
+    if (path == DBS_PATH_GRID) return DBS_OK;
+    if (path == DBS_PATH_COOP) {
+        int rc = coop_setup(h);
+        if (rc) {
+            // a size the path cannot hold is an argument error, not a broken handle
+            if (rc == DBS_E_ARG) h->status = DBS_OK;
+            return rc;
         }
+        h->path = DBS_PATH_COOP;
         return DBS_OK;
     }
     if (path != DBS_PATH_CLUSTER) return DBS_E_ARG;
@@ -459,13 +468,14 @@ int dbs_set_path(dbs_suspension *h, int32_t path, int32_t cluster_size)
         return fail(h, rc, "cluster size %d not valid for S=%lld", G, (long long)h->S);
     }
     h->solo = e;
+    h->path = DBS_PATH_CLUSTER;
     return DBS_OK;
 }
 
 int dbs_get_path(dbs_suspension *h, int32_t *path, int32_t *cluster_size)
 {
     if (!h) return DBS_E_ARG;
-    if (path) *path = h->solo ? DBS_PATH_CLUSTER : DBS_PATH_GRID;
+    if (path) *path = h->path;
     if (cluster_size) *cluster_size = h->solo ? h->solo->G[0] : 0;
     return DBS_OK;
 }

@@ -11,6 +11,11 @@ struct dbs_ensemble;
 
 struct dbs_suspension {
     dbs_ensemble *solo = nullptr;  // private one-member ensemble of the cluster path
+    int path = 0;                  // DBS_PATH_GRID / DBS_PATH_CLUSTER / DBS_PATH_COOP
+    // cooperative dataflow path: tagged record and partial buffers, split, next tag
+    ulonglong2 *ll_rec = nullptr, *ll_part = nullptr;
+    int flow_I = 0, flow_q = 0, flow_C = 0, flow_creq = 0;
+    unsigned flow_base = 1;
     dbs_params p{};
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -46,6 +51,8 @@ dbs::EvalArgs base_args(const dbs_suspension *h);
 int ensure_trig(dbs_suspension *h, int64_t k_hi, cudaStream_t st = nullptr);  // st: h->stream if null
 int check_flags(dbs_suspension *h);
 void drop_graph(dbs_suspension *h);
+// defined in dbs_suspension.cu (cooperative path)
+int coop_setup(dbs_suspension *h);
 // defined in dbs_ensemble.cu
 int solo_step(dbs_suspension *h, int64_t n);
 bool ens_member_ok(const dbs_suspension *h);               // can run on the cluster path

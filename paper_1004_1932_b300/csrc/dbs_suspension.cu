@@ -14,6 +14,7 @@
 #include "dbs.h"
 #include "dbs_common.cuh"
 #include "eval_kernel.cuh"
+#include "flow_kernel.cuh"
 #include "dbs_internal.cuh"
 
 using namespace dbs;
@@ -81,6 +82,8 @@ static bool all_finite(const double *a, int64_t n)
         if (!std::isfinite(a[i])) return false;
     return true;
 }
+
+static void drop_flow(dbs_suspension *h);
 
 static bool is_f64(const dbs_suspension *h) { return h->p.precision == DBS_FP64; }
 
@@ -410,6 +413,7 @@ static int alloc_all(dbs_suspension *h)
 static void free_all(dbs_suspension *h)
 {
     drop_graph(h);
+    drop_flow(h);
     void *bufs[] = {h->x, h->v0, h->Fd, h->Fext, h->lam, h->sinphi, h->cosphi, h->vout, h->Ftmp, h->packA,
                     h->packB, h->packT, h->trig, h->part, h->tickets, h->done, h->step, h->flags,
                     h->Racc, h->Rbar};
@@ -616,11 +620,122 @@ int dbs_set_external_force(dbs_suspension *h, const double *F)
     return DBS_OK;
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// cooperative dataflow path (flow_kernel)
+// ---------------------------------------------------------------------------
+#ifndef DBS_FLOW_WARPS
+#define DBS_FLOW_WARPS 4
+#endif
+constexpr int FLOW_W = DBS_FLOW_WARPS;     // warps per CTA
+constexpr int FLOW_MAX_C = 16;             // j-chunks per i-block by default
+constexpr int FLOW_MAX_STEPS = 1024;       // Heun steps per launch
+
+static const void *flow_fn(const dbs_suspension *h)
+{
+    return h->p.mobility == DBS_OSEEN ? (const void *)flow_kernel<0, FLOW_W>
+                                      : (const void *)flow_kernel<1, FLOW_W>;
+}
+
+static void drop_flow(dbs_suspension *h)
+{
+    cudaFree(h->ll_rec);
+    cudaFree(h->ll_part);
+    h->ll_rec = h->ll_part = nullptr;
+}
+
+// Split: the most j-chunks (up to the requested count) for which all I x C CTAs
+// are co-resident.
+int coop_setup(dbs_suspension *h)
+{
+    if (h->p.precision != DBS_FP32C || h->S > SMALL_S)
+        return fail(h, DBS_E_ARG, "cooperative path needs FP32C and S <= %lld", (long long)SMALL_S);
+    int coop = 0;
+    CK(h, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device));
+    if (!coop) return fail(h, DBS_E_ARG, "device without cooperative launch");
+    const int I = (int)((h->S + FLOW_IB - 1) / FLOW_IB);
+    const int creq = h->flow_creq > 0 ? h->flow_creq : FLOW_MAX_C;
+    const void *k = flow_fn(h);
+    int q = std::max(1, (I + creq - 1) / creq), C = 0;
+    for (;; ++q) {
+        C = (I + q - 1) / q;
+        const size_t smem = (size_t)q * FLOW_IB * sizeof(DbF32);
+        CK(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int occ = 0;
+        CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 32 * FLOW_W, smem));
+        if ((int64_t)occ * h->sms >= (int64_t)I * C) break;
+        if (q >= I) return fail(h, DBS_E_ARG, "cooperative path: grid does not fit the device");
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    drop_flow(h);
+    const size_t spad = (size_t)I * FLOW_IB;
+    CK(h, cudaMalloc(&h->ll_rec, 2 * spad * 6 * sizeof(ulonglong2)));
+    CK(h, cudaMalloc(&h->ll_part, 2 * (size_t)C * spad * 6 * sizeof(ulonglong2)));
+    CK(h, cudaMemsetAsync(h->ll_rec, 0, 2 * spad * 6 * sizeof(ulonglong2), h->stream));
+    CK(h, cudaMemsetAsync(h->ll_part, 0, 2 * (size_t)C * spad * 6 * sizeof(ulonglong2), h->stream));
+    h->flow_I = I;
+    h->flow_q = q;
+    h->flow_C = C;
+    h->flow_base = 1;
+    return DBS_OK;
+}
+
+static int coop_step(dbs_suspension *h, int64_t n)
+{
+    const size_t spad = (size_t)h->flow_I * FLOW_IB;
+    int64_t left = n;
+    while (left > 0) {
+        const int K = (int)std::min<int64_t>(left, FLOW_MAX_STEPS);
+        int rc = ensure_trig(h, h->n_host + K + 1);
+        if (rc) return rc;
+        if (h->flow_base > 0xffffffffu - (unsigned)(2 * K + 2)) {
+            // tags are about to wrap: clear the buffers so that no old tag can match
+            CK(h, cudaMemsetAsync(h->ll_rec, 0, 2 * spad * 6 * sizeof(ulonglong2), h->stream));
+            CK(h, cudaMemsetAsync(h->ll_part, 0, 2 * (size_t)h->flow_C * spad * 6 * sizeof(ulonglong2),
+                                  h->stream));
+            h->flow_base = 1;
+        }
+        const EvalArgs A = base_args(h);
+        FlowArgs P{};
+        P.rec = h->ll_rec;
+        P.part = h->ll_part;
+        P.pack = (DbF32 *)h->packA;
+        P.n0 = h->n_host;
+        P.I = h->flow_I;
+        P.q = h->flow_q;
+        P.C = h->flow_C;
+        P.K = K;
+        P.base = h->flow_base;
+        P.timeout_ns = 1000000000ull;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(h->flow_I * h->flow_C);
+        cfg.blockDim = dim3(32 * FLOW_W);
+        cfg.dynamicSmemBytes = (size_t)h->flow_q * FLOW_IB * sizeof(DbF32);
+        cfg.stream = h->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaError_t e = h->p.mobility == DBS_OSEEN ? cudaLaunchKernelEx(&cfg, flow_kernel<0, FLOW_W>, A, P)
+                                                   : cudaLaunchKernelEx(&cfg, flow_kernel<1, FLOW_W>, A, P);
+        if (e != cudaSuccess) return fail(h, DBS_E_CUDA, "cooperative launch: %s", cudaGetErrorString(e));
+        h->flow_base += (unsigned)(2 * K + 1);
+        h->n_host += K;
+        left -= K;
+    }
+    return DBS_OK;
+}
+
+extern "C" {
+
 int dbs_step(dbs_suspension *h, int64_t n)
 {
     GUARD(h);
     if (n < 0) return DBS_E_ARG;
     if (h->solo) return solo_step(h, n);
+    if (h->path == DBS_PATH_COOP) return coop_step(h, n);
     int64_t left = n, k = h->n_host;
     int rc;
     if (left >= GRAPH_STEPS) {
@@ -708,6 +823,10 @@ int dbs_set_chunks(dbs_suspension *h, int32_t chunks)
         const size_t pb = (size_t)h->chunks * h->S * (is_f64(h) ? 6 * sizeof(double) : 12 * sizeof(float));
         CK(h, cudaMalloc(&h->part, pb));
     }
+    if (h->path == DBS_PATH_COOP) {
+        h->flow_creq = chunks;
+        return coop_setup(h);
+    }
     return DBS_OK;
 }
 
@@ -717,6 +836,26 @@ int dbs_get_launch(dbs_suspension *h, int32_t *bt, int32_t *chunks, int32_t *gri
     if (bt) *bt = h->bt;
     if (chunks) *chunks = h->chunks;
     if (grid) *grid = h->grid;
+    return DBS_OK;
+}
+
+int dbs_test_wait_timeout(int32_t timeout_ms, int32_t *status)
+{
+    if (!status || timeout_ms < 1 || timeout_ms > 10000) return DBS_E_ARG;
+    void *w = nullptr;
+    if (cudaMalloc(&w, 32) != cudaSuccess) return DBS_E_NOMEM;
+    cudaError_t e = cudaMemset(w, 0, 32);
+    if (e == cudaSuccess) {
+        wait_timeout_kernel<<<1, 32>>>((const ulonglong2 *)w, (int *)((char *)w + 16),
+                                       (unsigned long long)timeout_ms * 1000000ull);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int flags = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&flags, (char *)w + 16, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(w);
+    if (e != cudaSuccess) return DBS_E_CUDA;
+    *status = (flags & FLAG_TIMEOUT) ? DBS_E_TIMEOUT : DBS_OK;
     return DBS_OK;
 }
 

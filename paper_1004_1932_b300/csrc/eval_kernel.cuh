@@ -48,6 +48,31 @@ constexpr int kPairUnroll = DBS_UNROLL;  // unroll of the fast j-loop
 
 namespace dbs {
 
+// Loads of data that other CTAs rewrite during a persistent (cooperative)
+// launch bypass L1, which is not coherent across SMs: COOP = true uses
+// ld.global.cg (L2) for them.
+template <bool COOP, typename T>
+__device__ __forceinline__ T ldm(const T *p)
+{
+    if constexpr (COOP) return __ldcg(p);
+    else return *p;
+}
+
+template <bool COOP>
+__device__ __forceinline__ DbF32 ld_rec(const DbF32 *p)
+{
+    if constexpr (COOP) {
+        const float4 *q = (const float4 *)p;
+        DbF32 r;
+        r.a = __ldcg(q);
+        r.b = __ldcg(q + 1);
+        r.c = __ldcg(q + 2);
+        return r;
+    } else {
+        return *p;
+    }
+}
+
 // ---- FP32 pair terms, two j-spheres per call ----------------------------------
 // Target sphere (px, py, pz), duplicated in both halves, against the two
 // spheres of one j-record (half .x = sphere 2r, half .y = sphere 2r + 1).
@@ -142,15 +167,17 @@ __device__ __forceinline__ void pair_f64(bool self, double px, double py, double
 }
 
 // ---- epilogue: self term, Heun, spring force, repack, period average --------
-template <typename Real, int PHASE>
-__device__ __forceinline__ void epilogue(const EvalArgs &A, int s, const double u[6], int64_t n)
+template <typename Real, int PHASE, bool COOP = false>
+__device__ __forceinline__ void epilogue(const EvalArgs &A, void *pack_out, int s, const double u[6],
+                                         int64_t n)
 {
     using Rec = typename RecOf<Real>::type;
     const int64_t o = 6 * (int64_t)s;
     if constexpr (PHASE == PHASE_APPLY) {
         double v[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) v[k] = A.apply_self ? fma(A.Fd[o + k], A.inv6pimua, u[k]) : u[k];
+        for (int k = 0; k < 6; ++k)
+            v[k] = A.apply_self ? fma(ldm<COOP>(A.Fd + o + k), A.inv6pimua, u[k]) : u[k];
         if (!finite6(v)) atomicOr(A.flags, FLAG_NONFINITE);
 #pragma unroll
         for (int k = 0; k < 6; ++k) A.vout[o + k] = v[k];
@@ -158,13 +185,13 @@ __device__ __forceinline__ void epilogue(const EvalArgs &A, int s, const double 
         double xq[6];  // point of the next evaluation
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            const double v = fma(A.Fd[o + k], A.inv6pimua, u[k]);  // Eq. (3a) self term + pair sum
+            const double v = fma(ldm<COOP>(A.Fd + o + k), A.inv6pimua, u[k]);  // Eq. (3a) + pair sum
             if (PHASE == PHASE_PREDICT) {
                 A.v0[o + k] = v;
-                xq[k] = fma(A.dt, v, A.x[o + k]);                    // x~ = x_n + dt v0
+                xq[k] = fma(A.dt, v, ldm<COOP>(A.x + o + k));                    // x~ = x_n + dt v0
             } else {
-                xq[k] = fma(0.5 * A.dt, A.v0[o + k] + v, A.x[o + k]);  // x_n + dt/2 (v0 + v1)
-                A.x[o + k] = xq[k];
+                xq[k] = fma(0.5 * A.dt, ldm<COOP>(A.v0 + o + k) + v, ldm<COOP>(A.x + o + k));
+                A.x[o + k] = xq[k];                                              // x_n + dt/2 (v0 + v1)
             }
         }
         if (!finite6(xq)) atomicOr(A.flags, FLAG_NONFINITE);
@@ -179,7 +206,7 @@ __device__ __forceinline__ void epilogue(const EvalArgs &A, int s, const double 
         }
 #pragma unroll
         for (int k = 0; k < 6; ++k) A.Fd[o + k] = Fn[k];
-        store_rec((Rec *)A.pack_out, s, xq, Fn, A);
+        store_rec((Rec *)pack_out, s, xq, Fn, A);
         // stroke average of the geometric centre (corrector only), trapezoid rule
         if (PHASE == PHASE_CORRECT && A.avg_m > 0) {
             const int64_t k_local = n + 1 - A.avg_n0;
@@ -190,7 +217,7 @@ __device__ __forceinline__ void epilogue(const EvalArgs &A, int s, const double 
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     const double Rt = 0.5 * (xq[k] + xq[3 + k]);
-                    double acc = A.Racc[r + k];
+                    double acc = ldm<COOP>(A.Racc + r + k);
                     if (end) {
                         acc += 0.5 * Rt;
                         if (kidx < A.avg_maxk) A.Rbar[kidx * 3 * A.S + r + k] = acc / (double)A.avg_m;
@@ -208,7 +235,7 @@ __device__ __forceinline__ void epilogue(const EvalArgs &A, int s, const double 
 // ---- j-sweeps -------------------------------------------------------------------
 // Dumbbell-record range [db, de) through tiles of TDB records.  The CTA's own
 // dumbbells are [blk_lo, blk_hi); tiles that overlap them take the guarded path.
-template <int MOB, int BT, int TDB>
+template <int MOB, int BT, int TDB, bool COOP = false>
 __device__ __forceinline__ void sweep_f32(const DbF32 *__restrict__ pin, DbF32 *tile, int db,
                                           int de, int s, int blk_lo, int blk_hi, bool active,
                                           float c2s, float c3s, float s_[6], float c_[6],
@@ -217,7 +244,7 @@ __device__ __forceinline__ void sweep_f32(const DbF32 *__restrict__ pin, DbF32 *
     const int tid = threadIdx.x;
     float2 pax = make_float2(0.f, 0.f), pay = pax, paz = pax, pbx = pax, pby = pax, pbz = pax;
     if (active) {
-        const DbF32 me = pin[s];
+        const DbF32 me = ld_rec<COOP>(pin + s);
         pax = make_float2(me.a.x, me.a.x);
         pay = make_float2(me.a.z, me.a.z);
         paz = make_float2(me.b.x, me.b.x);
@@ -229,7 +256,7 @@ __device__ __forceinline__ void sweep_f32(const DbF32 *__restrict__ pin, DbF32 *
     for (int t0 = db; t0 < de; t0 += TDB) {
         const int len = min(TDB, de - t0);
         __syncthreads();
-        for (int k = tid; k < len; k += BT) tile[k] = pin[t0 + k];
+        for (int k = tid; k < len; k += BT) tile[k] = ld_rec<COOP>(pin + t0 + k);
         __syncthreads();
         const bool diag = (t0 < blk_hi) && (t0 + len > blk_lo);
         float2 qa[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
@@ -328,26 +355,17 @@ inline size_t eval_smem_bytes(int bt, int tdb, int chunks)
     return t > st ? t : st;
 }
 
-template <typename Real, int MOB, int PHASE, int BT, int TDB>
-__global__ void __launch_bounds__(BT, (MinBlocks<Real, BT>::value)) eval_kernel(const EvalArgs A)
+// All work units of one evaluation assigned to this CTA (the body of
+// eval_kernel, shared with the cooperative multi-step kernel).
+template <typename Real, int MOB, int PHASE, int BT, int TDB, bool COOP = false>
+__device__ __forceinline__ void eval_units(const EvalArgs &A, const void *pack_in, void *pack_out,
+                                           int64_t n, float4 *smem_dyn, int &s_last)
 {
     using Rec = typename RecOf<Real>::type;
-    // dynamic shared memory, max(TDB records, C x BT x 48 B): the j-tile during
-    // the sweep, then (FP32C, last CTA of an i-block) the staged chunk partials
-    extern __shared__ float4 smem_dyn[];
     Rec *tile = (Rec *)smem_dyn;
     float4 *stage = smem_dyn;
-    __shared__ int s_last;
-
     const int tid = threadIdx.x;
-    // Programmatic dependent launch: this grid may have been scheduled before the
-    // previous evaluation finished; wait for it (and its memory) before reading
-    // anything it wrote, then allow the next evaluation to be scheduled.  Both
-    // are no-ops for an ordinary launch.
-    asm volatile("griddepcontrol.wait;\n" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-    const int64_t n = *A.step;
-    const Rec *pin = (const Rec *)A.pack_in;
+    const Rec *pin = (const Rec *)pack_in;
     const int S = (int)A.S, C = A.chunks;
     const int iblocks = (S + BT - 1) / BT;
     const int units = iblocks * C;
@@ -362,7 +380,7 @@ __global__ void __launch_bounds__(BT, (MinBlocks<Real, BT>::value)) eval_kernel(
         const int blk_lo = ib_ * BT;
         const int blk_hi = min(blk_lo + BT, S);
 
-        if (PHASE != PHASE_APPLY && active) {
+        if (!COOP && PHASE != PHASE_APPLY && active) {
             // warm L1 with what the epilogue of this dumbbell will read, in case this
             // CTA turns out to be the last of its i-block
             const int64_t o = 6 * (int64_t)s;
@@ -377,8 +395,8 @@ __global__ void __launch_bounds__(BT, (MinBlocks<Real, BT>::value)) eval_kernel(
         if constexpr (sizeof(Real) == 4) {
             float s_[6] = {0, 0, 0, 0, 0, 0}, c_[6] = {0, 0, 0, 0, 0, 0};
             float r2min = 3.0e38f;
-            sweep_f32<MOB, BT, TDB>((const DbF32 *)pin, (DbF32 *)tile, db, de, s, blk_lo, blk_hi,
-                                    active, A.c2, A.c3, s_, c_, r2min);
+            sweep_f32<MOB, BT, TDB, COOP>((const DbF32 *)pin, (DbF32 *)tile, db, de, s, blk_lo,
+                                          blk_hi, active, A.c2, A.c3, s_, c_, r2min);
             if (MOB == 1 && active && r2min < A.overlap_r2) atomicOr(A.flags, FLAG_OVERLAP);
             if (C > 1) {
                 if (active) {
@@ -499,8 +517,26 @@ __global__ void __launch_bounds__(BT, (MinBlocks<Real, BT>::value)) eval_kernel(
                 }
             }
         }
-        if (do_epi && active) epilogue<Real, PHASE>(A, s, u, n);
+        if (do_epi && active) epilogue<Real, PHASE, COOP>(A, pack_out, s, u, n);
     }
+}
+
+template <typename Real, int MOB, int PHASE, int BT, int TDB>
+__global__ void __launch_bounds__(BT, (MinBlocks<Real, BT>::value)) eval_kernel(const EvalArgs A)
+{
+    // dynamic shared memory, max(TDB records, C x BT x 48 B): the j-tile during
+    // the sweep, then (FP32C, last CTA of an i-block) the staged chunk partials
+    extern __shared__ float4 smem_dyn[];
+    __shared__ int s_last;
+    const int tid = threadIdx.x;
+    // Programmatic dependent launch: this grid may have been scheduled before the
+    // previous evaluation finished; wait for it (and its memory) before reading
+    // anything it wrote, then allow the next evaluation to be scheduled.  Both
+    // are no-ops for an ordinary launch.
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    const int64_t n = *A.step;
+    eval_units<Real, MOB, PHASE, BT, TDB>(A, A.pack_in, A.pack_out, n, smem_dyn, s_last);
 
     if (PHASE == PHASE_CORRECT) {
         // the last CTA of the launch advances the device step counter; every CTA

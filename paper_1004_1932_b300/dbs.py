@@ -22,7 +22,8 @@ OK = 0
 E_ARG, E_NOMEM, E_CUDA, E_OVERLAP, E_NONFINITE, E_TIMEOUT, E_STATE = -1, -2, -3, -4, -5, -6, -7
 OSEEN, RPY = 0, 1
 FP32C, FP64 = 0, 1
-PATH_GRID, PATH_CLUSTER = 0, 1
+PATH_GRID, PATH_CLUSTER, PATH_COOP = 0, 1, 2
+_PATHS = {"grid": PATH_GRID, "cluster": PATH_CLUSTER, "coop": PATH_COOP}
 K_PREFACTOR = 15.0 / 64.0  # Eq. (9d) as printed
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -204,14 +205,15 @@ class Suspension:
         return ms.value
 
     def set_path(self, path, cluster_size: int = 0):
-        """dbs_step path: "grid" (per-evaluation launches) or "cluster" (resident cluster)."""
-        p = {"grid": PATH_GRID, "cluster": PATH_CLUSTER}.get(path, path)
+        """dbs_step path: "grid" (per-evaluation launches), "cluster" (resident
+        cluster) or "coop" (one cooperative launch per up to 1024 steps)."""
+        p = _PATHS.get(path, path)
         self._check(load().dbs_set_path(self._h, ctypes.c_int32(int(p)), ctypes.c_int32(int(cluster_size))))
 
     def get_path(self):
         p, g = ctypes.c_int32(), ctypes.c_int32()
         self._check(load().dbs_get_path(self._h, ctypes.byref(p), ctypes.byref(g)))
-        return ("cluster" if p.value == PATH_CLUSTER else "grid"), g.value
+        return {v: k for k, v in _PATHS.items()}[p.value], g.value
 
     def set_chunks(self, chunks: int):
         """j-split of the pair sum (0 = built-in choice); used by the autotuner."""
@@ -506,6 +508,17 @@ def mobility_apply_noalloc(S, x_dev, F_dev, *, a, mu, mobility="rpy", v_dev, str
         None if stream is None else ctypes.c_void_p(_devptr_stream(stream)))
     if rc != OK:
         raise DbsError(rc, "dbs_mobility_apply_noalloc")
+
+
+def check_wait_timeout(timeout_ms: int = 100) -> int:
+    """Run the cooperative path's bounded wait on a word that nothing writes;
+    returns the status it reported (E_TIMEOUT expected).  Raises if the device
+    did not stay usable."""
+    st = ctypes.c_int32(-100)
+    rc = load().dbs_test_wait_timeout(ctypes.c_int32(int(timeout_ms)), ctypes.byref(st))
+    if rc != OK:
+        raise DbsError(rc, "dbs_test_wait_timeout")
+    return st.value
 
 
 class DeviceView:
