@@ -300,7 +300,7 @@ DBS_API int dbs_pair_distance_error(int64_t S, const double *A0_dev, const doubl
  *                    (about one second): a launch whose exchange cannot
  *                    complete ends with DBS_E_TIMEOUT instead of hanging.
  *                    FP32C, S <= 2048.  dbs_set_chunks on this path sets the
- *                    number of j-chunks (default 16, fewer if the grid would
+ *                    number of j-chunks (default 8, fewer if the grid would
  *                    not be co-resident).
  */
 #define DBS_PATH_COOP 2

@@ -59,6 +59,7 @@ struct EvalArgs {
     const double *sinphi; // [S] sin(phi^s)
     const double *cosphi; // [S] cos(phi^s)
     const double2 *trig;  // ring of (sin, cos)(omega t_k) at index k & trig_mask
+    const float4 *trig_df;  // the same ring as FP32 pairs (sin_hi, sin_lo, cos_hi, cos_lo)
     int trig_mask;
     double *vout;         // APPLY output [N][3]
     float *part;          // j-split partial sums [C][N][6] (FP32C) or [C][N][3] doubles (FP64)

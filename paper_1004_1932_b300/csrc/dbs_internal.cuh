@@ -29,6 +29,7 @@ struct dbs_suspension {
            *sinphi = nullptr, *cosphi = nullptr, *vout = nullptr, *Ftmp = nullptr;
     void *packA = nullptr, *packB = nullptr, *packT = nullptr;
     double2 *trig = nullptr;
+    float4 *trig_df = nullptr;
     int64_t trig_hi = -1;  // ring holds (sin, cos)(omega t_k) for k <= trig_hi (last TRIG_RING/2 fills)
     float *part = nullptr;
     unsigned *tickets = nullptr, *done = nullptr;

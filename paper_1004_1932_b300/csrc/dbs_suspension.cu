@@ -105,6 +105,7 @@ EvalArgs base_args(const dbs_suspension *h)
     A.sinphi = h->sinphi;
     A.cosphi = h->cosphi;
     A.trig = h->trig;
+    A.trig_df = h->trig_df;
     A.trig_mask = TRIG_RING - 1;
     A.vout = h->vout;
     A.part = h->part;
@@ -220,9 +221,10 @@ __global__ void pack_kernel(EvalArgs A, const double *Fgiven, double *Fd_out, vo
     store_rec((Rec *)out, s, xq, F, A);
 }
 
-// ring[k & mask] = (sin, cos)(omega t_k), t_k = k dt, for k in [k0, k0 + count)
-__global__ void trig_fill_kernel(double2 *ring, int mask, int64_t k0, int count, double omega,
-                                 double dt)
+// ring[k & mask] = (sin, cos)(omega t_k), t_k = k dt, for k in [k0, k0 + count);
+// ring_df holds the same values split into FP32 (hi, lo) pairs.
+__global__ void trig_fill_kernel(double2 *ring, float4 *ring_df, int mask, int64_t k0, int count,
+                                 double omega, double dt)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
@@ -230,6 +232,8 @@ __global__ void trig_fill_kernel(double2 *ring, int mask, int64_t k0, int count,
     double sw, cw;
     sincos(omega * ((double)k * dt), &sw, &cw);
     ring[k & mask] = make_double2(sw, cw);
+    const float sh = (float)sw, ch = (float)cw;
+    ring_df[k & mask] = make_float4(sh, (float)(sw - (double)sh), ch, (float)(cw - (double)ch));
 }
 
 __global__ void avg_start_kernel(EvalArgs A)
@@ -250,7 +254,7 @@ int ensure_trig(dbs_suspension *h, int64_t k_hi, cudaStream_t st)
     while (h->trig_hi < k_hi) {
         const int count = TRIG_RING / 2;
         trig_fill_kernel<<<(count + 127) / 128, 128, 0, st>>>(
-            h->trig, TRIG_RING - 1, h->trig_hi + 1, count, h->p.omega, h->p.dt);
+            h->trig, h->trig_df, TRIG_RING - 1, h->trig_hi + 1, count, h->p.omega, h->p.dt);
         CK(h, cudaGetLastError());
         h->trig_hi += count;
     }
@@ -388,6 +392,7 @@ static int alloc_all(dbs_suspension *h)
     CK(h, cudaMalloc(&h->packB, pack_bytes(h)));
     CK(h, cudaMalloc(&h->packT, pack_bytes(h)));
     CK(h, cudaMalloc(&h->trig, sizeof(double2) * TRIG_RING));
+    CK(h, cudaMalloc(&h->trig_df, sizeof(float4) * TRIG_RING));
     const int64_t iblocks = (h->S + h->bt - 1) / h->bt;
     if (h->chunks > 1) {
         const size_t pb = (size_t)h->chunks * h->S * (is_f64(h) ? 6 * sizeof(double) : 12 * sizeof(float));
@@ -415,7 +420,7 @@ static void free_all(dbs_suspension *h)
     drop_graph(h);
     drop_flow(h);
     void *bufs[] = {h->x, h->v0, h->Fd, h->Fext, h->lam, h->sinphi, h->cosphi, h->vout, h->Ftmp, h->packA,
-                    h->packB, h->packT, h->trig, h->part, h->tickets, h->done, h->step, h->flags,
+                    h->packB, h->packT, h->trig, h->trig_df, h->part, h->tickets, h->done, h->step, h->flags,
                     h->Racc, h->Rbar};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -626,10 +631,10 @@ int dbs_set_external_force(dbs_suspension *h, const double *F)
 // cooperative dataflow path (flow_kernel)
 // ---------------------------------------------------------------------------
 #ifndef DBS_FLOW_WARPS
-#define DBS_FLOW_WARPS 4
+#define DBS_FLOW_WARPS 8
 #endif
 constexpr int FLOW_W = DBS_FLOW_WARPS;     // warps per CTA
-constexpr int FLOW_MAX_C = 16;             // j-chunks per i-block by default
+constexpr int FLOW_MAX_C = 8;              // j-chunks per i-block by default
 constexpr int FLOW_MAX_STEPS = 1024;       // Heun steps per launch
 
 static const void *flow_fn(const dbs_suspension *h)
@@ -637,6 +642,9 @@ static const void *flow_fn(const dbs_suspension *h)
     return h->p.mobility == DBS_OSEEN ? (const void *)flow_kernel<0, FLOW_W>
                                       : (const void *)flow_kernel<1, FLOW_W>;
 }
+
+// dynamic shared memory of flow_kernel: the chunk's records
+static size_t flow_smem(int q, int /*C*/) { return (size_t)q * FLOW_IB * sizeof(DbF32); }
 
 static void drop_flow(dbs_suspension *h)
 {
@@ -660,7 +668,7 @@ int coop_setup(dbs_suspension *h)
     int q = std::max(1, (I + creq - 1) / creq), C = 0;
     for (;; ++q) {
         C = (I + q - 1) / q;
-        const size_t smem = (size_t)q * FLOW_IB * sizeof(DbF32);
+        const size_t smem = flow_smem(q, C);
         CK(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int occ = 0;
         CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 32 * FLOW_W, smem));
@@ -711,7 +719,7 @@ static int coop_step(dbs_suspension *h, int64_t n)
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(h->flow_I * h->flow_C);
         cfg.blockDim = dim3(32 * FLOW_W);
-        cfg.dynamicSmemBytes = (size_t)h->flow_q * FLOW_IB * sizeof(DbF32);
+        cfg.dynamicSmemBytes = flow_smem(h->flow_q, h->flow_C);
         cfg.stream = h->stream;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeCooperative;

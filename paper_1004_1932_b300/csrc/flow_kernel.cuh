@@ -30,10 +30,15 @@
 // others then run out too, so a launch always ends.
 //
 // Precision (FP32C).  Pair sums as in eval_kernel (FP32 pair math, two-sum
-// across ranges).  Positions stay FP64 (relative to the suspension's centre).
-// The spring force is formed from d^2 - L^2 computed in FP64, so that the
-// small stretch d - L = (d^2 - L^2)/(d + L) keeps FP32 relative accuracy; the
-// force itself, the velocity and the Heun average are FP32, as in the records.
+// across ranges).  Inside the launch the owner keeps positions (relative to
+// the suspension's centre) and the stroke-average sums as unevaluated FP32
+// pairs hi + lo (double-single, 48-bit significand; Dekker's exact two-sum and
+// FMA two-product), because an FP64 instruction costs a whole warp-issue slot
+// of 64 cycles on this part while FP32 pairs run at full rate.  The rest length
+// L and the squared length d^2 are formed in the same arithmetic, so the small
+// stretch d - L = (d^2 - L^2)/(d + L) keeps FP32 relative accuracy; the force,
+// the velocity and the Heun average are FP32, as in the records.  Positions
+// and sums enter and leave the launch as FP64.
 #pragma once
 #include "dbs_common.cuh"
 #include "eval_kernel.cuh"
@@ -53,13 +58,13 @@ struct FlowArgs {
 };
 
 // Owner state of one i-block, in shared memory (component-major: lane d reads
-// column d).
+// column d).  Positions are relative to the centre; all pairs are double-single.
 struct FlowOwner {
-    double xr[6][FLOW_IB];   // x - centre, spheres 2s (0..2) and 2s+1 (3..5)
-    double R[3][FLOW_IB];    // stroke-average accumulator (trapezoid sum)
-    double lam[FLOW_IB], sphi[FLOW_IB], cphi[FLOW_IB];
-    float F[6][FLOW_IB];     // force at the current evaluation point
-    float v0[6][FLOW_IB];    // Heun predictor velocity
+    float xh[6][FLOW_IB], xl[6][FLOW_IB];   // spheres 2s (0..2) and 2s+1 (3..5)
+    float Rh[3][FLOW_IB], Rl[3][FLOW_IB];   // stroke-average sums (trapezoid rule)
+    float lamh[FLOW_IB], laml[FLOW_IB], sph[FLOW_IB], spl[FLOW_IB], cph[FLOW_IB], cpl[FLOW_IB];
+    float F[6][FLOW_IB];                    // force at the current evaluation point
+    float v0[6][FLOW_IB];                   // Heun predictor velocity
     float fext[6][FLOW_IB];
 };
 
@@ -111,30 +116,103 @@ __device__ __noinline__ ulonglong2 wait_tagged(const ulonglong2 *p, unsigned tag
 
 __device__ __forceinline__ float lo_float(unsigned long long w) { return __uint_as_float((unsigned)w); }
 
-// Record floats of dumbbell d from the owner state: positions relative to the
-// centre (rounded once), G = F / (8 pi mu).
-__device__ __forceinline__ void owner_record(const FlowOwner &o, int d, float k8, float r[12])
+// ---- double-single (hi + lo) arithmetic, |lo| <= ulp(hi)/2 -------------------
+struct ds { float h, l; };
+
+__device__ __forceinline__ ds ds_fast(float a, float b)   // |a| >= |b|
 {
-    r[0] = (float)o.xr[0][d]; r[1] = (float)o.xr[3][d];
-    r[2] = (float)o.xr[1][d]; r[3] = (float)o.xr[4][d];
-    r[4] = (float)o.xr[2][d]; r[5] = (float)o.xr[5][d];
-    r[6] = o.F[0][d] * k8;  r[7] = o.F[3][d] * k8;
-    r[8] = o.F[1][d] * k8;  r[9] = o.F[4][d] * k8;
-    r[10] = o.F[2][d] * k8; r[11] = o.F[5][d] * k8;
+    const float s = a + b;
+    return {s, b - (s - a)};
 }
 
+__device__ __forceinline__ ds ds_add(ds a, ds b)
+{
+    const float s = a.h + b.h;
+    const float bb = s - a.h;
+    const float e = (a.h - (s - bb)) + (b.h - bb) + a.l + b.l;
+    return ds_fast(s, e);
+}
+
+__device__ __forceinline__ ds ds_mul(ds a, ds b)
+{
+    const float p = a.h * b.h;
+    const float e = fmaf(a.h, b.h, -p) + fmaf(a.h, b.l, a.l * b.h);
+    return ds_fast(p, e);
+}
+
+__device__ __forceinline__ ds ds_mul_f(ds a, float b)
+{
+    const float p = a.h * b;
+    return ds_fast(p, fmaf(a.h, b, -p) + a.l * b);
+}
+
+__device__ __forceinline__ ds ds_of(double x)
+{
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+
+__device__ __forceinline__ double ds_to_double(ds a) { return (double)a.h + (double)a.l; }
+
+__device__ __forceinline__ ds ds_neg(ds a) { return {-a.h, -a.l}; }
+
+// Poll the tagged words p[j] (bit j of `pending`) until all carry `tag`; every round issues the
+// loads of all words still missing, so a round costs one memory round trip
+// however many words it waits for.  False on timeout or abort (see wait_tagged).
+template <int NB>
+__device__ __forceinline__ bool wait_batch(const ulonglong2 *const (&p)[NB], unsigned pending,
+                                           unsigned tag, ulonglong2 (&v)[NB], int *flags,
+                                           unsigned long long timeout_ns)
+{
+    unsigned long long t0 = 0;
+    for (unsigned it = 0;; ++it) {
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+            if ((pending >> j) & 1u) v[j] = ld_tagged(p[j]);
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+            if (((pending >> j) & 1u) && tagged(v[j], tag)) pending &= ~(1u << j);
+        if (!pending) return true;
+        if (it == 0) t0 = flow_ns();
+        if ((it & 15u) == 15u) {
+            if (*(volatile int *)flags & FLAG_TIMEOUT) return false;
+            if (flow_ns() - t0 > timeout_ns) {
+                atomicOr(flags, FLAG_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void put_record(DbF32 *t, const float r[12])
+{
+    float4 *q = (float4 *)t;
+    q[0] = make_float4(r[0], r[1], r[2], r[3]);
+    q[1] = make_float4(r[4], r[5], r[6], r[7]);
+    q[2] = make_float4(r[8], r[9], r[10], r[11]);
+}
+
+__device__ __forceinline__ void publish_record(ulonglong2 *dst, const float r[12], unsigned tag)
+{
+#pragma unroll
+    for (int w = 0; w < 6; ++w) st_tagged(dst + w, r[2 * w], r[2 * w + 1], tag);
+}
+
+__device__ __forceinline__ bool finite_f(float v) { return ((__float_as_uint(v) >> 23) & 0xffu) != 0xffu; }
+
 template <int W>
-struct FlowMinBlocks { static constexpr int value = W <= 4 ? 4 : 2; };
+struct FlowMinBlocks { static constexpr int value = W <= 4 ? 4 : (W <= 8 ? 2 : 1); };
 
 template <int MOB, int W>
 __global__ void __launch_bounds__(32 * W, FlowMinBlocks<W>::value)
 flow_kernel(const EvalArgs A, const FlowArgs P)
 {
-    extern __shared__ float4 flow_smem[];  // the chunk's records, q * 32 DbF32
+    constexpr int NT = 32 * W;
+    extern __shared__ float4 flow_smem[];   // the chunk's records, q * 32 DbF32
     __shared__ FlowOwner own;
     __shared__ float red[W][6][FLOW_IB];
-    __shared__ float2 pairs[6][FLOW_IB];   // owner: own chunk's pair, then the folded total
-    __shared__ float tgt[6][FLOW_IB];      // non-owner: target positions (x0 x1 y0 y1 z0 z1)
+    __shared__ float2 pairs[6][FLOW_IB];    // owner: own chunk's pair, then the folded total
+    __shared__ float tgt[FLOW_IB][6];       // non-owner: target positions (x0 x1 y0 y1 z0 z1)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ib = blockIdx.x / P.C, c = blockIdx.x - ib * P.C;
@@ -145,73 +223,101 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
     const int s = ib * FLOW_IB + lane;
     const bool active = s < S;
     const int db = c * P.q * FLOW_IB;
-    const int m = min(db + P.q * FLOW_IB, S) - db;   // records in the chunk
-    const int own_off = ib * FLOW_IB - db;          // owner: own i-block's place in the tile
+    const int m = min(db + P.q * FLOW_IB, S) - db;    // records in the chunk
+    const int own_off = ib * FLOW_IB - db;           // owner: own i-block's place in the tile
+    const int n_ib = min(FLOW_IB, S - ib * FLOW_IB);  // dumbbells of i-block ib
     DbF32 *tile = (DbF32 *)flow_smem;
     const float k8 = A.inv8pimu_f;
+    const float inv6 = (float)A.inv6pimua, k0f = (float)A.k0;
     const double cen[3] = {A.cx, A.cy, A.cz};
+    const ds ell = ds_of(A.ell), dt = ds_of(A.dt);
 
     // ---- owner: load the state, publish the records of evaluation 0 ----------
     if (owner && warp == 0 && active) {
         const int64_t o = 6 * (int64_t)s;
+        float r[12];
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            own.xr[k][lane] = A.x[o + k] - cen[k % 3];
+            const ds x = ds_of(A.x[o + k] - cen[k % 3]);
+            own.xh[k][lane] = x.h;
+            own.xl[k][lane] = x.l;
             own.F[k][lane] = (float)A.Fd[o + k];
             own.fext[k][lane] = A.Fext ? (float)A.Fext[o + k] : 0.f;
         }
-        own.lam[lane] = A.lam[s];
-        own.sphi[lane] = A.sinphi[s];
-        own.cphi[lane] = A.cosphi[s];
+        ds t = ds_of(A.lam[s]);
+        own.lamh[lane] = t.h; own.laml[lane] = t.l;
+        t = ds_of(A.sinphi[s]);
+        own.sph[lane] = t.h; own.spl[lane] = t.l;
+        t = ds_of(A.cosphi[s]);
+        own.cph[lane] = t.h; own.cpl[lane] = t.l;
         if (A.avg_m > 0) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) own.R[k][lane] = A.Racc[3 * (int64_t)s + k];
+            for (int k = 0; k < 3; ++k) {
+                t = ds_of(A.Racc[3 * (int64_t)s + k]);
+                own.Rh[k][lane] = t.h;
+                own.Rl[k][lane] = t.l;
+            }
         }
-        float r[12];
-        owner_record(own, lane, k8, r);
-        float4 *t = (float4 *)(tile + own_off + lane);
-        t[0] = make_float4(r[0], r[1], r[2], r[3]);
-        t[1] = make_float4(r[4], r[5], r[6], r[7]);
-        t[2] = make_float4(r[8], r[9], r[10], r[11]);
-        ulonglong2 *dst = P.rec + (size_t)s * 6;
-#pragma unroll
-        for (int w = 0; w < 6; ++w) st_tagged(dst + w, r[2 * w], r[2 * w + 1], P.base);
+        r[0] = own.xh[0][lane]; r[1] = own.xh[3][lane]; r[2] = own.xh[1][lane];
+        r[3] = own.xh[4][lane]; r[4] = own.xh[2][lane]; r[5] = own.xh[5][lane];
+        r[6] = own.F[0][lane] * k8; r[7] = own.F[3][lane] * k8; r[8] = own.F[1][lane] * k8;
+        r[9] = own.F[4][lane] * k8; r[10] = own.F[2][lane] * k8; r[11] = own.F[5][lane] * k8;
+        put_record(tile + own_off + lane, r);
+        publish_record(P.rec + (size_t)s * 6, r, P.base);
     }
 
+    // words polled in step 1: the chunk's records (own i-block excepted on the
+    // owner), then, off the owner, the targets' positions (3 words each)
+    const int n_chunk = (m - (owner ? n_ib : 0)) * 6;
+    const int n_words = n_chunk + (owner ? 0 : 3 * n_ib);
     const float2 c2 = make_float2(A.c2, A.c2), c3 = make_float2(A.c3, A.c3);
-    for (int e = 0; e < 2 * P.K; ++e) {
-        const unsigned tag = P.base + (unsigned)e;
-        const int par = e & 1;
-        const bool corr = (e & 1) != 0;
-        const int64_t n = P.n0 + (e >> 1);
-        const ulonglong2 *R = P.rec + (size_t)par * Spad * 6;
 
-        // 1. the chunk's records (own i-block excepted on the owner) and the targets
+    for (int ev = 0; ev < 2 * P.K; ++ev) {
+        const unsigned tag = P.base + (unsigned)ev;
+        const int par = ev & 1;
+        const bool corr = (ev & 1) != 0;
+        const int64_t n = P.n0 + (ev >> 1);
+        const ulonglong2 *R = P.rec + (size_t)par * Spad * 6;
+        float4 trig = make_float4(0.f, 0.f, 1.f, 0.f);
+        if (owner && warp == 0) trig = A.trig_df[(n + 1) & A.trig_mask];   // used by the epilogue
+
+        // 1. poll the words of this evaluation, up to 8 per thread in flight
         bool ok = true;
-        for (int idx = tid; idx < m * 6; idx += 32 * W) {
-            const int jr = idx / 6, w = idx - jr * 6;
-            if (owner && jr >= own_off && jr < own_off + FLOW_IB) continue;
-            const ulonglong2 v = wait_tagged(R + (size_t)(db + jr) * 6 + w, tag, A.flags, P.timeout_ns);
-            if (!tagged(v, tag)) {
-                ok = false;
-                break;
-            }
-            float *t = (float *)(tile + jr) + 2 * w;
-            t[0] = lo_float(v.x);
-            t[1] = lo_float(v.y);
-        }
-        if (!owner && ok) {
-            for (int idx = tid; idx < FLOW_IB * 3; idx += 32 * W) {
-                const int d = idx / 3, w = idx - d * 3;
-                if (ib * FLOW_IB + d >= S) continue;
-                const ulonglong2 v =
-                    wait_tagged(R + (size_t)(ib * FLOW_IB + d) * 6 + w, tag, A.flags, P.timeout_ns);
-                if (!tagged(v, tag)) {
-                    ok = false;
-                    break;
+        for (int b0 = 0; b0 < n_words && ok; b0 += 8 * NT) {
+            const ulonglong2 *pp[8];
+            unsigned pend = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int idx = b0 + j * NT + tid;
+                pp[j] = R;
+                if (idx < n_chunk) {
+                    const int jj = idx / 6, w = idx - jj * 6;
+                    const int jr = (owner && jj >= own_off) ? jj + n_ib : jj;
+                    pp[j] = R + (size_t)(db + jr) * 6 + w;
+                    pend |= 1u << j;
+                } else if (idx < n_words) {
+                    const int t = idx - n_chunk, d = t / 3, w = t - d * 3;
+                    pp[j] = R + (size_t)(ib * FLOW_IB + d) * 6 + w;
+                    pend |= 1u << j;
                 }
-                tgt[2 * w][d] = lo_float(v.x);
-                tgt[2 * w + 1][d] = lo_float(v.y);
+            }
+            ulonglong2 v[8];
+            ok = wait_batch<8>(pp, pend, tag, v, A.flags, P.timeout_ns);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (!((pend >> j) & 1u)) continue;
+                const int idx = b0 + j * NT + tid;
+                float *dst;
+                if (idx < n_chunk) {
+                    const int jj = idx / 6, w = idx - jj * 6;
+                    const int jr = (owner && jj >= own_off) ? jj + n_ib : jj;
+                    dst = (float *)(tile + jr) + 2 * w;
+                } else {
+                    const int t = idx - n_chunk, d = t / 3, w = t - d * 3;
+                    dst = &tgt[d][2 * w];
+                }
+                dst[0] = lo_float(v[j].x);
+                dst[1] = lo_float(v[j].y);
             }
         }
         if (__syncthreads_or(!ok)) return;
@@ -219,20 +325,20 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
         // 2. sweep: warp `warp` takes records [j0, j1) of the chunk
         float2 qa[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         float2 qb[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        float r2min = 3.0e38f;
         if (active) {
             float p[6];
             if (owner) {
-                const float4 a = tile[own_off + lane].a, b = tile[own_off + lane].b;
-                p[0] = a.x; p[1] = a.y; p[2] = a.z; p[3] = a.w; p[4] = b.x; p[5] = b.y;
+                const float4 a4 = tile[own_off + lane].a, b4 = tile[own_off + lane].b;
+                p[0] = a4.x; p[1] = a4.y; p[2] = a4.z; p[3] = a4.w; p[4] = b4.x; p[5] = b4.y;
             } else {
 #pragma unroll
-                for (int k = 0; k < 6; ++k) p[k] = tgt[k][lane];
+                for (int k = 0; k < 6; ++k) p[k] = tgt[lane][k];
             }
             const float2 pax = make_float2(p[0], p[0]), pay = make_float2(p[2], p[2]);
             const float2 paz = make_float2(p[4], p[4]), pbx = make_float2(p[1], p[1]);
             const float2 pby = make_float2(p[3], p[3]), pbz = make_float2(p[5], p[5]);
             const int j0 = (m * warp) / W, j1 = (m * (warp + 1)) / W;
+            float r2min = 3.0e38f;
             if (!owner) {
 #pragma unroll 2
                 for (int k = j0; k < j1; ++k) {
@@ -246,6 +352,7 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
                                       qb[2], r2min, false, false);
                 }
             } else {
+                // the owner's chunk holds its own dumbbells: mask the self pairs
                 for (int k = j0; k < j1; ++k) {
                     const float4 ra = tile[k].a, rb = tile[k].b, rc = tile[k].c;
                     const float2 jx = make_float2(ra.x, ra.y), jy = make_float2(ra.z, ra.w);
@@ -269,9 +376,9 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
 
         // 3a. fold the W warp sums; a non-owner publishes its pair and is done
         ulonglong2 *Pp = P.part + (size_t)par * P.C * Spad * 6;
-        for (int it = tid; it < 6 * FLOW_IB; it += 32 * W) {
+        for (int it = tid; it < 6 * FLOW_IB; it += NT) {
             const int k = it >> 5, d = it & 31;
-            if (ib * FLOW_IB + d >= S) continue;
+            if (d >= n_ib) continue;
             float sum = red[0][k][d], cmp = 0.f;
 #pragma unroll
             for (int w = 1; w < W; ++w) two_sum_acc(sum, cmp, red[w][k][d]);
@@ -279,40 +386,30 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
             else st_tagged(Pp + ((size_t)c * Spad + ib * FLOW_IB + d) * 6 + k, sum, cmp, tag);
         }
         if (!owner) continue;
-        __syncthreads();
 
-        // 3b. owner: all C pairs in chunk order
-        for (int it = tid; it < 6 * FLOW_IB; it += 32 * W) {
+        // 3b. owner: all C pairs in chunk order (the same thread wrote pairs[k][d])
+        for (int it = tid; it < 6 * FLOW_IB; it += NT) {
             const int k = it >> 5, d = it & 31;
+            if (d >= n_ib) continue;
             const int sd = ib * FLOW_IB + d;
-            if (sd >= S) continue;
             float sum = 0.f, cmp = 0.f;
-            for (int cb = 0; cb < P.C; cb += 8) {
-                // up to 8 chunks' words in flight at once, then the stragglers one by one
-                ulonglong2 v[8];
+            for (int cb = 0; cb < P.C && ok; cb += 8) {
+                const ulonglong2 *pp[8];
+                unsigned pend = 0;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int cc = cb + j;
-                    v[j] = (cc < P.C && cc != c) ? ld_tagged(Pp + ((size_t)cc * Spad + sd) * 6 + k)
-                                                 : make_ulonglong2(0ull, 0ull);
+                    pp[j] = Pp + ((size_t)(cc < P.C ? cc : c) * Spad + sd) * 6 + k;
+                    if (cc < P.C && cc != c) pend |= 1u << j;
                 }
+                ulonglong2 v[8];
+                ok = wait_batch<8>(pp, pend, tag, v, A.flags, P.timeout_ns);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int cc = cb + j;
                     if (cc < P.C) {
-                        float ps, pc;
-                        if (cc == c) {
-                            ps = pairs[k][d].x;
-                            pc = pairs[k][d].y;
-                        } else {
-                            if (!tagged(v[j], tag)) {
-                                v[j] = wait_tagged(Pp + ((size_t)cc * Spad + sd) * 6 + k, tag, A.flags,
-                                                   P.timeout_ns);
-                                ok &= tagged(v[j], tag);
-                            }
-                            ps = lo_float(v[j].x);
-                            pc = lo_float(v[j].y);
-                        }
+                        const float ps = cc == c ? pairs[k][d].x : lo_float(v[j].x);
+                        const float pc = cc == c ? pairs[k][d].y : lo_float(v[j].y);
                         if (cc == 0) {
                             sum = ps;
                             cmp = pc;
@@ -322,9 +419,7 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
                         }
                     }
                 }
-                if (!ok) break;
             }
-            // every thread has read pairs[k][d] of its own items before rewriting them
             pairs[k][d] = make_float2(sum, cmp);
         }
         if (__syncthreads_or(!ok)) return;
@@ -334,89 +429,68 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
             const int d = lane;
             float v[6];
 #pragma unroll
-            for (int k = 0; k < 6; ++k)
-                v[k] = fmaf(own.F[k][d], (float)A.inv6pimua, pairs[k][d].x + pairs[k][d].y);  // Eq. (3a)
-            double xq[6];
-            if (!corr) {
+            for (int k = 0; k < 6; ++k) v[k] = fmaf(own.F[k][d], inv6, pairs[k][d].x + pairs[k][d].y);  // Eq. (3a)
+            ds xq[6];
+            bool fin = true;
 #pragma unroll
-                for (int k = 0; k < 6; ++k) {
+            for (int k = 0; k < 6; ++k) {
+                const ds x = {own.xh[k][d], own.xl[k][d]};
+                if (!corr) {
                     own.v0[k][d] = v[k];
-                    xq[k] = fma(A.dt, (double)v[k], own.xr[k][d]);             // x~ = x_n + dt v0
+                    xq[k] = ds_add(x, ds_mul_f(dt, v[k]));                          // x~ = x_n + dt v0
+                } else {
+                    xq[k] = ds_add(x, ds_mul_f(dt, 0.5f * (own.v0[k][d] + v[k])));  // x_n + dt/2 (v0 + v1)
+                    own.xh[k][d] = xq[k].h;
+                    own.xl[k][d] = xq[k].l;
                 }
-            } else {
-#pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    xq[k] = fma(A.dt, (double)(0.5f * (own.v0[k][d] + v[k])), own.xr[k][d]);
-                    own.xr[k][d] = xq[k];                                       // x_n + dt/2 (v0 + v1)
-                }
+                fin &= finite_f(xq[k].h);
             }
-            if (!finite6(xq)) atomicOr(A.flags, FLAG_NONFINITE);
+            if (!fin) atomicOr(A.flags, FLAG_NONFINITE);
             // Eq. (4) at t_{n+1}: F_a = k0 (d - L) e/d with d - L = (d^2 - L^2)/(d + L)
-            const double2 sc = A.trig[(n + 1) & A.trig_mask];
-            const double L = rest_length(A.ell, own.lam[d], sc.x, sc.y, own.sphi[d], own.cphi[d]);
-            const double ex = xq[3] - xq[0], ey = xq[4] - xq[1], ez = xq[5] - xq[2];
-            const double dd = fma(ez, ez, fma(ey, ey, ex * ex));
-            const float stretch2 = (float)fma(-L, L, dd);
-            const float dist = sqrtf((float)dd);
-            const float f = (float)A.k0 * (stretch2 / (dist + (float)L)) / dist;
-            const float fe[3] = {f * (float)ex, f * (float)ey, f * (float)ez};
+            const ds sarg = ds_add(ds_mul({trig.x, trig.y}, {own.cph[d], own.cpl[d]}),
+                                   ds_mul({trig.z, trig.w}, {own.sph[d], own.spl[d]}));
+            const ds L = ds_add(ell, ds_mul({own.lamh[d], own.laml[d]}, sarg));
+            const ds ex = ds_add(xq[3], ds_neg(xq[0]));
+            const ds ey = ds_add(xq[4], ds_neg(xq[1]));
+            const ds ez = ds_add(xq[5], ds_neg(xq[2]));
+            const ds dd = ds_add(ds_add(ds_mul(ex, ex), ds_mul(ey, ey)), ds_mul(ez, ez));
+            const ds st2 = ds_add(dd, ds_neg(ds_mul(L, L)));
+            const float rd = rsqrtf(dd.h);
+            const float f = k0f * __fdividef((st2.h + st2.l) * rd, dd.h * rd + L.h);
+            const float fe[3] = {f * ex.h, f * ey.h, f * ez.h};
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 own.F[k][d] = fe[k] + own.fext[k][d];
                 own.F[3 + k][d] = -fe[k] + own.fext[3 + k][d];
             }
-            if (!corr) {
-                // the predictor point's record (positions of x~), kept apart from x_n
-                float r[12];
-                r[0] = (float)xq[0]; r[1] = (float)xq[3]; r[2] = (float)xq[1];
-                r[3] = (float)xq[4]; r[4] = (float)xq[2]; r[5] = (float)xq[5];
-                r[6] = own.F[0][d] * k8; r[7] = own.F[3][d] * k8; r[8] = own.F[1][d] * k8;
-                r[9] = own.F[4][d] * k8; r[10] = own.F[2][d] * k8; r[11] = own.F[5][d] * k8;
-                float4 *t = (float4 *)(tile + own_off + d);
-                t[0] = make_float4(r[0], r[1], r[2], r[3]);
-                t[1] = make_float4(r[4], r[5], r[6], r[7]);
-                t[2] = make_float4(r[8], r[9], r[10], r[11]);
-                ulonglong2 *dst = P.rec + ((size_t)(par ^ 1) * Spad + s) * 6;
+            float r[12];
+            r[0] = xq[0].h; r[1] = xq[3].h; r[2] = xq[1].h; r[3] = xq[4].h; r[4] = xq[2].h; r[5] = xq[5].h;
+            r[6] = own.F[0][d] * k8; r[7] = own.F[3][d] * k8; r[8] = own.F[1][d] * k8;
+            r[9] = own.F[4][d] * k8; r[10] = own.F[2][d] * k8; r[11] = own.F[5][d] * k8;
+            put_record(tile + own_off + d, r);
+            if (ev + 1 < 2 * P.K) publish_record(P.rec + ((size_t)(par ^ 1) * Spad + s) * 6, r, tag + 1);
+            else put_record(P.pack + s, r);   // the final state's records, for the grid path
+            // stroke average of the geometric centre (corrector), trapezoid rule
+            if (corr && A.avg_m > 0) {
+                const int64_t k_local = n + 1 - A.avg_n0;
+                if (k_local > 0) {
+                    const bool end = (k_local % A.avg_m) == 0;
+                    const int64_t kidx = k_local / A.avg_m - 1;
 #pragma unroll
-                for (int w = 0; w < 6; ++w) st_tagged(dst + w, r[2 * w], r[2 * w + 1], tag + 1);
-            } else {
-                float r[12];
-                owner_record(own, d, k8, r);
-                float4 *t = (float4 *)(tile + own_off + d);
-                t[0] = make_float4(r[0], r[1], r[2], r[3]);
-                t[1] = make_float4(r[4], r[5], r[6], r[7]);
-                t[2] = make_float4(r[8], r[9], r[10], r[11]);
-                if (e + 1 < 2 * P.K) {
-                    ulonglong2 *dst = P.rec + ((size_t)(par ^ 1) * Spad + s) * 6;
-#pragma unroll
-                    for (int w = 0; w < 6; ++w) st_tagged(dst + w, r[2 * w], r[2 * w + 1], tag + 1);
-                } else {
-                    DbF32 pr;
-                    pr.a = t[0];
-                    pr.b = t[1];
-                    pr.c = t[2];
-                    P.pack[s] = pr;
-                }
-                // stroke average of the geometric centre, trapezoid rule
-                if (A.avg_m > 0) {
-                    const int64_t k_local = n + 1 - A.avg_n0;
-                    if (k_local > 0) {
-                        const bool end = (k_local % A.avg_m) == 0;
-                        const int64_t kidx = k_local / A.avg_m - 1;
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            const double Rt = 0.5 * (xq[k] + xq[3 + k]) + cen[k];
-                            double acc = own.R[k][d];
-                            if (end) {
-                                acc += 0.5 * Rt;
-                                if (kidx < A.avg_maxk)
-                                    A.Rbar[kidx * 3 * A.S + 3 * (int64_t)s + k] = acc / (double)A.avg_m;
-                                acc = 0.5 * Rt;
-                            } else {
-                                acc += Rt;
-                            }
-                            own.R[k][d] = acc;
+                    for (int k = 0; k < 3; ++k) {
+                        ds Rt = ds_add(xq[k], xq[3 + k]);
+                        Rt = ds_add({0.5f * Rt.h, 0.5f * Rt.l}, ds_of(cen[k]));
+                        ds acc = {own.Rh[k][d], own.Rl[k][d]};
+                        if (end) {
+                            acc = ds_add(acc, {0.5f * Rt.h, 0.5f * Rt.l});
+                            if (kidx < A.avg_maxk)
+                                A.Rbar[kidx * 3 * A.S + 3 * (int64_t)s + k] = ds_to_double(acc) / (double)A.avg_m;
+                            acc = {0.5f * Rt.h, 0.5f * Rt.l};
+                        } else {
+                            acc = ds_add(acc, Rt);
                         }
+                        own.Rh[k][d] = acc.h;
+                        own.Rl[k][d] = acc.l;
                     }
                 }
             }
@@ -429,12 +503,13 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
         const int64_t o = 6 * (int64_t)s;
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            A.x[o + k] = own.xr[k][lane] + cen[k % 3];
+            A.x[o + k] = ds_to_double({own.xh[k][lane], own.xl[k][lane]}) + cen[k % 3];
             A.Fd[o + k] = (double)own.F[k][lane];
         }
         if (A.avg_m > 0) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) A.Racc[3 * (int64_t)s + k] = own.R[k][lane];
+            for (int k = 0; k < 3; ++k)
+                A.Racc[3 * (int64_t)s + k] = ds_to_double({own.Rh[k][lane], own.Rl[k][lane]});
         }
     }
     if (blockIdx.x == 0 && tid == 0) *A.step = P.n0 + P.K;
