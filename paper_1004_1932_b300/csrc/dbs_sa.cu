@@ -1,9 +1,10 @@
 // Stroke-averaged far-field model, Eqs. (9a)-(9e) (Sec. III.B), and the
 // pair-distance comparison of the averaged model against the microscopic one.
 //
-// One thread owns one dumbbell s and sweeps all others r through shared-memory
-// tiles of packed records (centre relative to the system centre, amplitude,
-// orientation, sin/cos of the phase).  Per pair, with D = R^s - R^r,
+// A CTA owns 32 dumbbells s (one per lane); its 8 warps split every
+// shared-memory tile of packed source records r (centre relative to the system
+// centre, amplitude, orientation, sin/cos of the phase) and their partial sums
+// are folded in warp order.  Per pair, with D = R^s - R^r,
 // Dh = D/|D|, s = Dh.N^s, r = Dh.N^r, q = N^s.N^r and
 // sin(phi^s - phi^r) = sin phi^s cos phi^r - cos phi^s sin phi^r:
 //   J = (9/64) a w ell^2 lam^s lam^r sin(dphi) |D|^-4
@@ -18,6 +19,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -28,8 +30,9 @@ using namespace dbs;
 
 namespace {
 
-constexpr int SA_BT = 64;
-constexpr int SA_TILE = 128;
+constexpr int SA_LANES = 32;  // target dumbbells per CTA (one per lane)
+constexpr int SA_W = 8;       // warps per CTA; each takes 1/SA_W of every tile
+constexpr int SA_TILE = 256;
 thread_local char g_sa_create_error[256] = "";
 
 struct __align__(16) SaRecF32 {
@@ -121,12 +124,13 @@ __device__ __forceinline__ void sa_pair(bool self, T Rx, T Ry, T Rz, T lam_s, T 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(SA_BT) sa_eval_kernel(SaArgs A)
+__global__ void __launch_bounds__(SA_LANES * SA_W) sa_eval_kernel(SaArgs A)
 {
     using Rec = typename SaRecOf<T>::type;
     __shared__ Rec tile[SA_TILE];
-    const int tid = threadIdx.x;
-    const int64_t sg = (int64_t)blockIdx.x * SA_BT + tid;
+    __shared__ T red[SA_W][12][SA_LANES];   // per warp: J sum, J comp., K sum, K comp. (x, y, z)
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t sg = (int64_t)blockIdx.x * SA_LANES + lane;
     const bool active = sg < A.S;
     const Rec *in = (const Rec *)A.rec_in;
     Rec me{};
@@ -144,10 +148,11 @@ __global__ void __launch_bounds__(SA_BT) sa_eval_kernel(SaArgs A)
     for (int64_t t0 = 0; t0 < A.S; t0 += SA_TILE) {
         const int len = (int)min((int64_t)SA_TILE, A.S - t0);
         __syncthreads();
-        for (int k = tid; k < len; k += SA_BT) tile[k] = in[t0 + k];
+        for (int k = tid; k < len; k += SA_LANES * SA_W) tile[k] = in[t0 + k];
         __syncthreads();
+        const int k0 = (len * warp) / SA_W, k1 = (len * (warp + 1)) / SA_W;
         T J[3] = {0, 0, 0}, K[3] = {0, 0, 0};
-        for (int k = 0; k < len; ++k)
+        for (int k = k0; k < k1; ++k)
             sa_pair<T, Rec>(t0 + k == sg, Rx, Ry, Rz, lam, Nx, Ny, Nz, sn, cs, tile[k], J, K);
         if constexpr (sizeof(T) == 4) {
             for (int k = 0; k < 3; ++k) {
@@ -158,6 +163,28 @@ __global__ void __launch_bounds__(SA_BT) sa_eval_kernel(SaArgs A)
             for (int k = 0; k < 3; ++k) {
                 Js[k] += J[k];
                 Ks[k] += K[k];
+            }
+        }
+    }
+    for (int k = 0; k < 3; ++k) {
+        red[warp][k][lane] = Js[k];
+        red[warp][3 + k][lane] = Jc[k];
+        red[warp][6 + k][lane] = Ks[k];
+        red[warp][9 + k][lane] = Kc[k];
+    }
+    __syncthreads();
+    if (warp != 0) return;
+    // the SA_W warp partials, in warp order
+    for (int w = 1; w < SA_W; ++w) {
+        for (int k = 0; k < 3; ++k) {
+            if constexpr (sizeof(T) == 4) {
+                two_sum_acc(Js[k], Jc[k], red[w][k][lane]);
+                Jc[k] += red[w][3 + k][lane];
+                two_sum_acc(Ks[k], Kc[k], red[w][6 + k][lane]);
+                Kc[k] += red[w][9 + k][lane];
+            } else {
+                Js[k] += red[w][k][lane];
+                Ks[k] += red[w][6 + k][lane];
             }
         }
     }
@@ -232,43 +259,76 @@ __global__ void sa_pack_kernel(SaArgs A)
 }
 
 // ---- pair-distance comparison (FP64) ----------------------------------------
-constexpr int CMP_BT = 256;
+// The upper triangle of pairs (s < r) is cut into 32 x 32 tiles; CTAs take
+// tiles in a grid-stride loop, reduce their pairs in a fixed tree order into a
+// per-CTA partial, and the last CTA to finish (arrival ticket) combines the
+// partials in CTA order, so the result does not depend on CTA timing.  The
+// partials live in a file-scope device array: calls are serialised on the host.
+constexpr int PD_T = 32;
+constexpr int PD_BT = 256;
+constexpr int PD_MAX_BLOCKS = 1184;
+__device__ double g_pd_part[PD_MAX_BLOCKS * 3];
+__device__ double g_pd_out[3];
+__device__ unsigned g_pd_ticket;
 
-__global__ void __launch_bounds__(CMP_BT) pair_dist_kernel(int64_t S, const double *A0, const double *A1,
-                                                           const double *B0, const double *B1,
-                                                           double *blk_out)
+// tile t of the upper triangle (row-major) -> block row bi, block column bj >= bi
+__device__ __forceinline__ void pd_tile(int64_t t, int64_t nb, int64_t &bi, int64_t &bj)
 {
-    __shared__ double smax[CMP_BT], ssq[CMP_BT], sref[CMP_BT];
+    const double b = 2.0 * (double)nb + 1.0;
+    int64_t i = (int64_t)floor((b - sqrt(b * b - 8.0 * (double)t)) * 0.5);
+    auto start = [nb](int64_t r) { return r * nb - r * (r - 1) / 2; };  // first tile of row r
+    if (i < 0) i = 0;
+    while (i > 0 && start(i) > t) --i;
+    while (i + 1 < nb && start(i + 1) <= t) ++i;
+    bi = i;
+    bj = i + (t - start(i));
+}
+
+__device__ __forceinline__ double pd_dist(const double *a, const double *b)
+{
+    const double x = a[0] - b[0], y = a[1] - b[1], z = a[2] - b[2];
+    return sqrt(fma(z, z, fma(y, y, x * x)));
+}
+
+__global__ void __launch_bounds__(PD_BT) pair_dist_kernel(int64_t S, const double *A0, const double *A1,
+                                                           const double *B0, const double *B1)
+{
+    __shared__ double rows[4][PD_T][3], cols[4][PD_T][3];
+    __shared__ double smax[PD_BT], ssq[PD_BT], sref[PD_BT];
+    __shared__ int s_last;
     const int tid = threadIdx.x;
+    const double *src[4] = {A0, A1, B0, B1};
+    const int64_t nb = (S + PD_T - 1) / PD_T, ntiles = nb * (nb + 1) / 2;
     double mx = 0, sq = 0, rf = 0;
-    // rows s in a grid-stride loop; each thread handles pairs (s, r > s)
-    for (int64_t s = (int64_t)blockIdx.x * CMP_BT + tid; s < S; s += (int64_t)gridDim.x * CMP_BT) {
-        const double a0x = A0[3 * s], a0y = A0[3 * s + 1], a0z = A0[3 * s + 2];
-        const double a1x = A1[3 * s], a1y = A1[3 * s + 1], a1z = A1[3 * s + 2];
-        const double b0x = B0[3 * s], b0y = B0[3 * s + 1], b0z = B0[3 * s + 2];
-        const double b1x = B1[3 * s], b1y = B1[3 * s + 1], b1z = B1[3 * s + 2];
-        for (int64_t r = s + 1; r < S; ++r) {
-            double e;
-            const double dA1 = sqrt((a1x - A1[3 * r]) * (a1x - A1[3 * r]) + (a1y - A1[3 * r + 1]) * (a1y - A1[3 * r + 1]) +
-                                    (a1z - A1[3 * r + 2]) * (a1z - A1[3 * r + 2]));
-            const double dA0 = sqrt((a0x - A0[3 * r]) * (a0x - A0[3 * r]) + (a0y - A0[3 * r + 1]) * (a0y - A0[3 * r + 1]) +
-                                    (a0z - A0[3 * r + 2]) * (a0z - A0[3 * r + 2]));
-            const double dB1 = sqrt((b1x - B1[3 * r]) * (b1x - B1[3 * r]) + (b1y - B1[3 * r + 1]) * (b1y - B1[3 * r + 1]) +
-                                    (b1z - B1[3 * r + 2]) * (b1z - B1[3 * r + 2]));
-            const double dB0 = sqrt((b0x - B0[3 * r]) * (b0x - B0[3 * r]) + (b0y - B0[3 * r + 1]) * (b0y - B0[3 * r + 1]) +
-                                    (b0z - B0[3 * r + 2]) * (b0z - B0[3 * r + 2]));
-            const double dA = dA1 - dA0, dB = dB1 - dB0;
-            e = dA - dB;
-            mx = fmax(mx, fabs(e));
-            sq += e * e;
-            rf += dB * dB;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        int64_t bi, bj;
+        pd_tile(t, nb, bi, bj);
+        __syncthreads();
+        for (int q = tid; q < 4 * PD_T * 3; q += PD_BT) {
+            const int a = q / (PD_T * 3), e = (q / 3) % PD_T, k = q % 3;
+            const int64_t s = bi * PD_T + e, r = bj * PD_T + e;
+            rows[a][e][k] = s < S ? src[a][3 * s + k] : 0.0;
+            cols[a][e][k] = r < S ? src[a][3 * r + k] : 0.0;
+        }
+        __syncthreads();
+        const int e = tid & (PD_T - 1);
+        const int64_t s = bi * PD_T + e;
+        for (int f = tid / PD_T; f < PD_T; f += PD_BT / PD_T) {
+            const int64_t r = bj * PD_T + f;
+            if (s >= S || r >= S || r <= s) continue;
+            const double dA = pd_dist(rows[1][e], cols[1][f]) - pd_dist(rows[0][e], cols[0][f]);
+            const double dB = pd_dist(rows[3][e], cols[3][f]) - pd_dist(rows[2][e], cols[2][f]);
+            const double err = dA - dB;
+            mx = fmax(mx, fabs(err));
+            sq = fma(err, err, sq);
+            rf = fma(dB, dB, rf);
         }
     }
     smax[tid] = mx;
     ssq[tid] = sq;
     sref[tid] = rf;
     __syncthreads();
-    for (int w = CMP_BT / 2; w > 0; w >>= 1) {
+    for (int w = PD_BT / 2; w > 0; w >>= 1) {
         if (tid < w) {
             smax[tid] = fmax(smax[tid], smax[tid + w]);
             ssq[tid] += ssq[tid + w];
@@ -277,9 +337,41 @@ __global__ void __launch_bounds__(CMP_BT) pair_dist_kernel(int64_t S, const doub
         __syncthreads();
     }
     if (tid == 0) {
-        blk_out[3 * blockIdx.x] = smax[0];
-        blk_out[3 * blockIdx.x + 1] = ssq[0];
-        blk_out[3 * blockIdx.x + 2] = sref[0];
+        g_pd_part[3 * blockIdx.x] = smax[0];
+        g_pd_part[3 * blockIdx.x + 1] = ssq[0];
+        g_pd_part[3 * blockIdx.x + 2] = sref[0];
+        __threadfence();
+        s_last = atomicAdd(&g_pd_ticket, 1u) == gridDim.x - 1u;
+        if (s_last) __threadfence();
+    }
+    __syncthreads();
+    if (!s_last) return;
+    // last CTA: thread t folds partials t, t + PD_BT, ... in order, then the tree
+    mx = 0;
+    sq = 0;
+    rf = 0;
+    for (unsigned b = tid; b < gridDim.x; b += PD_BT) {
+        mx = fmax(mx, __ldcg(&g_pd_part[3 * b]));
+        sq += __ldcg(&g_pd_part[3 * b + 1]);
+        rf += __ldcg(&g_pd_part[3 * b + 2]);
+    }
+    smax[tid] = mx;
+    ssq[tid] = sq;
+    sref[tid] = rf;
+    __syncthreads();
+    for (int w = PD_BT / 2; w > 0; w >>= 1) {
+        if (tid < w) {
+            smax[tid] = fmax(smax[tid], smax[tid + w]);
+            ssq[tid] += ssq[tid + w];
+            sref[tid] += sref[tid + w];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        g_pd_out[0] = smax[0];
+        g_pd_out[1] = ssq[0];
+        g_pd_out[2] = sref[0];
+        g_pd_ticket = 0u;
     }
 }
 
@@ -350,9 +442,9 @@ static SaArgs sa_args(const dbs_sa *h)
 
 static void sa_launch(const dbs_sa *h, const SaArgs &A)
 {
-    const int blocks = (int)((h->p.S + SA_BT - 1) / SA_BT);
-    if (sa_f64(h)) sa_eval_kernel<double><<<blocks, SA_BT, 0, h->stream>>>(A);
-    else sa_eval_kernel<float><<<blocks, SA_BT, 0, h->stream>>>(A);
+    const int blocks = (int)((h->p.S + SA_LANES - 1) / SA_LANES);
+    if (sa_f64(h)) sa_eval_kernel<double><<<blocks, SA_LANES * SA_W, 0, h->stream>>>(A);
+    else sa_eval_kernel<float><<<blocks, SA_LANES * SA_W, 0, h->stream>>>(A);
 }
 
 static int sa_repack(dbs_sa *h)
@@ -541,27 +633,21 @@ int dbs_sa_copy_centres(dbs_sa *h, double *R_dev)
 int dbs_pair_distance_error(int64_t S, const double *A0, const double *A1, const double *B0,
                             const double *B1, double *out, void *stream)
 {
-    if (S < 2 || !A0 || !A1 || !B0 || !B1 || !out) return DBS_E_ARG;
+    if (S < 2 || S > (int64_t)1 << 31 || !A0 || !A1 || !B0 || !B1 || !out) return DBS_E_ARG;
+    static std::mutex mu;  // the partials and the ticket are one file-scope array per device
+    std::lock_guard<std::mutex> lock(mu);
     cudaStream_t st = (cudaStream_t)stream;
-    const int blocks = (int)std::min<int64_t>(148, (S + CMP_BT - 1) / CMP_BT);
-    double *blk = nullptr;
-    if (cudaMalloc(&blk, sizeof(double) * 3 * blocks) != cudaSuccess) return DBS_E_NOMEM;
-    pair_dist_kernel<<<blocks, CMP_BT, 0, st>>>(S, A0, A1, B0, B1, blk);
-    std::vector<double> hb(3 * blocks);
+    const int64_t nb = (S + PD_T - 1) / PD_T, ntiles = nb * (nb + 1) / 2;
+    const int blocks = (int)std::min<int64_t>(PD_MAX_BLOCKS, ntiles);
+    pair_dist_kernel<<<blocks, PD_BT, 0, st>>>(S, A0, A1, B0, B1);
+    double hb[3];
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), blk, sizeof(double) * 3 * blocks, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbolAsync(hb, g_pd_out, sizeof(hb), 0, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(blk);
     if (e != cudaSuccess) return DBS_E_CUDA;
-    double mx = 0, sq = 0, rf = 0;
-    for (int b = 0; b < blocks; ++b) {
-        mx = std::max(mx, hb[3 * b]);
-        sq += hb[3 * b + 1];
-        rf += hb[3 * b + 2];
-    }
-    out[0] = mx;
-    out[1] = sq;
-    out[2] = rf;
+    out[0] = hb[0];
+    out[1] = hb[1];
+    out[2] = hb[2];
     out[3] = (double)S * (double)(S - 1) / 2.0;
     return DBS_OK;
 }

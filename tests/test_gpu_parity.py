@@ -213,10 +213,10 @@ def test_stroke_averaged_rates_and_steps(prec):
     np.testing.assert_allclose(np.linalg.norm(N, axis=1), 1.0, rtol=1e-14)
 
 
-def test_pair_distance_error_matches_oracle():
+@pytest.mark.parametrize("S", [2, 33, 300, 1000])
+def test_pair_distance_error_matches_oracle(S):
     import torch
-    rng = np.random.default_rng(12)
-    S = 300
+    rng = np.random.default_rng(12 + S)
     A0 = rng.uniform(-20, 20, (S, 3))
     A1 = A0 + rng.normal(scale=0.01, size=(S, 3))
     B0 = A0.copy()
