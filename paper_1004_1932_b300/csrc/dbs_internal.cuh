@@ -12,8 +12,8 @@ struct dbs_ensemble;
 struct dbs_suspension {
     dbs_ensemble *solo = nullptr;  // private one-member ensemble of the cluster path
     int path = 0;                  // DBS_PATH_GRID / DBS_PATH_CLUSTER / DBS_PATH_COOP
-    // cooperative dataflow path: tagged record and partial buffers, split, next tag
-    ulonglong2 *ll_rec = nullptr, *ll_part = nullptr;
+    // cooperative dataflow path: tagged record buffer, split, next tag
+    ulonglong2 *ll_rec = nullptr;
     int flow_I = 0, flow_q = 0, flow_C = 0, flow_creq = 0;
     unsigned flow_base = 1;
     dbs_params p{};

@@ -643,45 +643,68 @@ static const void *flow_fn(const dbs_suspension *h)
                                       : (const void *)flow_kernel<1, FLOW_W>;
 }
 
-// dynamic shared memory of flow_kernel: the chunk's records
-static size_t flow_smem(int q, int /*C*/) { return (size_t)q * FLOW_IB * sizeof(DbF32); }
+// dynamic shared memory of flow_kernel: the chunk's records and the owner's
+// table of chunk pairs
+static size_t flow_smem(int q, int C)
+{
+    return (size_t)q * FLOW_IB * sizeof(DbF32) + (size_t)C * 6 * FLOW_IB * sizeof(ulonglong2);
+}
+
+static cudaLaunchConfig_t flow_config(const dbs_suspension *h, int q, int C, cudaLaunchAttribute *attr)
+{
+    const int I = (int)((h->S + FLOW_IB - 1) / FLOW_IB);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(I * C);
+    cfg.blockDim = dim3(32 * FLOW_W);
+    cfg.dynamicSmemBytes = flow_smem(q, C);
+    cfg.stream = h->stream;
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = C;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    return cfg;
+}
 
 static void drop_flow(dbs_suspension *h)
 {
     cudaFree(h->ll_rec);
-    cudaFree(h->ll_part);
-    h->ll_rec = h->ll_part = nullptr;
+    h->ll_rec = nullptr;
 }
 
-// Split: the most j-chunks (up to the requested count) for which all I x C CTAs
-// are co-resident.
+// Split: the most j-chunks (up to the requested count, at most 16: one
+// thread-block cluster per i-block) for which all I clusters are co-resident.
 int coop_setup(dbs_suspension *h)
 {
     if (h->p.precision != DBS_FP32C || h->S > SMALL_S)
         return fail(h, DBS_E_ARG, "cooperative path needs FP32C and S <= %lld", (long long)SMALL_S);
-    int coop = 0;
+    int coop = 0, clusters = 0;
     CK(h, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device));
-    if (!coop) return fail(h, DBS_E_ARG, "device without cooperative launch");
+    CK(h, cudaDeviceGetAttribute(&clusters, cudaDevAttrClusterLaunch, h->device));
+    if (!coop || !clusters) return fail(h, DBS_E_ARG, "device without cooperative or cluster launch");
     const int I = (int)((h->S + FLOW_IB - 1) / FLOW_IB);
-    const int creq = h->flow_creq > 0 ? h->flow_creq : FLOW_MAX_C;
+    const int creq = std::min(h->flow_creq > 0 ? h->flow_creq : FLOW_MAX_C, 16);
     const void *k = flow_fn(h);
+    CK(h, cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     int q = std::max(1, (I + creq - 1) / creq), C = 0;
     for (;; ++q) {
         C = (I + q - 1) / q;
-        const size_t smem = flow_smem(q, C);
-        CK(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int occ = 0;
-        CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 32 * FLOW_W, smem));
-        if ((int64_t)occ * h->sms >= (int64_t)I * C) break;
+        CK(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)flow_smem(q, C)));
+        cudaLaunchAttribute attr[2];
+        cudaLaunchConfig_t cfg = flow_config(h, q, C, attr);
+        int ncl = 0;
+        CK(h, cudaOccupancyMaxActiveClusters(&ncl, k, &cfg));
+        if (ncl >= I) break;
         if (q >= I) return fail(h, DBS_E_ARG, "cooperative path: grid does not fit the device");
     }
     CK(h, cudaStreamSynchronize(h->stream));
     drop_flow(h);
     const size_t spad = (size_t)I * FLOW_IB;
     CK(h, cudaMalloc(&h->ll_rec, 2 * spad * 6 * sizeof(ulonglong2)));
-    CK(h, cudaMalloc(&h->ll_part, 2 * (size_t)C * spad * 6 * sizeof(ulonglong2)));
     CK(h, cudaMemsetAsync(h->ll_rec, 0, 2 * spad * 6 * sizeof(ulonglong2), h->stream));
-    CK(h, cudaMemsetAsync(h->ll_part, 0, 2 * (size_t)C * spad * 6 * sizeof(ulonglong2), h->stream));
     h->flow_I = I;
     h->flow_q = q;
     h->flow_C = C;
@@ -700,14 +723,11 @@ static int coop_step(dbs_suspension *h, int64_t n)
         if (h->flow_base > 0xffffffffu - (unsigned)(2 * K + 2)) {
             // tags are about to wrap: clear the buffers so that no old tag can match
             CK(h, cudaMemsetAsync(h->ll_rec, 0, 2 * spad * 6 * sizeof(ulonglong2), h->stream));
-            CK(h, cudaMemsetAsync(h->ll_part, 0, 2 * (size_t)h->flow_C * spad * 6 * sizeof(ulonglong2),
-                                  h->stream));
             h->flow_base = 1;
         }
         const EvalArgs A = base_args(h);
         FlowArgs P{};
         P.rec = h->ll_rec;
-        P.part = h->ll_part;
         P.pack = (DbF32 *)h->packA;
         P.n0 = h->n_host;
         P.I = h->flow_I;
@@ -716,16 +736,8 @@ static int coop_step(dbs_suspension *h, int64_t n)
         P.K = K;
         P.base = h->flow_base;
         P.timeout_ns = 1000000000ull;
-        cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3(h->flow_I * h->flow_C);
-        cfg.blockDim = dim3(32 * FLOW_W);
-        cfg.dynamicSmemBytes = flow_smem(h->flow_q, h->flow_C);
-        cfg.stream = h->stream;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeCooperative;
-        attr[0].val.cooperative = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
+        cudaLaunchAttribute attr[2];
+        const cudaLaunchConfig_t cfg = flow_config(h, h->flow_q, h->flow_C, attr);
         cudaError_t e = h->p.mobility == DBS_OSEEN ? cudaLaunchKernelEx(&cfg, flow_kernel<0, FLOW_W>, A, P)
                                                    : cudaLaunchKernelEx(&cfg, flow_kernel<1, FLOW_W>, A, P);
         if (e != cudaSuccess) return fail(h, DBS_E_CUDA, "cooperative launch: %s", cudaGetErrorString(e));

@@ -20,14 +20,20 @@
 //   1. every CTA polls the records of its chunk (and, off the owner, the
 //      positions of its targets) for tag e, into shared memory;
 //   2. sweeps them (W warps, one record range each) and folds the W sums;
-//   3. a non-owner stores its (sum, compensation) pairs with tag e;
-//      the owner polls the other C-1 chunks' pairs, folds all C in chunk order,
-//      runs the epilogue and publishes the next records with tag e + 1.
+//   3. the C CTAs of an i-block form one thread-block cluster: a non-owner
+//      writes its (sum, compensation) pairs, tagged the same way, straight
+//      into the owner's shared memory (DSMEM); the owner polls its own shared
+//      memory for the C-1 tags, folds all C pairs in chunk order, runs the
+//      epilogue and publishes the next records with tag e + 1.
 // Records and partials are double-buffered by the parity of e; the dependence
 // chain of the algorithm guarantees that a slot is rewritten only after every
-// reader of its previous contents is done.  Every wait is bounded (global
-// timer); a wait that runs out raises FLAG_TIMEOUT and the CTA returns, and the
-// others then run out too, so a launch always ends.
+// reader of its previous contents is done (the owner's table of pairs needs
+// no second buffer: a non-owner can only start the next sweep once the owner
+// has published records it folded from this table).  Every wait is bounded
+// (global timer); a wait that runs out raises FLAG_TIMEOUT, the CTA stops
+// working but keeps to the protocol (no early exit, so no CTA leaves while a
+// cluster peer may still write its shared memory), and the others then give up
+// too: a launch always ends.
 //
 // Precision (FP32C).  Pair sums as in eval_kernel (FP32 pair math, two-sum
 // across ranges).  Inside the launch the owner keeps positions (relative to
@@ -40,6 +46,8 @@
 // the velocity and the Heun average are FP32, as in the records.  Positions
 // and sums enter and leave the launch as FP64.
 #pragma once
+#include <cooperative_groups.h>
+
 #include "dbs_common.cuh"
 #include "eval_kernel.cuh"
 
@@ -49,7 +57,6 @@ constexpr int FLOW_IB = 32;  // dumbbells per i-block (one per lane)
 
 struct FlowArgs {
     ulonglong2 *rec;   // tagged records [2][Spad][6]: word w holds record floats 2w, 2w+1
-    ulonglong2 *part;  // tagged partials [2][C][Spad][6]: word k holds (sum, compensation) of component k
     DbF32 *pack;       // plain records of the final state (the grid path's input)
     int64_t n0;        // step number at launch
     int I, q, C, K;    // i-blocks, i-blocks per chunk, chunks, Heun steps
@@ -198,6 +205,28 @@ __device__ __forceinline__ void publish_record(ulonglong2 *dst, const float r[12
     for (int w = 0; w < 6; ++w) st_tagged(dst + w, r[2 * w], r[2 * w + 1], tag);
 }
 
+// A tagged pair into the shared memory of cluster rank `rank` (the local
+// address `local` mapped there).
+__device__ __forceinline__ void st_tagged_peer(const void *local, unsigned rank, float a, float b,
+                                               unsigned tag)
+{
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                 : "=r"(r) : "r"((unsigned)__cvta_generic_to_shared(local)), "r"(rank));
+    const unsigned long long hi = (unsigned long long)tag << 32;
+    asm volatile("st.relaxed.cluster.shared::cluster.v2.u64 [%0], {%1, %2};" ::"r"(r),
+                 "l"(hi | __float_as_uint(a)), "l"(hi | __float_as_uint(b))
+                 : "memory");
+}
+
+__device__ __forceinline__ ulonglong2 ld_tagged_local(const ulonglong2 *p)
+{
+    ulonglong2 v;
+    asm volatile("ld.relaxed.cluster.shared::cta.v2.u64 {%0, %1}, [%2];"
+                 : "=l"(v.x), "=l"(v.y) : "r"((unsigned)__cvta_generic_to_shared(p)) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ bool finite_f(float v) { return ((__float_as_uint(v) >> 23) & 0xffu) != 0xffu; }
 
 template <int W>
@@ -208,10 +237,13 @@ __global__ void __launch_bounds__(32 * W, FlowMinBlocks<W>::value)
 flow_kernel(const EvalArgs A, const FlowArgs P)
 {
     constexpr int NT = 32 * W;
-    extern __shared__ float4 flow_smem[];   // the chunk's records, q * 32 DbF32
+    namespace cg = cooperative_groups;
+    // dynamic: the chunk's records (q x 32 DbF32), then the owner's table of
+    // tagged chunk pairs [C][6][32]
+    extern __shared__ float4 flow_smem[];
     __shared__ FlowOwner own;
     __shared__ float red[W][6][FLOW_IB];
-    __shared__ float2 pairs[6][FLOW_IB];    // owner: own chunk's pair, then the folded total
+    __shared__ float2 pairs[6][FLOW_IB];    // owner: the C pairs folded
     __shared__ float tgt[FLOW_IB][6];       // non-owner: target positions (x0 x1 y0 y1 z0 z1)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -227,10 +259,14 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
     const int own_off = ib * FLOW_IB - db;           // owner: own i-block's place in the tile
     const int n_ib = min(FLOW_IB, S - ib * FLOW_IB);  // dumbbells of i-block ib
     DbF32 *tile = (DbF32 *)flow_smem;
+    ulonglong2 *ptab = (ulonglong2 *)(tile + P.q * FLOW_IB);
     const float k8 = A.inv8pimu_f;
     const float inv6 = (float)A.inv6pimua, k0f = (float)A.k0;
     const double cen[3] = {A.cx, A.cy, A.cz};
     const ds ell = ds_of(A.ell), dt = ds_of(A.dt);
+    cg::cluster_group cluster = cg::this_cluster();   // the C CTAs of i-block ib, rank c
+    for (int i = tid; i < P.C * 6 * FLOW_IB; i += NT) ptab[i] = make_ulonglong2(0ull, 0ull);  // no tag is 0
+    cluster.sync();   // every CTA of the cluster runs, and its table is clear, before a peer writes it
 
     // ---- owner: load the state, publish the records of evaluation 0 ----------
     if (owner && warp == 0 && active) {
@@ -272,6 +308,7 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
     const int n_words = n_chunk + (owner ? 0 : 3 * n_ib);
     const float2 c2 = make_float2(A.c2, A.c2), c3 = make_float2(A.c3, A.c3);
 
+    bool dead = false;   // a wait ran out: stop working, keep the protocol
     for (int ev = 0; ev < 2 * P.K; ++ev) {
         const unsigned tag = P.base + (unsigned)ev;
         const int par = ev & 1;
@@ -282,7 +319,7 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
         if (owner && warp == 0) trig = A.trig_df[(n + 1) & A.trig_mask];   // used by the epilogue
 
         // 1. poll the words of this evaluation, up to 8 per thread in flight
-        bool ok = true;
+        bool ok = !dead;
         for (int b0 = 0; b0 < n_words && ok; b0 += 8 * NT) {
             const ulonglong2 *pp[8];
             unsigned pend = 0;
@@ -320,12 +357,12 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
                 dst[1] = lo_float(v[j].y);
             }
         }
-        if (__syncthreads_or(!ok)) return;
+        dead = __syncthreads_or(!ok);
 
         // 2. sweep: warp `warp` takes records [j0, j1) of the chunk
         float2 qa[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         float2 qb[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        if (active) {
+        if (active && !dead) {
             float p[6];
             if (owner) {
                 const float4 a4 = tile[own_off + lane].a, b4 = tile[own_off + lane].b;
@@ -374,42 +411,57 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
         }
         __syncthreads();
 
-        // 3a. fold the W warp sums; a non-owner publishes its pair and is done
-        ulonglong2 *Pp = P.part + (size_t)par * P.C * Spad * 6;
-        for (int it = tid; it < 6 * FLOW_IB; it += NT) {
+        // 3a. fold the W warp sums into this chunk's pair; a non-owner writes
+        // it, tagged, into the owner's table through DSMEM and is done
+        float2 mine0 = {0.f, 0.f}, mine1 = {0.f, 0.f};   // owner: its own pairs (items tid, tid + NT)
+        for (int it = tid, j = 0; it < 6 * FLOW_IB; it += NT, ++j) {
             const int k = it >> 5, d = it & 31;
-            if (d >= n_ib) continue;
+            if (d >= n_ib || dead) continue;
             float sum = red[0][k][d], cmp = 0.f;
 #pragma unroll
             for (int w = 1; w < W; ++w) two_sum_acc(sum, cmp, red[w][k][d]);
-            if (owner) pairs[k][d] = make_float2(sum, cmp);
-            else st_tagged(Pp + ((size_t)c * Spad + ib * FLOW_IB + d) * 6 + k, sum, cmp, tag);
+            if (owner) (j == 0 ? mine0 : mine1) = make_float2(sum, cmp);
+            else st_tagged_peer(&ptab[(c * 6 + k) * FLOW_IB + d], (unsigned)c_own, sum, cmp, tag);
         }
         if (!owner) continue;
 
-        // 3b. owner: all C pairs in chunk order (the same thread wrote pairs[k][d])
-        for (int it = tid; it < 6 * FLOW_IB; it += NT) {
+        // 3b. owner: the other chunks' pairs, polled in its own shared memory
+        // (all loads of a round in flight together), folded in chunk order
+        ok = !dead;
+        for (int it = tid, j = 0; it < 6 * FLOW_IB && ok; it += NT, ++j) {
             const int k = it >> 5, d = it & 31;
             if (d >= n_ib) continue;
-            const int sd = ib * FLOW_IB + d;
             float sum = 0.f, cmp = 0.f;
             for (int cb = 0; cb < P.C && ok; cb += 8) {
-                const ulonglong2 *pp[8];
+                ulonglong2 v[8];
                 unsigned pend = 0;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int cc = cb + j;
-                    pp[j] = Pp + ((size_t)(cc < P.C ? cc : c) * Spad + sd) * 6 + k;
-                    if (cc < P.C && cc != c) pend |= 1u << j;
-                }
-                ulonglong2 v[8];
-                ok = wait_batch<8>(pp, pend, tag, v, A.flags, P.timeout_ns);
+                for (int q8 = 0; q8 < 8; ++q8)
+                    if (cb + q8 < P.C && cb + q8 != c) pend |= 1u << q8;
+                unsigned long long t0 = 0;   // read the global timer only once a wait begins
+                for (unsigned round = 0; pend; ++round) {
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int cc = cb + j;
+                    for (int q8 = 0; q8 < 8; ++q8)
+                        if ((pend >> q8) & 1u) v[q8] = ld_tagged_local(&ptab[((cb + q8) * 6 + k) * FLOW_IB + d]);
+#pragma unroll
+                    for (int q8 = 0; q8 < 8; ++q8)
+                        if (((pend >> q8) & 1u) && tagged(v[q8], tag)) pend &= ~(1u << q8);
+                    if (pend && round == 0) t0 = flow_ns();
+                    if (pend && (round & 63u) == 63u) {
+                        if ((*(volatile int *)A.flags & FLAG_TIMEOUT) || flow_ns() - t0 > P.timeout_ns) {
+                            atomicOr(A.flags, FLAG_TIMEOUT);
+                            ok = false;
+                            break;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q8 = 0; q8 < 8; ++q8) {
+                    const int cc = cb + q8;
                     if (cc < P.C) {
-                        const float ps = cc == c ? pairs[k][d].x : lo_float(v[j].x);
-                        const float pc = cc == c ? pairs[k][d].y : lo_float(v[j].y);
+                        const float2 mp = j == 0 ? mine0 : mine1;
+                        const float ps = cc == c ? mp.x : lo_float(v[q8].x);
+                        const float pc = cc == c ? mp.y : lo_float(v[q8].y);
                         if (cc == 0) {
                             sum = ps;
                             cmp = pc;
@@ -422,10 +474,10 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
             }
             pairs[k][d] = make_float2(sum, cmp);
         }
-        if (__syncthreads_or(!ok)) return;
+        dead = __syncthreads_or(!ok);
 
         // 3c. owner epilogue: one lane per dumbbell
-        if (warp == 0 && active) {
+        if (warp == 0 && active && !dead) {
             const int d = lane;
             float v[6];
 #pragma unroll
@@ -497,6 +549,7 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
         }
         __syncthreads();  // the tile's own records are complete before the next sweep
     }
+    cluster.sync();   // no CTA leaves while a peer may still write its shared memory
 
     // ---- owner: write the state back ------------------------------------------
     if (owner && warp == 0 && active) {
