@@ -53,6 +53,8 @@ def _args():
     p.add_argument("--no-large", action="store_true", help="skip the N=65536 kernel measurement")
     p.add_argument("--no-ensemble", action="store_true", help="skip the 256-system ensemble measurement")
     p.add_argument("--no-serving", action="store_true", help="skip the serving-trace measurement")
+    p.add_argument("--path", default="auto", choices=["auto", "grid", "cluster", "coop"],
+                   help="stepping path of the microscopic model (auto: the autotuner times all three)")
     p.add_argument("--cpu-sample-steps", type=int, default=400,
                    help="Heun steps of the oracle timed for the CPU baseline")
     return p.parse_args()
@@ -313,9 +315,12 @@ def run_ours(args):
     flush_buf = torch.empty(int(2 * l2_bytes) // 4, dtype=torch.float32, device=dev)
 
     from paper_1004_1932_b300 import autotune
-    probe = dbs.Suspension.from_inputs(s, precision="fp32c", stream=stream, device=local)
-    path_choice = autotune.choose_path(probe)
-    probe.close()
+    if args.path == "auto":
+        probe = dbs.Suspension.from_inputs(s, precision="fp32c", stream=stream, device=local)
+        path_choice = autotune.choose_path(probe)
+        probe.close()
+    else:
+        path_choice = {"path": args.path, "s_per_step": None}
 
     def make():
         h = dbs.Suspension.from_inputs(s, precision="fp32c", stream=stream, device=local)

@@ -18,6 +18,7 @@ enum : int {
     FLAG_OVERLAP = 1,    // r < 2a under RPY, or coincident spheres
     FLAG_NONFINITE = 2,  // a velocity or position is NaN/Inf
     FLAG_TIMEOUT = 4,    // a bounded wait ran out
+    FLAG_LAUNCH = 8,     // a kernel found itself launched in a shape it cannot run
 };
 
 enum Phase : int {

@@ -265,6 +265,14 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
     const double cen[3] = {A.cx, A.cy, A.cz};
     const ds ell = ds_of(A.ell), dt = ds_of(A.dt);
     cg::cluster_group cluster = cg::this_cluster();   // the C CTAs of i-block ib, rank c
+    // The exchange addresses cluster ranks 0..C-1: a launch without that shape
+    // (one the host did not make) must not touch a peer's shared memory.  The
+    // shape is the same for every CTA, so all of them leave here together.
+    if (cluster.num_blocks() != (unsigned)P.C || cluster.block_rank() != (unsigned)c ||
+        gridDim.x != (unsigned)(P.I * P.C)) {
+        if (tid == 0) atomicOr(A.flags, FLAG_LAUNCH);
+        return;
+    }
     for (int i = tid; i < P.C * 6 * FLOW_IB; i += NT) ptab[i] = make_ulonglong2(0ull, 0ull);  // no tag is 0
     cluster.sync();   // every CTA of the cluster runs, and its table is clear, before a peer writes it
 

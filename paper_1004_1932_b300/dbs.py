@@ -304,6 +304,12 @@ class StrokeAveraged:
             load().dbs_sa_destroy(self._h)
             self._h = None
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
     def __del__(self):
         try:
             self.close()
