@@ -48,31 +48,6 @@ constexpr int kPairUnroll = DBS_UNROLL;  // unroll of the fast j-loop
 
 namespace dbs {
 
-// Loads of data that other CTAs rewrite during a persistent (cooperative)
-// launch bypass L1, which is not coherent across SMs: COOP = true uses
-// ld.global.cg (L2) for them.
-template <bool COOP, typename T>
-__device__ __forceinline__ T ldm(const T *p)
-{
-    if constexpr (COOP) return __ldcg(p);
-    else return *p;
-}
-
-template <bool COOP>
-__device__ __forceinline__ DbF32 ld_rec(const DbF32 *p)
-{
-    if constexpr (COOP) {
-        const float4 *q = (const float4 *)p;
-        DbF32 r;
-        r.a = __ldcg(q);
-        r.b = __ldcg(q + 1);
-        r.c = __ldcg(q + 2);
-        return r;
-    } else {
-        return *p;
-    }
-}
-
 // ---- FP32 pair terms, two j-spheres per call ----------------------------------
 // Target sphere (px, py, pz), duplicated in both halves, against the two
 // spheres of one j-record (half .x = sphere 2r, half .y = sphere 2r + 1).
@@ -167,7 +142,7 @@ __device__ __forceinline__ void pair_f64(bool self, double px, double py, double
 }
 
 // ---- epilogue: self term, Heun, spring force, repack, period average --------
-template <typename Real, int PHASE, bool COOP = false>
+template <typename Real, int PHASE>
 __device__ __forceinline__ void epilogue(const EvalArgs &A, void *pack_out, int s, const double u[6],
                                          int64_t n)
 {
@@ -177,7 +152,7 @@ __device__ __forceinline__ void epilogue(const EvalArgs &A, void *pack_out, int 
         double v[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k)
-            v[k] = A.apply_self ? fma(ldm<COOP>(A.Fd + o + k), A.inv6pimua, u[k]) : u[k];
+            v[k] = A.apply_self ? fma(A.Fd[o + k], A.inv6pimua, u[k]) : u[k];
         if (!finite6(v)) atomicOr(A.flags, FLAG_NONFINITE);
 #pragma unroll
         for (int k = 0; k < 6; ++k) A.vout[o + k] = v[k];
@@ -185,12 +160,12 @@ __device__ __forceinline__ void epilogue(const EvalArgs &A, void *pack_out, int 
         double xq[6];  // point of the next evaluation
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            const double v = fma(ldm<COOP>(A.Fd + o + k), A.inv6pimua, u[k]);  // Eq. (3a) + pair sum
+            const double v = fma(A.Fd[o + k], A.inv6pimua, u[k]);  // Eq. (3a) + pair sum
             if (PHASE == PHASE_PREDICT) {
                 A.v0[o + k] = v;
-                xq[k] = fma(A.dt, v, ldm<COOP>(A.x + o + k));                    // x~ = x_n + dt v0
+                xq[k] = fma(A.dt, v, A.x[o + k]);                    // x~ = x_n + dt v0
             } else {
-                xq[k] = fma(0.5 * A.dt, ldm<COOP>(A.v0 + o + k) + v, ldm<COOP>(A.x + o + k));
+                xq[k] = fma(0.5 * A.dt, A.v0[o + k] + v, A.x[o + k]);
                 A.x[o + k] = xq[k];                                              // x_n + dt/2 (v0 + v1)
             }
         }
@@ -217,7 +192,7 @@ __device__ __forceinline__ void epilogue(const EvalArgs &A, void *pack_out, int 
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     const double Rt = 0.5 * (xq[k] + xq[3 + k]);
-                    double acc = ldm<COOP>(A.Racc + r + k);
+                    double acc = A.Racc[r + k];
                     if (end) {
                         acc += 0.5 * Rt;
                         if (kidx < A.avg_maxk) A.Rbar[kidx * 3 * A.S + r + k] = acc / (double)A.avg_m;
@@ -235,7 +210,7 @@ __device__ __forceinline__ void epilogue(const EvalArgs &A, void *pack_out, int 
 // ---- j-sweeps -------------------------------------------------------------------
 // Dumbbell-record range [db, de) through tiles of TDB records.  The CTA's own
 // dumbbells are [blk_lo, blk_hi); tiles that overlap them take the guarded path.
-template <int MOB, int BT, int TDB, bool COOP = false>
+template <int MOB, int BT, int TDB>
 __device__ __forceinline__ void sweep_f32(const DbF32 *__restrict__ pin, DbF32 *tile, int db,
                                           int de, int s, int blk_lo, int blk_hi, bool active,
                                           float c2s, float c3s, float s_[6], float c_[6],
@@ -244,7 +219,7 @@ __device__ __forceinline__ void sweep_f32(const DbF32 *__restrict__ pin, DbF32 *
     const int tid = threadIdx.x;
     float2 pax = make_float2(0.f, 0.f), pay = pax, paz = pax, pbx = pax, pby = pax, pbz = pax;
     if (active) {
-        const DbF32 me = ld_rec<COOP>(pin + s);
+        const DbF32 me = pin[s];
         pax = make_float2(me.a.x, me.a.x);
         pay = make_float2(me.a.z, me.a.z);
         paz = make_float2(me.b.x, me.b.x);
@@ -256,7 +231,7 @@ __device__ __forceinline__ void sweep_f32(const DbF32 *__restrict__ pin, DbF32 *
     for (int t0 = db; t0 < de; t0 += TDB) {
         const int len = min(TDB, de - t0);
         __syncthreads();
-        for (int k = tid; k < len; k += BT) tile[k] = ld_rec<COOP>(pin + t0 + k);
+        for (int k = tid; k < len; k += BT) tile[k] = pin[t0 + k];
         __syncthreads();
         const bool diag = (t0 < blk_hi) && (t0 + len > blk_lo);
         float2 qa[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
@@ -356,8 +331,8 @@ inline size_t eval_smem_bytes(int bt, int tdb, int chunks)
 }
 
 // All work units of one evaluation assigned to this CTA (the body of
-// eval_kernel, shared with the cooperative multi-step kernel).
-template <typename Real, int MOB, int PHASE, int BT, int TDB, bool COOP = false>
+// eval_kernel).
+template <typename Real, int MOB, int PHASE, int BT, int TDB>
 __device__ __forceinline__ void eval_units(const EvalArgs &A, const void *pack_in, void *pack_out,
                                            int64_t n, float4 *smem_dyn, int &s_last)
 {
@@ -380,7 +355,7 @@ __device__ __forceinline__ void eval_units(const EvalArgs &A, const void *pack_i
         const int blk_lo = ib_ * BT;
         const int blk_hi = min(blk_lo + BT, S);
 
-        if (!COOP && PHASE != PHASE_APPLY && active) {
+        if (PHASE != PHASE_APPLY && active) {
             // warm L1 with what the epilogue of this dumbbell will read, in case this
             // CTA turns out to be the last of its i-block
             const int64_t o = 6 * (int64_t)s;
@@ -395,7 +370,7 @@ __device__ __forceinline__ void eval_units(const EvalArgs &A, const void *pack_i
         if constexpr (sizeof(Real) == 4) {
             float s_[6] = {0, 0, 0, 0, 0, 0}, c_[6] = {0, 0, 0, 0, 0, 0};
             float r2min = 3.0e38f;
-            sweep_f32<MOB, BT, TDB, COOP>((const DbF32 *)pin, (DbF32 *)tile, db, de, s, blk_lo,
+            sweep_f32<MOB, BT, TDB>((const DbF32 *)pin, (DbF32 *)tile, db, de, s, blk_lo,
                                           blk_hi, active, A.c2, A.c3, s_, c_, r2min);
             if (MOB == 1 && active && r2min < A.overlap_r2) atomicOr(A.flags, FLAG_OVERLAP);
             if (C > 1) {
@@ -517,7 +492,7 @@ __device__ __forceinline__ void eval_units(const EvalArgs &A, const void *pack_i
                 }
             }
         }
-        if (do_epi && active) epilogue<Real, PHASE, COOP>(A, pack_out, s, u, n);
+        if (do_epi && active) epilogue<Real, PHASE>(A, pack_out, s, u, n);
     }
 }
 
