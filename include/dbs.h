@@ -115,6 +115,19 @@ DBS_API int dbs_set_stroke(dbs_suspension *h, const double *lambda, const double
 DBS_API int dbs_set_external_force(dbs_suspension *h, const double *F);
 
 /*
+ * Additive Brownian noise (closing remarks of Sec. IV: a constant matrix C
+ * in place of a Cholesky factor of the hydrodynamic tensor, adequate for
+ * dilute suspensions).  Every sphere is displaced by sigma z per Heun step,
+ * sigma = sqrt(2 kT dt / (6 pi mu a)), z ~ N(0, I_3) the same in predictor and
+ * corrector.  z is drawn from Philox4x32-10 (Salmon et al., SC'11) on the
+ * counter (n mod 2^32, n / 2^32, sphere index, 0) with `seed` as the key,
+ * then Box-Muller: z0, z1 = sqrt(-2 ln u0) (cos, sin)(2 pi u1),
+ * z2 = sqrt(-2 ln u2) cos(2 pi u3), u = (r + 1/2) 2^-32.  kT = 0 turns it
+ * off (the default).  kT must be finite and >= 0, else DBS_E_ARG.  All paths.
+ */
+DBS_API int dbs_set_noise(dbs_suspension *h, double kT, uint64_t seed);
+
+/*
  * Advance n >= 0 Heun steps (Sec. IV) on the device.  Asynchronous: returns
  * after enqueuing; geometry faults found on the device (DBS_E_OVERLAP,
  * DBS_E_NONFINITE) are reported by the next synchronising call

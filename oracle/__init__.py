@@ -129,8 +129,10 @@ def velocities(x, t, *, a, mu, k0, ell, omega, lam, phi, mobility=RPY, Fext=None
     return v
 
 
-def heun(x, n0, nsteps, *, a, mu, k0, ell, omega, dt, lam, phi, mobility=RPY, Fext=None):
-    """Advance positions ``x`` (copied) by ``nsteps`` Heun steps from step ``n0``."""
+def heun(x, n0, nsteps, *, a, mu, k0, ell, omega, dt, lam, phi, mobility=RPY, Fext=None,
+         kT=0.0, seed=0):
+    """Advance positions ``x`` (copied) by ``nsteps`` Heun steps from step ``n0``;
+    with kT > 0 the additive noise of ``orc_heun_noise`` (generator key ``seed``)."""
     x = np.array(x, dtype=np.float64, order="C", copy=True)
     lam, pl = _c(lam)
     phi, pp = _c(phi)
@@ -138,8 +140,28 @@ def heun(x, n0, nsteps, *, a, mu, k0, ell, omega, dt, lam, phi, mobility=RPY, Fe
     pe = None
     if Fext is not None:
         Fext, pe = _c(Fext)
-    lib().orc_heun(ctypes.byref(p), pl, pp, pe, x.ctypes.data_as(_dp), _i64(n0), _i64(nsteps))
+    if kT > 0:
+        lib().orc_heun_noise(ctypes.byref(p), pl, pp, pe, x.ctypes.data_as(_dp), _i64(n0),
+                             _i64(nsteps), ctypes.c_double(kT), ctypes.c_uint64(int(seed)))
+    else:
+        lib().orc_heun(ctypes.byref(p), pl, pp, pe, x.ctypes.data_as(_dp), _i64(n0), _i64(nsteps))
     return x
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 on a 4-word counter with a 2-word key; returns 4 uint32."""
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib().orc_philox4x32_10(c, k, o)
+    return np.array(list(o), dtype=np.uint32)
+
+
+def sphere_normals(seed, n, i):
+    """The three standard normals of sphere i at step n (additive noise)."""
+    z = np.empty(3)
+    lib().orc_sphere_normals(ctypes.c_uint64(int(seed)), _i64(n), _i64(i), z.ctypes.data_as(_dp))
+    return z
 
 
 def heun_period_avg(x, n0, m, nper, *, a, mu, k0, ell, omega, dt, lam, phi, mobility=RPY,

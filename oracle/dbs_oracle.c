@@ -27,6 +27,12 @@
  *   orc_sa_heun           Heun on (R, N) for Eqs. (9a)-(9b), N renormalised
  *                         after each step
  *   orc_pair_distance_change  |R^s - R^r|(k) - |R^s - R^r|(k0) for all pairs
+ *   orc_philox4x32_10     the counter-based generator Philox4x32-10 (Salmon et
+ *                         al., SC'11), written from its published definition
+ *   orc_sphere_normals    standard normals of one sphere at one step (Box-Muller)
+ *   orc_heun_noise        Heun with the additive noise of a constant matrix
+ *                         C = sqrt(2 kT / (6 pi mu a)) I, the dilute-limit
+ *                         approximation of the closing remarks of Sec. IV
  *
  * Conventions: spheres are 0-based; dumbbell s owns spheres 2s and 2s+1
  * (the paper's 2s-1 and 2s).  Positions, forces and velocities are [N][3]
@@ -43,6 +49,10 @@
  *  - K prefactor: the printed 15/64 of Eq. (9d) is used by default and is
  *    passed in as an argument; an exact stroke average of the shape-driven
  *    pair (a test of this oracle) confirms it.
+ *  - Additive noise (the paper names the constant matrix C but not its value
+ *    or the integrator): C = sqrt(2 kT / (6 pi mu a)) I, the square root of the
+ *    self part of Eq. (3) times 2 kT; each Heun step adds C dW with
+ *    dW = sqrt(dt) z, the same z in predictor and corrector.
  */
 #include <math.h>
 #include <stdint.h>
@@ -374,4 +384,88 @@ void orc_mobility_rows(int64_t N, const double *x, const double *F, double a, do
             if (be != al) add_pair_term(x + 3 * al, x + 3 * be, F + 3 * be, a, mu, mobility, acc);
         for (int i = 0; i < 3; ++i) v[3 * k + i] = acc[i];
     }
+}
+
+/*
+ * Philox4x32-10: ten rounds on the 128-bit counter c with the 64-bit key k,
+ *   c -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)),
+ * M0 = 0xD2511F53, M1 = 0xCD9E8D57, where hi/lo are the halves of the 64-bit
+ * product; before every round but the first the key advances by the Weyl
+ * constants W0 = 0x9E3779B9, W1 = 0xBB67AE85 (mod 2^32).
+ */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/*
+ * Standard normals of sphere i at step n: Philox4x32-10 on the counter
+ * (n mod 2^32, n / 2^32, i, 0) with key (seed mod 2^32, seed / 2^32), the four
+ * words r mapped to u = (r + 1/2) 2^-32 in (0, 1), then Box-Muller:
+ *   z0 = sqrt(-2 ln u0) cos(2 pi u1),  z1 = sqrt(-2 ln u0) sin(2 pi u1),
+ *   z2 = sqrt(-2 ln u2) cos(2 pi u3).
+ */
+void orc_sphere_normals(uint64_t seed, int64_t n, int64_t i, double z[3])
+{
+    uint64_t un = (uint64_t)n;
+    uint32_t ctr[4] = {(uint32_t)un, (uint32_t)(un >> 32), (uint32_t)i, 0u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t r[4];
+    orc_philox4x32_10(ctr, key, r);
+    double u[4];
+    for (int k = 0; k < 4; ++k) u[k] = ((double)r[k] + 0.5) / 4294967296.0;
+    double ra = sqrt(-2.0 * log(u[0])), rb = sqrt(-2.0 * log(u[2]));
+    z[0] = ra * cos(2.0 * ORC_PI * u[1]);
+    z[1] = ra * sin(2.0 * ORC_PI * u[1]);
+    z[2] = rb * cos(2.0 * ORC_PI * u[3]);
+}
+
+/*
+ * Heun with additive noise, nsteps steps from step counter n0:
+ *   w = sigma z_n (z_n: orc_sphere_normals per sphere), sigma = sqrt(2 kT dt / (6 pi mu a)),
+ *   x~ = x_n + dt v(x_n, t_n) + w,
+ *   x_{n+1} = x_n + dt/2 [v(x_n, t_n) + v(x~, t_{n+1})] + w.
+ * With kT = 0 this is orc_heun.
+ */
+void orc_heun_noise(const orc_params *p, const double *lambda, const double *phi, const double *Fext,
+                    double *x, int64_t n0, int64_t nsteps, double kT, uint64_t seed)
+{
+    int64_t N = 2 * p->S, N3 = 3 * N;
+    double sigma = sqrt(2.0 * kT * p->dt / (6.0 * ORC_PI * p->mu * p->a));
+    double *v0 = (double *)malloc(sizeof(double) * N3);
+    double *v1 = (double *)malloc(sizeof(double) * N3);
+    double *xt = (double *)malloc(sizeof(double) * N3);
+    double *w = (double *)malloc(sizeof(double) * N3);
+    for (int64_t n = n0; n < n0 + nsteps; ++n) {
+        double t0 = (double)n * p->dt;
+        double t1 = (double)(n + 1) * p->dt;
+        for (int64_t i = 0; i < N; ++i) {
+            double z[3];
+            orc_sphere_normals(seed, n, i, z);
+            for (int k = 0; k < 3; ++k) w[3 * i + k] = sigma * z[k];
+        }
+        orc_velocities(p, lambda, phi, Fext, x, t0, v0);
+        for (int64_t k = 0; k < N3; ++k) xt[k] = x[k] + p->dt * v0[k] + w[k];
+        orc_velocities(p, lambda, phi, Fext, xt, t1, v1);
+        for (int64_t k = 0; k < N3; ++k) x[k] = x[k] + 0.5 * p->dt * (v0[k] + v1[k]) + w[k];
+    }
+    free(v0);
+    free(v1);
+    free(xt);
+    free(w);
 }

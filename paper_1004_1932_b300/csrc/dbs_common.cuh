@@ -81,6 +81,8 @@ struct EvalArgs {
     float overlap_r2;     // (2a)^2 in FP32 (RPY overlap threshold)
     int chunks;           // C, number of j-chunks per i-block
     int apply_self;       // APPLY: 1 = add self term, 0 = interaction only
+    double noise_sigma;   // additive noise per step, sqrt(2 kT dt / (6 pi mu a)); 0 = off
+    unsigned long long noise_seed;  // key of the noise generator
 };
 
 // Knuth two-sum: s + c accumulates p with the rounding error of every addition kept in c.

@@ -195,6 +195,8 @@ static ResSys make_sys(const dbs_suspension *h, int G)
     P.avg_n0 = h->avg_n0;
     P.avg_m = h->avg_m;
     P.avg_maxk = h->avg_maxk;
+    P.noise_sigma = h->noise_sigma;
+    P.noise_seed = h->noise_seed;
     P.pack_args = A;
     return P;
 }

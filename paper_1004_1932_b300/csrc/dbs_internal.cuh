@@ -12,6 +12,8 @@ struct dbs_ensemble;
 struct dbs_suspension {
     dbs_ensemble *solo = nullptr;  // private one-member ensemble of the cluster path
     int path = 0;                  // DBS_PATH_GRID / DBS_PATH_CLUSTER / DBS_PATH_COOP
+    double noise_sigma = 0.0;      // additive noise per step (dbs_set_noise); 0 = off
+    unsigned long long noise_seed = 0;
     // cooperative dataflow path: tagged record buffer, split, next tag
     ulonglong2 *ll_rec = nullptr;
     int flow_I = 0, flow_q = 0, flow_C = 0, flow_creq = 0;

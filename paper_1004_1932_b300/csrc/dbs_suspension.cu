@@ -134,6 +134,8 @@ EvalArgs base_args(const dbs_suspension *h)
     A.overlap_r2 = (float)(4.0 * h->p.a * h->p.a);
     A.chunks = h->chunks;
     A.apply_self = 1;
+    A.noise_sigma = h->noise_sigma;
+    A.noise_seed = h->noise_seed;
     return A;
 }
 
@@ -602,6 +604,17 @@ int dbs_set_stroke(dbs_suspension *h, const double *lambda, const double *phase)
     int rc = repack(h);
     if (rc) return rc;
     CK(h, cudaStreamSynchronize(h->stream));
+    return DBS_OK;
+}
+
+int dbs_set_noise(dbs_suspension *h, double kT, uint64_t seed)
+{
+    GUARD(h);
+    if (!(kT >= 0.0) || !std::isfinite(kT)) return DBS_E_ARG;
+    CK(h, cudaStreamSynchronize(h->stream));
+    drop_graph(h);
+    h->noise_sigma = std::sqrt(2.0 * kT * h->p.dt / (6.0 * PI * h->p.mu * h->p.a));
+    h->noise_seed = seed;
     return DBS_OK;
 }
 

@@ -23,6 +23,7 @@
 // timing.
 #pragma once
 #include "dbs_common.cuh"
+#include "noise.cuh"
 
 // Tuning macros (defaults measured on B300 at N = 65536, see profiles/):
 //   DBS_RPY_W35           RPY coefficients as A = w + c2 w^3, B = (r.G)(w^3 + c3 w^5)
@@ -158,15 +159,23 @@ __device__ __forceinline__ void epilogue(const EvalArgs &A, void *pack_out, int 
         for (int k = 0; k < 6; ++k) A.vout[o + k] = v[k];
     } else {
         double xq[6];  // point of the next evaluation
+        double w[6] = {0, 0, 0, 0, 0, 0};  // additive noise of step n, the same in both phases
+        if (A.noise_sigma > 0.0) {
+            Real z[6];
+            sphere_normals(A.noise_seed, n, 2 * (int64_t)s, z);
+            sphere_normals(A.noise_seed, n, 2 * (int64_t)s + 1, z + 3);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) w[k] = A.noise_sigma * (double)z[k];
+        }
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             const double v = fma(A.Fd[o + k], A.inv6pimua, u[k]);  // Eq. (3a) + pair sum
             if (PHASE == PHASE_PREDICT) {
                 A.v0[o + k] = v;
-                xq[k] = fma(A.dt, v, A.x[o + k]);                    // x~ = x_n + dt v0
+                xq[k] = fma(A.dt, v, A.x[o + k]) + w[k];             // x~ = x_n + dt v0 (+ noise)
             } else {
-                xq[k] = fma(0.5 * A.dt, A.v0[o + k] + v, A.x[o + k]);
-                A.x[o + k] = xq[k];                                              // x_n + dt/2 (v0 + v1)
+                xq[k] = fma(0.5 * A.dt, A.v0[o + k] + v, A.x[o + k]) + w[k];
+                A.x[o + k] = xq[k];                                  // x_n + dt/2 (v0 + v1) (+ noise)
             }
         }
         if (!finite6(xq)) atomicOr(A.flags, FLAG_NONFINITE);

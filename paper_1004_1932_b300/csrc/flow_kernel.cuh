@@ -264,6 +264,8 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
     const float inv6 = (float)A.inv6pimua, k0f = (float)A.k0;
     const double cen[3] = {A.cx, A.cy, A.cz};
     const ds ell = ds_of(A.ell), dt = ds_of(A.dt);
+    const bool noise = A.noise_sigma > 0.0;
+    const ds sigma = ds_of(A.noise_sigma);
     cg::cluster_group cluster = cg::this_cluster();   // the C CTAs of i-block ib, rank c
     // The exchange addresses cluster ranks 0..C-1: a launch without that shape
     // (one the host did not make) must not touch a peer's shared memory.  The
@@ -491,6 +493,11 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
 #pragma unroll
             for (int k = 0; k < 6; ++k) v[k] = fmaf(own.F[k][d], inv6, pairs[k][d].x + pairs[k][d].y);  // Eq. (3a)
             ds xq[6];
+            float z[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // additive noise of step n
+            if (noise) {
+                sphere_normals(A.noise_seed, n, 2 * (int64_t)s, z);
+                sphere_normals(A.noise_seed, n, 2 * (int64_t)s + 1, z + 3);
+            }
             bool fin = true;
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
@@ -500,6 +507,9 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
                     xq[k] = ds_add(x, ds_mul_f(dt, v[k]));                          // x~ = x_n + dt v0
                 } else {
                     xq[k] = ds_add(x, ds_mul_f(dt, 0.5f * (own.v0[k][d] + v[k])));  // x_n + dt/2 (v0 + v1)
+                }
+                if (noise) xq[k] = ds_add(xq[k], ds_mul_f(sigma, z[k]));
+                if (corr) {
                     own.xh[k][d] = xq[k].h;
                     own.xl[k][d] = xq[k].l;
                 }

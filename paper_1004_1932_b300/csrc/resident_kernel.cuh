@@ -42,6 +42,8 @@ struct ResSys {
     int *flags;                 // fault flags
     double *Racc, *Rbar;        // stroke-average accumulator / snapshots
     int64_t avg_n0, avg_m, avg_maxk;
+    double noise_sigma;         // additive noise per step (0 = off)
+    unsigned long long noise_seed;
     EvalArgs pack_args;         // centre and scaling used by store_rec
 };
 
@@ -197,15 +199,23 @@ resident_kernel(const ResSys *__restrict__ systems, const int *__restrict__ csys
                 }
             }
             double xq[6];
+            double w[6] = {0, 0, 0, 0, 0, 0};   // additive noise of step n
+            if (P.noise_sigma > 0.0) {
+                float z[6];
+                sphere_normals(P.noise_seed, n, 2 * (int64_t)s, z);
+                sphere_normals(P.noise_seed, n, 2 * (int64_t)s + 1, z + 3);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) w[k] = P.noise_sigma * (double)z[k];
+            }
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
                 const double u = (double)S_[k] + (double)C_[k];
                 const double v = fma(F[k], P.inv6pimua, u);          // Eq. (3a) + pair sum
                 if ((e & 1) == 0) {
                     v0[k] = v;
-                    xq[k] = fma(P.dt, v, x[k]);                      // predictor
+                    xq[k] = fma(P.dt, v, x[k]) + w[k];               // predictor
                 } else {
-                    x[k] = fma(0.5 * P.dt, v0[k] + v, x[k]);         // corrector
+                    x[k] = fma(0.5 * P.dt, v0[k] + v, x[k]) + w[k];  // corrector
                     xq[k] = x[k];
                 }
             }

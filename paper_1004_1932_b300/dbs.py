@@ -172,6 +172,11 @@ class Suspension:
             F = _arr(F, (self.N, 3))
             self._check(load().dbs_set_external_force(self._h, _p(F)))
 
+    def set_noise(self, kT: float, seed: int = 0):
+        """Additive Brownian noise of temperature kT (0 = off), generator key ``seed``."""
+        self._check(load().dbs_set_noise(self._h, ctypes.c_double(float(kT)),
+                                         ctypes.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF)))
+
     def step(self, n: int = 1):
         self._check(load().dbs_step(self._h, _i64(int(n))))
 

@@ -30,6 +30,7 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--path", default="grid", choices=["grid", "cluster", "coop"])
     ap.add_argument("--breakdown", type=int, default=0, help="stroke periods of the hot path to time by part")
+    ap.add_argument("--kT", type=float, default=0.0, help="additive Brownian noise (dbs_set_noise), 0 = off")
     ap.add_argument("--cluster", type=int, default=0, help="cluster size of the cluster path (0 = auto)")
     a = ap.parse_args(argv)
     s = inputs.paper_scale(a.S, seed=a.seed, mobility=a.mobility)
@@ -38,6 +39,8 @@ def main(argv=None):
         print(json.dumps(breakdown(s, a)))
         return
     with dbs.Suspension.from_inputs(s, precision=a.precision, device=0) as h:
+        if a.kT > 0:
+            h.set_noise(a.kT, a.seed)
         if a.path == "grid":
             ms = h.step_timed(a.steps)
             print(json.dumps({"S": a.S, "N": N, "mobility": a.mobility, "precision": a.precision,
@@ -52,7 +55,7 @@ def main(argv=None):
             h.step(a.steps)
             h.sync()
             el = time.perf_counter() - t0
-            print(json.dumps({"S": a.S, "N": N, "mobility": a.mobility, "path": a.path,
+            print(json.dumps({"S": a.S, "N": N, "mobility": a.mobility, "path": a.path, "kT": a.kT,
                               "cluster": h.get_path()[1], "ms_per_step": 1e3 * el / a.steps}))
 
 
