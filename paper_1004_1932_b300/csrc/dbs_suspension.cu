@@ -615,6 +615,8 @@ int dbs_set_noise(dbs_suspension *h, double kT, uint64_t seed)
     drop_graph(h);
     h->noise_sigma = std::sqrt(2.0 * kT * h->p.dt / (6.0 * PI * h->p.mu * h->p.a));
     h->noise_seed = seed;
+    // the cooperative path runs a separate kernel instantiation with noise: re-derive its split
+    if (h->path == DBS_PATH_COOP) return coop_setup(h);
     return DBS_OK;
 }
 
@@ -653,8 +655,10 @@ constexpr int FLOW_MAX_STEPS = 1024;       // Heun steps per launch
 
 static const void *flow_fn(const dbs_suspension *h)
 {
-    return h->p.mobility == DBS_OSEEN ? (const void *)flow_kernel<0, FLOW_W>
-                                      : (const void *)flow_kernel<1, FLOW_W>;
+    const bool noise = h->noise_sigma > 0.0;
+    if (h->p.mobility == DBS_OSEEN)
+        return noise ? (const void *)flow_kernel<0, FLOW_W, true> : (const void *)flow_kernel<0, FLOW_W, false>;
+    return noise ? (const void *)flow_kernel<1, FLOW_W, true> : (const void *)flow_kernel<1, FLOW_W, false>;
 }
 
 // dynamic shared memory of flow_kernel: the chunk's records and the owner's
@@ -752,8 +756,8 @@ static int coop_step(dbs_suspension *h, int64_t n)
         P.timeout_ns = 1000000000ull;
         cudaLaunchAttribute attr[2];
         const cudaLaunchConfig_t cfg = flow_config(h, h->flow_q, h->flow_C, attr);
-        cudaError_t e = h->p.mobility == DBS_OSEEN ? cudaLaunchKernelEx(&cfg, flow_kernel<0, FLOW_W>, A, P)
-                                                   : cudaLaunchKernelEx(&cfg, flow_kernel<1, FLOW_W>, A, P);
+        void *args[] = {(void *)&A, (void *)&P};
+        cudaError_t e = cudaLaunchKernelExC(&cfg, flow_fn(h), args);
         if (e != cudaSuccess) return fail(h, DBS_E_CUDA, "cooperative launch: %s", cudaGetErrorString(e));
         h->flow_base += (unsigned)(2 * K + 1);
         h->n_host += K;

@@ -73,6 +73,7 @@ struct FlowOwner {
     float F[6][FLOW_IB];                    // force at the current evaluation point
     float v0[6][FLOW_IB];                   // Heun predictor velocity
     float fext[6][FLOW_IB];
+    float z[6][FLOW_IB];                    // additive-noise normals of the current step
 };
 
 __device__ __forceinline__ ulonglong2 ld_tagged(const ulonglong2 *p)
@@ -227,12 +228,26 @@ __device__ __forceinline__ ulonglong2 ld_tagged_local(const ulonglong2 *p)
     return v;
 }
 
+// The three normals of one sphere at step n into z[0], z[32], z[64] (kept out of
+// line: the kernel's per-evaluation code stays short).
+__device__ __noinline__ void draw_sphere_normals(unsigned long long seed, int64_t n, int64_t sphere,
+                                                 float *z)
+{
+    float w[3];
+    sphere_normals(seed, n, sphere, w);
+    z[0] = w[0];
+    z[FLOW_IB] = w[1];
+    z[2 * FLOW_IB] = w[2];
+}
+
 __device__ __forceinline__ bool finite_f(float v) { return ((__float_as_uint(v) >> 23) & 0xffu) != 0xffu; }
 
 template <int W>
 struct FlowMinBlocks { static constexpr int value = W <= 4 ? 4 : (W <= 8 ? 2 : 1); };
 
-template <int MOB, int W>
+// NOISE: additive Brownian noise on (a separate instantiation, so that the
+// deterministic kernel carries none of its code).
+template <int MOB, int W, bool NOISE>
 __global__ void __launch_bounds__(32 * W, FlowMinBlocks<W>::value)
 flow_kernel(const EvalArgs A, const FlowArgs P)
 {
@@ -254,6 +269,7 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
     const int Spad = P.I * FLOW_IB;
     const int s = ib * FLOW_IB + lane;
     const bool active = s < S;
+    const int g_ib0 = ib * FLOW_IB;   // first dumbbell of the i-block
     const int db = c * P.q * FLOW_IB;
     const int m = min(db + P.q * FLOW_IB, S) - db;    // records in the chunk
     const int own_off = ib * FLOW_IB - db;           // owner: own i-block's place in the tile
@@ -264,7 +280,6 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
     const float inv6 = (float)A.inv6pimua, k0f = (float)A.k0;
     const double cen[3] = {A.cx, A.cy, A.cz};
     const ds ell = ds_of(A.ell), dt = ds_of(A.dt);
-    const bool noise = A.noise_sigma > 0.0;
     const ds sigma = ds_of(A.noise_sigma);
     cg::cluster_group cluster = cg::this_cluster();   // the C CTAs of i-block ib, rank c
     // The exchange addresses cluster ranks 0..C-1: a launch without that shape
@@ -435,6 +450,17 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
         }
         if (!owner) continue;
 
+        // the normals of step n, drawn once (predictor) by the threads that have
+        // no pair to poll, for the 2 x 32 spheres of the i-block
+        if (NOISE && !corr) {
+            for (int q = tid - (NT >= 256 ? 6 * FLOW_IB : 0); q >= 0 && q < 2 * FLOW_IB;
+                 q += (NT >= 256 ? 2 * FLOW_IB : NT)) {
+                const int d = q >> 1, h = q & 1;
+                if (d < n_ib)
+                    draw_sphere_normals(A.noise_seed, n, 2 * ((int64_t)g_ib0 + d) + h, &own.z[3 * h][d]);
+            }
+        }
+
         // 3b. owner: the other chunks' pairs, polled in its own shared memory
         // (all loads of a round in flight together), folded in chunk order
         ok = !dead;
@@ -493,11 +519,6 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
 #pragma unroll
             for (int k = 0; k < 6; ++k) v[k] = fmaf(own.F[k][d], inv6, pairs[k][d].x + pairs[k][d].y);  // Eq. (3a)
             ds xq[6];
-            float z[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // additive noise of step n
-            if (noise) {
-                sphere_normals(A.noise_seed, n, 2 * (int64_t)s, z);
-                sphere_normals(A.noise_seed, n, 2 * (int64_t)s + 1, z + 3);
-            }
             bool fin = true;
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
@@ -508,7 +529,7 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
                 } else {
                     xq[k] = ds_add(x, ds_mul_f(dt, 0.5f * (own.v0[k][d] + v[k])));  // x_n + dt/2 (v0 + v1)
                 }
-                if (noise) xq[k] = ds_add(xq[k], ds_mul_f(sigma, z[k]));
+                if (NOISE) xq[k] = ds_add(xq[k], ds_mul_f(sigma, own.z[k][d]));   // + sigma z_n
                 if (corr) {
                     own.xh[k][d] = xq[k].h;
                     own.xl[k][d] = xq[k].l;
