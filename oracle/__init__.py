@@ -148,6 +148,31 @@ def heun(x, n0, nsteps, *, a, mu, k0, ell, omega, dt, lam, phi, mobility=RPY, Fe
     return x
 
 
+def sd_rates(x, t, niter, *, a, mu, k0=0.0, ell, omega, lam, phi, mobility=RPY):
+    """Shape-driven model (Appendix A.2): (dR/dt [S,3], dN/dt [S,3], f [S]) at
+    positions x and time t after ``niter`` constraint iterations."""
+    x, px = _c(x)
+    lam, pl = _c(lam)
+    phi, pp = _c(phi)
+    S = lam.shape[0]
+    p = _params(S, a, mu, k0, ell, omega, 0.0, mobility)
+    Rd, Nd, f = np.empty((S, 3)), np.empty((S, 3)), np.empty(S)
+    lib().orc_sd_rates(ctypes.byref(p), pl, pp, px, ctypes.c_double(t), ctypes.c_int(int(niter)),
+                       Rd.ctypes.data_as(_dp), Nd.ctypes.data_as(_dp), f.ctypes.data_as(_dp))
+    return Rd, Nd, f
+
+
+def sd_heun(x, n0, nsteps, niter, *, a, mu, k0=0.0, ell, omega, dt, lam, phi, mobility=RPY):
+    """Heun on (R, N) of the shape-driven model; returns the sphere positions."""
+    x = np.array(x, dtype=np.float64, order="C", copy=True)
+    lam, pl = _c(lam)
+    phi, pp = _c(phi)
+    p = _params(lam.shape[0], a, mu, k0, ell, omega, dt, mobility)
+    lib().orc_sd_heun(ctypes.byref(p), pl, pp, x.ctypes.data_as(_dp), _i64(n0), _i64(nsteps),
+                      ctypes.c_int(int(niter)))
+    return x
+
+
 def philox4x32_10(ctr, key):
     """Philox4x32-10 on a 4-word counter with a 2-word key; returns 4 uint32."""
     c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])

@@ -30,6 +30,10 @@
  *   orc_philox4x32_10     the counter-based generator Philox4x32-10 (Salmon et
  *                         al., SC'11), written from its published definition
  *   orc_sphere_normals    standard normals of one sphere at one step (Box-Muller)
+ *   orc_sd_rates          shape-driven dumbbells (Appendix A.2): constraint
+ *                         forces by the iteration f_(n), then dR/dt, dN/dt
+ *   orc_sd_heun           Heun on (R, N) of the shape-driven model, lengths
+ *                         prescribed by Eq. (4)
  *   orc_heun_noise        Heun with the additive noise of a constant matrix
  *                         C = sqrt(2 kT / (6 pi mu a)) I, the dilute-limit
  *                         approximation of the closing remarks of Sec. IV
@@ -468,4 +472,159 @@ void orc_heun_noise(const orc_params *p, const double *lambda, const double *phi
     free(v1);
     free(xt);
     free(w);
+}
+
+/*
+ * Shape-driven dumbbells (Appendix A.2, "Three-dimensional case"): the length
+ * of dumbbell s is prescribed, L^s(t) of Eq. (4), dL^s/dt = lambda^s omega
+ * cos(omega t + phi^s); sphere 2s is X^{s1}, sphere 2s+1 is X^{s2}, and
+ * N^s = (X^{s2} - X^{s1}) / |X^{s2} - X^{s1}|.  The internal forces
+ * F^{s1} = f^s N^s, F^{s2} = -f^s N^s (force- and torque-free) keep the shape:
+ *   dL^s/dt = N^s . (dX^{s2}/dt - dX^{s1}/dt).
+ * The paper solves this by the iteration
+ *   f^s_(n) = [dL^s/dt - sum_{r != s} b^{sr} f^r_(n-1)] / b^{ss},  f_(0) = 0,
+ *   b^{sr} = N^s . [h^{(s2)(r1)} + h^{(s1)(r2)} - h^{(s2)(r2)} - h^{(s1)(r1)}] . N^r,
+ * h^{(sb)(rc)} the mobility block of Eq. (3) between spheres (s,b) and (r,c)
+ * (self block (6 pi mu a)^{-1} I); here every b^{sr} is taken with the exact
+ * tensor, not its far-field expansion.  niter >= 1 iterations are made
+ * (niter = 1: the isolated dumbbell f_(1) = dL/dt / b^{ss}; niter = 2: the
+ * pair correction of the paper).  Then, with v = H F (Eq. (3)),
+ *   dR^s/dt = (v^{s1} + v^{s2}) / 2,
+ *   dN^s/dt = (I - N^s N^s^T) (v^{s2} - v^{s1}) / L^s.
+ * x must satisfy |X^{s2} - X^{s1}| = L^s(t).  f_out (optional) receives f.
+ */
+void orc_sd_rates(const orc_params *p, const double *lambda, const double *phi, const double *x,
+                  double t, int niter, double *Rdot, double *Ndot, double *f_out)
+{
+    int64_t S = p->S, N = 2 * S;
+    double self = 1.0 / (6.0 * ORC_PI * p->mu * p->a);
+    double *Nv = (double *)malloc(sizeof(double) * 3 * S);
+    double *L = (double *)malloc(sizeof(double) * S);
+    double *Ld = (double *)malloc(sizeof(double) * S);
+    double *bss = (double *)malloc(sizeof(double) * S);
+    double *f = (double *)calloc(S, sizeof(double));
+    double *fn = (double *)malloc(sizeof(double) * S);
+    for (int64_t s = 0; s < S; ++s) {
+        const double *x1 = x + 3 * (2 * s), *x2 = x + 3 * (2 * s + 1);
+        double e[3] = {x2[0] - x1[0], x2[1] - x1[1], x2[2] - x1[2]};
+        double d = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+        for (int k = 0; k < 3; ++k) Nv[3 * s + k] = e[k] / d;
+        L[s] = orc_rest_length(p->ell, lambda[s], p->omega, phi[s], t);
+        Ld[s] = lambda[s] * p->omega * cos(p->omega * t + phi[s]);
+        /* b^{ss}: h^{(s2)(s1)} and h^{(s1)(s2)} are the pair tensor at +-L N, h^{(sb)(sb)} the self block */
+        double u[3] = {0, 0, 0};
+        add_pair_term(x2, x1, Nv + 3 * s, p->a, p->mu, p->mobility, u);
+        double hc = u[0] * Nv[3 * s] + u[1] * Nv[3 * s + 1] + u[2] * Nv[3 * s + 2];
+        bss[s] = 2.0 * hc - 2.0 * self;
+    }
+    for (int it = 0; it < niter; ++it) {
+#pragma omp parallel for schedule(static)
+        for (int64_t s = 0; s < S; ++s) {
+            const double *xs1 = x + 3 * (2 * s), *xs2 = x + 3 * (2 * s + 1);
+            double sum = 0.0;
+            for (int64_t r = 0; r < S; ++r) {
+                if (r == s) continue;
+                const double *xr1 = x + 3 * (2 * r), *xr2 = x + 3 * (2 * r + 1);
+                double u[3] = {0, 0, 0}, w[3] = {0, 0, 0};
+                /* [h^{(s2)(r1)} - h^{(s2)(r2)}] N^r and [h^{(s1)(r2)} - h^{(s1)(r1)}] N^r */
+                add_pair_term(xs2, xr1, Nv + 3 * r, p->a, p->mu, p->mobility, u);
+                add_pair_term(xs1, xr2, Nv + 3 * r, p->a, p->mu, p->mobility, u);
+                add_pair_term(xs2, xr2, Nv + 3 * r, p->a, p->mu, p->mobility, w);
+                add_pair_term(xs1, xr1, Nv + 3 * r, p->a, p->mu, p->mobility, w);
+                double bsr = 0.0;
+                for (int k = 0; k < 3; ++k) bsr += Nv[3 * s + k] * (u[k] - w[k]);
+                sum += bsr * f[r];
+            }
+            fn[s] = (Ld[s] - sum) / bss[s];
+        }
+        for (int64_t s = 0; s < S; ++s) f[s] = fn[s];
+    }
+    double *F = (double *)malloc(sizeof(double) * 3 * N);
+    double *v = (double *)malloc(sizeof(double) * 3 * N);
+    for (int64_t s = 0; s < S; ++s)
+        for (int k = 0; k < 3; ++k) {
+            F[3 * (2 * s) + k] = f[s] * Nv[3 * s + k];
+            F[3 * (2 * s + 1) + k] = -f[s] * Nv[3 * s + k];
+        }
+    orc_mobility_apply(N, x, F, p->a, p->mu, p->mobility, v);
+    for (int64_t s = 0; s < S; ++s) {
+        const double *v1 = v + 3 * (2 * s), *v2 = v + 3 * (2 * s + 1);
+        double w[3], nw = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            Rdot[3 * s + k] = 0.5 * (v1[k] + v2[k]);
+            w[k] = (v2[k] - v1[k]) / L[s];
+            nw += Nv[3 * s + k] * w[k];
+        }
+        for (int k = 0; k < 3; ++k) Ndot[3 * s + k] = w[k] - Nv[3 * s + k] * nw;
+        if (f_out) f_out[s] = f[s];
+    }
+    free(Nv); free(L); free(Ld); free(bss); free(f); free(fn); free(F); free(v);
+}
+
+/*
+ * Heun on (R, N) of the shape-driven model, nsteps steps from step n0, x
+ * (spheres) updated in place:
+ *   R = (X^{s1} + X^{s2})/2, N = (X^{s2} - X^{s1})/|.|,
+ *   (R0', N0') = orc_sd_rates(x_n, t_n),  R~ = R + dt R0',  N~ = unit(N + dt N0'),
+ *   x~ = R~ -/+ N~ L(t_{n+1})/2,  (R1', N1') = orc_sd_rates(x~, t_{n+1}),
+ *   R_{n+1} = R + dt/2 (R0' + R1'),  N_{n+1} = unit(N + dt/2 (N0' + N1')),
+ *   x_{n+1} = R_{n+1} -/+ N_{n+1} L(t_{n+1})/2.
+ */
+static void sd_place(int64_t S, const double *R, const double *Nv, const orc_params *p,
+                     const double *lambda, const double *phi, double t, double *x)
+{
+    for (int64_t s = 0; s < S; ++s) {
+        double L = orc_rest_length(p->ell, lambda[s], p->omega, phi[s], t);
+        for (int k = 0; k < 3; ++k) {
+            x[3 * (2 * s) + k] = R[3 * s + k] - 0.5 * L * Nv[3 * s + k];
+            x[3 * (2 * s + 1) + k] = R[3 * s + k] + 0.5 * L * Nv[3 * s + k];
+        }
+    }
+}
+
+static void unit3(double *v)
+{
+    double n = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    for (int k = 0; k < 3; ++k) v[k] /= n;
+}
+
+void orc_sd_heun(const orc_params *p, const double *lambda, const double *phi, double *x, int64_t n0,
+                 int64_t nsteps, int niter)
+{
+    int64_t S = p->S;
+    double *R = (double *)malloc(sizeof(double) * 3 * S), *Nv = (double *)malloc(sizeof(double) * 3 * S);
+    double *R0 = (double *)malloc(sizeof(double) * 3 * S), *N0 = (double *)malloc(sizeof(double) * 3 * S);
+    double *R1 = (double *)malloc(sizeof(double) * 3 * S), *N1 = (double *)malloc(sizeof(double) * 3 * S);
+    double *Rt = (double *)malloc(sizeof(double) * 3 * S), *Nt = (double *)malloc(sizeof(double) * 3 * S);
+    double *xt = (double *)malloc(sizeof(double) * 6 * S);
+    for (int64_t n = n0; n < n0 + nsteps; ++n) {
+        double t0 = (double)n * p->dt, t1 = (double)(n + 1) * p->dt;
+        for (int64_t s = 0; s < S; ++s) {
+            const double *x1 = x + 3 * (2 * s), *x2 = x + 3 * (2 * s + 1);
+            for (int k = 0; k < 3; ++k) {
+                R[3 * s + k] = 0.5 * (x1[k] + x2[k]);
+                Nv[3 * s + k] = x2[k] - x1[k];
+            }
+            unit3(Nv + 3 * s);
+        }
+        orc_sd_rates(p, lambda, phi, x, t0, niter, R0, N0, NULL);
+        for (int64_t s = 0; s < S; ++s) {
+            for (int k = 0; k < 3; ++k) {
+                Rt[3 * s + k] = R[3 * s + k] + p->dt * R0[3 * s + k];
+                Nt[3 * s + k] = Nv[3 * s + k] + p->dt * N0[3 * s + k];
+            }
+            unit3(Nt + 3 * s);
+        }
+        sd_place(S, Rt, Nt, p, lambda, phi, t1, xt);
+        orc_sd_rates(p, lambda, phi, xt, t1, niter, R1, N1, NULL);
+        for (int64_t s = 0; s < S; ++s) {
+            for (int k = 0; k < 3; ++k) {
+                Rt[3 * s + k] = R[3 * s + k] + 0.5 * p->dt * (R0[3 * s + k] + R1[3 * s + k]);
+                Nt[3 * s + k] = Nv[3 * s + k] + 0.5 * p->dt * (N0[3 * s + k] + N1[3 * s + k]);
+            }
+            unit3(Nt + 3 * s);
+        }
+        sd_place(S, Rt, Nt, p, lambda, phi, t1, x);
+    }
+    free(R); free(Nv); free(R0); free(N0); free(R1); free(N1); free(Rt); free(Nt); free(xt);
 }
