@@ -128,6 +128,23 @@ DBS_API int dbs_set_external_force(dbs_suspension *h, const double *F);
 DBS_API int dbs_set_noise(dbs_suspension *h, double kT, uint64_t seed);
 
 /*
+ * Dynamics model.  DBS_DYN_SPRING (default): the spring of Eq. (4).
+ * DBS_DYN_SHAPE: shape-driven dumbbells (Appendix A.2), the infinitely stiff
+ * limit: lengths held at L(t) of Eq. (4) by axial internal forces
+ * F^{s1} = f^s N^s, F^{s2} = -f^s N^s from `iterations` >= 1 steps of the
+ * paper's iteration f_(n) (1: isolated dumbbells; 2: the pair correction;
+ * more approach the exact constraint solution), each one pair sum of Eq. (3)
+ * with the exact tensors; then Heun on centre R and axis N (N renormalised),
+ * spheres placed at R -/+ N L(t)/2.  Entering it projects the current
+ * positions onto L(t_n) (R and N kept).  Grid path only, no external force,
+ * no noise (DBS_E_STATE otherwise); k0 is ignored.  dbs_velocities then
+ * reports the shape-driven velocities.
+ */
+#define DBS_DYN_SPRING 0
+#define DBS_DYN_SHAPE 1
+DBS_API int dbs_set_dynamics(dbs_suspension *h, int32_t model, int32_t iterations);
+
+/*
  * Advance n >= 0 Heun steps (Sec. IV) on the device.  Asynchronous: returns
  * after enqueuing; geometry faults found on the device (DBS_E_OVERLAP,
  * DBS_E_NONFINITE) are reported by the next synchronising call

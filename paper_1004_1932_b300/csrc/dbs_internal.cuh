@@ -14,6 +14,9 @@ struct dbs_suspension {
     int path = 0;                  // DBS_PATH_GRID / DBS_PATH_CLUSTER / DBS_PATH_COOP
     double noise_sigma = 0.0;      // additive noise per step (dbs_set_noise); 0 = off
     unsigned long long noise_seed = 0;
+    int dyn = 0;                   // DBS_DYN_SPRING / DBS_DYN_SHAPE (dbs_set_dynamics)
+    int sd_iters = 1;              // shape-driven: constraint iterations per evaluation
+    double *sd_buf = nullptr;      // shape-driven work arrays (see dbs_shape.cu)
     // cooperative dataflow path: tagged record buffer, split, next tag
     ulonglong2 *ll_rec = nullptr;
     int flow_I = 0, flow_q = 0, flow_C = 0, flow_creq = 0;
@@ -50,12 +53,21 @@ struct dbs_suspension {
 
 // helpers defined in dbs_suspension.cu
 int fail(dbs_suspension *h, int status, const char *fmt, ...);
+int refuse(dbs_suspension *h, int status, const char *msg);  // no sticky status
 dbs::EvalArgs base_args(const dbs_suspension *h);
 int ensure_trig(dbs_suspension *h, int64_t k_hi, cudaStream_t st = nullptr);  // st: h->stream if null
 int check_flags(dbs_suspension *h);
 void drop_graph(dbs_suspension *h);
 // defined in dbs_suspension.cu (cooperative path)
 int coop_setup(dbs_suspension *h);
+// defined in dbs_suspension.cu: one APPLY evaluation of the pair-sum kernel with A
+void launch_apply(const dbs_suspension *h, const dbs::EvalArgs &A);
+// defined in dbs_shape.cu (shape-driven dynamics)
+int shape_step(dbs_suspension *h, int64_t n);
+int shape_reset(dbs_suspension *h);
+void shape_free(dbs_suspension *h);
+// defined in dbs_suspension.cu: spring records and forces of the current state into packA / Fd
+int spring_repack(dbs_suspension *h);
 // defined in dbs_ensemble.cu
 int solo_step(dbs_suspension *h, int64_t n);
 bool ens_member_ok(const dbs_suspension *h);               // can run on the cluster path

@@ -59,6 +59,13 @@ int fail(dbs_suspension *h, int status, const char *fmt, ...)
     return status;
 }
 
+// An argument or state error: the message is kept, the handle stays usable.
+int refuse(dbs_suspension *h, int status, const char *msg)
+{
+    snprintf(h->msg, sizeof(h->msg), "%s", msg);
+    return status;
+}
+
 #define CK(h, call)                                                                        \
     do {                                                                                   \
         cudaError_t e_ = (call);                                                           \
@@ -198,6 +205,8 @@ static void launch_eval(const dbs_suspension *h, int phase, const EvalArgs &A)
     else launch_eval_r<float>(h->p.mobility, phase, A, h->grid, h->bt, h->stream);
 }
 
+void launch_apply(const dbs_suspension *h, const EvalArgs &A) { launch_eval(h, PHASE_APPLY, A); }
+
 // Pack the current positions with spring (+ external) forces at t_n, or with a
 // given force Fgiven, into `out`; optionally record the FP64 force in Fd.
 template <typename Real>
@@ -268,6 +277,9 @@ static int reset_trig(dbs_suspension *h, int64_t n)
     h->trig_hi = n - 1;
     return ensure_trig(h, n + 1);
 }
+
+static int repack(dbs_suspension *h);
+int spring_repack(dbs_suspension *h) { return repack(h); }
 
 static int repack(dbs_suspension *h)
 {
@@ -421,6 +433,7 @@ static void free_all(dbs_suspension *h)
 {
     drop_graph(h);
     drop_flow(h);
+    shape_free(h);
     void *bufs[] = {h->x, h->v0, h->Fd, h->Fext, h->lam, h->sinphi, h->cosphi, h->vout, h->Ftmp, h->packA,
                     h->packB, h->packT, h->trig, h->trig_df, h->part, h->tickets, h->done, h->step, h->flags,
                     h->Racc, h->Rbar};
@@ -611,6 +624,7 @@ int dbs_set_noise(dbs_suspension *h, double kT, uint64_t seed)
 {
     GUARD(h);
     if (!(kT >= 0.0) || !std::isfinite(kT)) return DBS_E_ARG;
+    if (h->dyn == DBS_DYN_SHAPE && kT > 0.0) return refuse(h, DBS_E_STATE, "no noise with shape-driven dynamics");
     CK(h, cudaStreamSynchronize(h->stream));
     drop_graph(h);
     h->noise_sigma = std::sqrt(2.0 * kT * h->p.dt / (6.0 * PI * h->p.mu * h->p.a));
@@ -623,6 +637,7 @@ int dbs_set_noise(dbs_suspension *h, double kT, uint64_t seed)
 int dbs_set_external_force(dbs_suspension *h, const double *F)
 {
     GUARD(h);
+    if (h->dyn == DBS_DYN_SHAPE && F) return refuse(h, DBS_E_STATE, "no external force with shape-driven dynamics");
     if (F && !all_finite(F, 3 * h->N)) return DBS_E_ARG;
     drop_graph(h);
     if (!F) {
@@ -773,6 +788,7 @@ int dbs_step(dbs_suspension *h, int64_t n)
     GUARD(h);
     if (n < 0) return DBS_E_ARG;
     if (h->solo) return solo_step(h, n);
+    if (h->dyn == DBS_DYN_SHAPE) return shape_step(h, n);
     if (h->path == DBS_PATH_COOP) return coop_step(h, n);
     int64_t left = n, k = h->n_host;
     int rc;
@@ -912,6 +928,7 @@ int dbs_velocities_device(dbs_suspension *h, double *v_dev)
 int dbs_step_timed(dbs_suspension *h, int64_t n, double *mean_ms)
 {
     GUARD(h);
+    if (h->dyn == DBS_DYN_SHAPE) return refuse(h, DBS_E_STATE, "dbs_step_timed times the spring model");
     if (n < 1 || !mean_ms) return DBS_E_ARG;
     cudaEvent_t ev[4];
     for (auto &e : ev) CK(h, cudaEventCreate(&e));
@@ -985,7 +1002,7 @@ int dbs_set_state(dbs_suspension *h, const double *x, int64_t n)
     h->n_host = n;
     int rc = reset_trig(h, n);
     if (rc) return rc;
-    rc = repack(h);
+    rc = h->dyn == DBS_DYN_SHAPE ? shape_reset(h) : repack(h);
     if (rc) return rc;
     CK(h, cudaStreamSynchronize(h->stream));
     return DBS_OK;

@@ -172,6 +172,12 @@ class Suspension:
             F = _arr(F, (self.N, 3))
             self._check(load().dbs_set_external_force(self._h, _p(F)))
 
+    def set_dynamics(self, model: str = "spring", iterations: int = 2):
+        """"spring" (Eq. (4), default) or "shape": shape-driven dumbbells, lengths
+        held at L(t) by ``iterations`` steps of the constraint-force iteration."""
+        m = {"spring": 0, "shape": 1}[model]
+        self._check(load().dbs_set_dynamics(self._h, ctypes.c_int32(m), ctypes.c_int32(int(iterations))))
+
     def set_noise(self, kT: float, seed: int = 0):
         """Additive Brownian noise of temperature kT (0 = off), generator key ``seed``."""
         self._check(load().dbs_set_noise(self._h, ctypes.c_double(float(kT)),

@@ -31,6 +31,8 @@ def main(argv=None):
     ap.add_argument("--path", default="grid", choices=["grid", "cluster", "coop"])
     ap.add_argument("--breakdown", type=int, default=0, help="stroke periods of the hot path to time by part")
     ap.add_argument("--kT", type=float, default=0.0, help="additive Brownian noise (dbs_set_noise), 0 = off")
+    ap.add_argument("--shape", type=int, default=0,
+                    help="shape-driven dynamics with this many constraint iterations (0 = spring)")
     ap.add_argument("--cluster", type=int, default=0, help="cluster size of the cluster path (0 = auto)")
     a = ap.parse_args(argv)
     s = inputs.paper_scale(a.S, seed=a.seed, mobility=a.mobility)
@@ -41,6 +43,20 @@ def main(argv=None):
     with dbs.Suspension.from_inputs(s, precision=a.precision, device=0) as h:
         if a.kT > 0:
             h.set_noise(a.kT, a.seed)
+        if a.shape > 0:
+            import time
+            h.set_dynamics("shape", a.shape)
+            h.step(8)
+            h.sync()
+            t0 = time.perf_counter()
+            h.step(a.steps)
+            h.sync()
+            el = time.perf_counter() - t0
+            print(json.dumps({"S": a.S, "N": N, "mobility": a.mobility, "precision": a.precision,
+                              "dynamics": "shape", "iterations": a.shape,
+                              "ms_per_step": 1e3 * el / a.steps,
+                              "pair_sums_per_step": 2 * a.shape}))
+            return
         if a.path == "grid":
             ms = h.step_timed(a.steps)
             print(json.dumps({"S": a.S, "N": N, "mobility": a.mobility, "precision": a.precision,
