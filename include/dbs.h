@@ -193,7 +193,8 @@ DBS_API int dbs_step_timed(dbs_suspension *h, int64_t n, double *mean_ms);
  * Launch tuning of the pair-sum kernel (used by the autotuner): split the
  * j-range into `chunks` pieces (1 <= chunks <= max(1, S/8); 0 restores the
  * built-in choice).  Results change only in the rounding of the j-sum order.
- * dbs_get_launch reports dumbbells per CTA, chunks and grid size.
+ * dbs_get_launch reports dumbbells per CTA, chunks and grid size (on the
+ * cooperative path: dumbbells per i-block, j-chunks, CTAs).
  */
 DBS_API int dbs_set_chunks(dbs_suspension *h, int32_t chunks);
 DBS_API int dbs_get_launch(dbs_suspension *h, int32_t *bt, int32_t *chunks, int32_t *grid);

@@ -887,9 +887,10 @@ int dbs_set_chunks(dbs_suspension *h, int32_t chunks)
 int dbs_get_launch(dbs_suspension *h, int32_t *bt, int32_t *chunks, int32_t *grid)
 {
     GUARD(h);
-    if (bt) *bt = h->bt;
-    if (chunks) *chunks = h->chunks;
-    if (grid) *grid = h->grid;
+    const bool coop = h->path == DBS_PATH_COOP;
+    if (bt) *bt = coop ? FLOW_IB : h->bt;
+    if (chunks) *chunks = coop ? h->flow_C : h->chunks;
+    if (grid) *grid = coop ? h->flow_I * h->flow_C : h->grid;
     return DBS_OK;
 }
 
