@@ -478,6 +478,13 @@ DBS_API int dbs_mobility_apply_noalloc(int64_t S, const double *x_dev, const dou
  */
 DBS_API int dbs_test_wait_timeout(int32_t timeout_ms, int32_t *status);
 
+/*
+ * Diagnostic: set the evaluation tag the cooperative path uses next (>= 1), so
+ * that a test can run the tag wrap-around (the tagged buffers are cleared and
+ * the tags restart at 1 before they could wrap).  DBS_E_ARG for tag 0.
+ */
+DBS_API int dbs_test_set_flow_tag(dbs_suspension *h, uint32_t tag);
+
 /* Library version string. */
 DBS_API const char *dbs_version(void);
 

@@ -894,6 +894,14 @@ int dbs_get_launch(dbs_suspension *h, int32_t *bt, int32_t *chunks, int32_t *gri
     return DBS_OK;
 }
 
+int dbs_test_set_flow_tag(dbs_suspension *h, uint32_t tag)
+{
+    GUARD(h);
+    if (tag == 0) return DBS_E_ARG;
+    h->flow_base = tag;
+    return DBS_OK;
+}
+
 int dbs_test_wait_timeout(int32_t timeout_ms, int32_t *status)
 {
     if (!status || timeout_ms < 1 || timeout_ms > 10000) return DBS_E_ARG;

@@ -178,6 +178,10 @@ class Suspension:
         m = {"spring": 0, "shape": 1}[model]
         self._check(load().dbs_set_dynamics(self._h, ctypes.c_int32(m), ctypes.c_int32(int(iterations))))
 
+    def set_flow_tag(self, tag: int):
+        """Diagnostic: the next evaluation tag of the cooperative path (wrap-around tests)."""
+        self._check(load().dbs_test_set_flow_tag(self._h, ctypes.c_uint32(int(tag))))
+
     def set_noise(self, kT: float, seed: int = 0):
         """Additive Brownian noise of temperature kT (0 = off), generator key ``seed``."""
         self._check(load().dbs_set_noise(self._h, ctypes.c_double(float(kT)),

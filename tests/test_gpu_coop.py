@@ -106,6 +106,23 @@ def test_coop_period_averages_match_oracle():
     assert np.abs(got - ref).max() <= 1e-4 * s.ell
 
 
+@pytest.mark.parametrize("tag", [0xFFFFFFFF - 300, 0xFFFFFFFF - 3000])
+def test_coop_tag_wraparound(tag):
+    # the first launch (first case) or the second (second case) would run past
+    # 2^32 tags: the buffers are cleared and the tags restart, results unchanged
+    s = inputs.paper_scale(64, seed=12)
+    with _handle(s) as h:
+        h.set_path("coop")
+        h.step(2000)
+        ref = h.positions()
+    with _handle(s) as h:
+        h.set_path("coop")
+        h.set_flow_tag(tag)
+        h.step(2000)
+        x = h.positions()
+    assert np.array_equal(x, ref)
+
+
 def test_coop_refuses_what_it_cannot_hold():
     s = inputs.make_suspension(2049, seed=2, density=0.002)
     with _handle(s) as h:
