@@ -104,6 +104,7 @@ static int efail(dbs_ensemble *e, int st, const char *fmt, ...)
 static bool member_ok(const dbs_suspension *h)
 {
     return h && h->status == DBS_OK && h->p.precision == DBS_FP32C && h->S >= 1 &&
+           h->dyn == DBS_DYN_SPRING &&
            resident_smem_bytes((int)h->S, min_cluster(h->S, nt_for(h->S)), nt_for(h->S)) <= SMEM_LIMIT;
 }
 

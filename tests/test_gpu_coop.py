@@ -29,9 +29,10 @@ def _handle(s, precision="fp32c"):
                           mobility=s.mobility, precision=precision, lam=s.lam, phi=s.phi)
 
 
-@pytest.mark.parametrize("S,mob", [(16, "oseen"), (16, "rpy"), (300, "rpy"), (513, "oseen")])
+@pytest.mark.parametrize("S,mob", [(1, "rpy"), (2, "oseen"), (16, "oseen"), (16, "rpy"), (31, "rpy"),
+                                   (33, "oseen"), (300, "rpy"), (513, "oseen")])
 def test_coop_path_follows_oracle(S, mob):
-    s = inputs.make_suspension(S, seed=S + 11, density=0.002, mobility=mob) if S > 16 \
+    s = inputs.make_suspension(S, seed=S + 11, density=0.002, mobility=mob) if S > 40 \
         else inputs.make_suspension(S, seed=1, side=8.0, mobility=mob)
     nsteps = 1000
     ref = oracle.heun(s.x0, 0, nsteps, dt=s.dt, mobility=MOB[mob], **s.phys())

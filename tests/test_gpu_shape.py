@@ -111,6 +111,10 @@ def test_shape_mode_restrictions_and_return_to_spring():
                 call()
             assert ei.value.status == dbs.E_STATE
     with _handle(s) as h:
+        h.set_dynamics("shape", 2)
+        with pytest.raises(dbs.DbsError):
+            dbs.Ensemble([h])            # ensembles run the spring model only
+    with _handle(s) as h:
         with pytest.raises(dbs.DbsError):
             h.set_dynamics("shape", 0)
         h.set_dynamics("shape", 2)
