@@ -36,15 +36,15 @@
 // too: a launch always ends.
 //
 // Precision (FP32C).  Pair sums as in eval_kernel (FP32 pair math, two-sum
-// across ranges).  Inside the launch the owner keeps positions (relative to
-// the suspension's centre) and the stroke-average sums as unevaluated FP32
-// pairs hi + lo (double-single, 48-bit significand; Dekker's exact two-sum and
-// FMA two-product), because an FP64 instruction costs a whole warp-issue slot
-// of 64 cycles on this part while FP32 pairs run at full rate.  The rest length
-// L and the squared length d^2 are formed in the same arithmetic, so the small
-// stretch d - L = (d^2 - L^2)/(d + L) keeps FP32 relative accuracy; the force,
-// the velocity and the Heun average are FP32, as in the records.  Positions
-// and sums enter and leave the launch as FP64.
+// across ranges).  Positions (relative to the suspension's centre) and the
+// stroke-average sums are FP64 and the Heun update is FP64.  An FP64
+// instruction holds its sub-partition for 64 cycles on this part, so the
+// owner spreads that work over three warps, one per axis, each on its own
+// sub-partition.  The rest length L and d^2 = |x_b - x_a|^2 (from the FP64
+// difference) are formed as unevaluated FP32 pairs hi + lo (double-single:
+// Dekker's two-sum and the FMA two-product), so the small stretch
+// d - L = (d^2 - L^2)/(d + L) keeps FP32 relative accuracy; the force and the
+// velocity are FP32, as in the records.
 #pragma once
 #include <cooperative_groups.h>
 
@@ -67,13 +67,17 @@ struct FlowArgs {
 // Owner state of one i-block, in shared memory (component-major: lane d reads
 // column d).  Positions are relative to the centre; all pairs are double-single.
 struct FlowOwner {
-    float xh[6][FLOW_IB], xl[6][FLOW_IB];   // spheres 2s (0..2) and 2s+1 (3..5)
-    float Rh[3][FLOW_IB], Rl[3][FLOW_IB];   // stroke-average sums (trapezoid rule)
+    double x[6][FLOW_IB];                   // x - centre, spheres 2s (0..2) and 2s+1 (3..5)
+    double R[3][FLOW_IB];                   // stroke-average sums (trapezoid rule)
     float lamh[FLOW_IB], laml[FLOW_IB], sph[FLOW_IB], spl[FLOW_IB], cph[FLOW_IB], cpl[FLOW_IB];
     float F[6][FLOW_IB];                    // force at the current evaluation point
     float v0[6][FLOW_IB];                   // Heun predictor velocity
     float fext[6][FLOW_IB];
     float z[6][FLOW_IB];                    // additive-noise normals of the current step
+    float2 e[3][FLOW_IB];                   // x_b - x_a per axis (double-single)
+    float2 ee[3][FLOW_IB];                  // its square (double-single)
+    float2 L[FLOW_IB], L2[FLOW_IB];         // rest length at t_{n+1} and its square
+    float f[FLOW_IB];                       // k0 (d - L) / d
 };
 
 __device__ __forceinline__ ulonglong2 ld_tagged(const ulonglong2 *p)
@@ -279,8 +283,7 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
     const float k8 = A.inv8pimu_f;
     const float inv6 = (float)A.inv6pimua, k0f = (float)A.k0;
     const double cen[3] = {A.cx, A.cy, A.cz};
-    const ds ell = ds_of(A.ell), dt = ds_of(A.dt);
-    const ds sigma = ds_of(A.noise_sigma);
+    const ds ell = ds_of(A.ell);
     cg::cluster_group cluster = cg::this_cluster();   // the C CTAs of i-block ib, rank c
     // The exchange addresses cluster ranks 0..C-1: a launch without that shape
     // (one the host did not make) must not touch a peer's shared memory.  The
@@ -299,9 +302,7 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
         float r[12];
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            const ds x = ds_of(A.x[o + k] - cen[k % 3]);
-            own.xh[k][lane] = x.h;
-            own.xl[k][lane] = x.l;
+            own.x[k][lane] = A.x[o + k] - cen[k % 3];
             own.F[k][lane] = (float)A.Fd[o + k];
             own.fext[k][lane] = A.Fext ? (float)A.Fext[o + k] : 0.f;
         }
@@ -313,14 +314,10 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
         own.cph[lane] = t.h; own.cpl[lane] = t.l;
         if (A.avg_m > 0) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                t = ds_of(A.Racc[3 * (int64_t)s + k]);
-                own.Rh[k][lane] = t.h;
-                own.Rl[k][lane] = t.l;
-            }
+            for (int k = 0; k < 3; ++k) own.R[k][lane] = A.Racc[3 * (int64_t)s + k];
         }
-        r[0] = own.xh[0][lane]; r[1] = own.xh[3][lane]; r[2] = own.xh[1][lane];
-        r[3] = own.xh[4][lane]; r[4] = own.xh[2][lane]; r[5] = own.xh[5][lane];
+        r[0] = (float)own.x[0][lane]; r[1] = (float)own.x[3][lane]; r[2] = (float)own.x[1][lane];
+        r[3] = (float)own.x[4][lane]; r[4] = (float)own.x[2][lane]; r[5] = (float)own.x[5][lane];
         r[6] = own.F[0][lane] * k8; r[7] = own.F[3][lane] * k8; r[8] = own.F[1][lane] * k8;
         r[9] = own.F[4][lane] * k8; r[10] = own.F[2][lane] * k8; r[11] = own.F[5][lane] * k8;
         put_record(tile + own_off + lane, r);
@@ -341,7 +338,7 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
         const int64_t n = P.n0 + (ev >> 1);
         const ulonglong2 *R = P.rec + (size_t)par * Spad * 6;
         float4 trig = make_float4(0.f, 0.f, 1.f, 0.f);
-        if (owner && warp == 0) trig = A.trig_df[(n + 1) & A.trig_mask];   // used by the epilogue
+        if (owner && warp == 3) trig = A.trig_df[(n + 1) & A.trig_mask];   // rest length, epilogue warp 3
 
         // 1. poll the words of this evaluation, up to 8 per thread in flight
         bool ok = !dead;
@@ -512,78 +509,96 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
         }
         dead = __syncthreads_or(!ok);
 
-        // 3c. owner epilogue: one lane per dumbbell
-        if (warp == 0 && active && !dead) {
-            const int d = lane;
-            float v[6];
-#pragma unroll
-            for (int k = 0; k < 6; ++k) v[k] = fmaf(own.F[k][d], inv6, pairs[k][d].x + pairs[k][d].y);  // Eq. (3a)
-            ds xq[6];
-            bool fin = true;
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                const ds x = {own.xh[k][d], own.xl[k][d]};
-                if (!corr) {
-                    own.v0[k][d] = v[k];
-                    xq[k] = ds_add(x, ds_mul_f(dt, v[k]));                          // x~ = x_n + dt v0
-                } else {
-                    xq[k] = ds_add(x, ds_mul_f(dt, 0.5f * (own.v0[k][d] + v[k])));  // x_n + dt/2 (v0 + v1)
-                }
-                if (NOISE) xq[k] = ds_add(xq[k], ds_mul_f(sigma, own.z[k][d]));   // + sigma z_n
-                if (corr) {
-                    own.xh[k][d] = xq[k].h;
-                    own.xl[k][d] = xq[k].l;
-                }
-                fin &= finite_f(xq[k].h);
+        // 3c. owner epilogue.  Warps 0-2 take axis a = warp of the i-block's
+        // dumbbells (lane d): self term of Eq. (3a), FP64 Heun update of both
+        // spheres (Sec. IV), the axis component of e = x_b - x_a; warp 3 the rest
+        // length L(t_{n+1}) of Eq. (4).  Then warp 0 the spring magnitude, and
+        // warps 0-2 the forces, records and their publication.
+        const int a = warp, d = lane;
+        const bool eax = warp < 3 && active && !dead;
+        float pa = 0.f, pb = 0.f;   // record positions along a (FP32, centre-relative)
+        float eh = 0.f;
+        if (eax) {
+            const float va = fmaf(own.F[a][d], inv6, pairs[a][d].x + pairs[a][d].y);           // Eq. (3a)
+            const float vb = fmaf(own.F[a + 3][d], inv6, pairs[a + 3][d].x + pairs[a + 3][d].y);
+            double xa = own.x[a][d], xb = own.x[a + 3][d];
+            if (!corr) {
+                own.v0[a][d] = va;
+                own.v0[a + 3][d] = vb;
+                xa = fma(A.dt, (double)va, xa);                                   // x~ = x_n + dt v0
+                xb = fma(A.dt, (double)vb, xb);
+            } else {
+                xa = fma(0.5 * A.dt, (double)(own.v0[a][d] + va), xa);           // x_n + dt/2 (v0 + v1)
+                xb = fma(0.5 * A.dt, (double)(own.v0[a + 3][d] + vb), xb);
             }
-            if (!fin) atomicOr(A.flags, FLAG_NONFINITE);
-            // Eq. (4) at t_{n+1}: F_a = k0 (d - L) e/d with d - L = (d^2 - L^2)/(d + L)
-            const ds sarg = ds_add(ds_mul({trig.x, trig.y}, {own.cph[d], own.cpl[d]}),
-                                   ds_mul({trig.z, trig.w}, {own.sph[d], own.spl[d]}));
-            const ds L = ds_add(ell, ds_mul({own.lamh[d], own.laml[d]}, sarg));
-            const ds ex = ds_add(xq[3], ds_neg(xq[0]));
-            const ds ey = ds_add(xq[4], ds_neg(xq[1]));
-            const ds ez = ds_add(xq[5], ds_neg(xq[2]));
-            const ds dd = ds_add(ds_add(ds_mul(ex, ex), ds_mul(ey, ey)), ds_mul(ez, ez));
-            const ds st2 = ds_add(dd, ds_neg(ds_mul(L, L)));
-            const float rd = rsqrtf(dd.h);
-            const float f = k0f * __fdividef((st2.h + st2.l) * rd, dd.h * rd + L.h);
-            const float fe[3] = {f * ex.h, f * ey.h, f * ez.h};
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                own.F[k][d] = fe[k] + own.fext[k][d];
-                own.F[3 + k][d] = -fe[k] + own.fext[3 + k][d];
+            if (NOISE) {
+                xa = fma(A.noise_sigma, (double)own.z[a][d], xa);
+                xb = fma(A.noise_sigma, (double)own.z[a + 3][d], xb);
             }
-            float r[12];
-            r[0] = xq[0].h; r[1] = xq[3].h; r[2] = xq[1].h; r[3] = xq[4].h; r[4] = xq[2].h; r[5] = xq[5].h;
-            r[6] = own.F[0][d] * k8; r[7] = own.F[3][d] * k8; r[8] = own.F[1][d] * k8;
-            r[9] = own.F[4][d] * k8; r[10] = own.F[2][d] * k8; r[11] = own.F[5][d] * k8;
-            put_record(tile + own_off + d, r);
-            if (ev + 1 < 2 * P.K) publish_record(P.rec + ((size_t)(par ^ 1) * Spad + s) * 6, r, tag + 1);
-            else put_record(P.pack + s, r);   // the final state's records, for the grid path
-            // stroke average of the geometric centre (corrector), trapezoid rule
+            if (corr) {
+                own.x[a][d] = xa;
+                own.x[a + 3][d] = xb;
+            }
+            if (!(finite1(xa) && finite1(xb))) atomicOr(A.flags, FLAG_NONFINITE);
+            const ds e = ds_of(xb - xa);
+            const ds e2 = ds_mul(e, e);
+            own.e[a][d] = make_float2(e.h, e.l);
+            own.ee[a][d] = make_float2(e2.h, e2.l);
+            eh = e.h;
+            pa = (float)xa;
+            pb = (float)xb;
+            // stroke average of the geometric centre along a (corrector), trapezoid rule
             if (corr && A.avg_m > 0) {
                 const int64_t k_local = n + 1 - A.avg_n0;
                 if (k_local > 0) {
-                    const bool end = (k_local % A.avg_m) == 0;
-                    const int64_t kidx = k_local / A.avg_m - 1;
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        ds Rt = ds_add(xq[k], xq[3 + k]);
-                        Rt = ds_add({0.5f * Rt.h, 0.5f * Rt.l}, ds_of(cen[k]));
-                        ds acc = {own.Rh[k][d], own.Rl[k][d]};
-                        if (end) {
-                            acc = ds_add(acc, {0.5f * Rt.h, 0.5f * Rt.l});
-                            if (kidx < A.avg_maxk)
-                                A.Rbar[kidx * 3 * A.S + 3 * (int64_t)s + k] = ds_to_double(acc) / (double)A.avg_m;
-                            acc = {0.5f * Rt.h, 0.5f * Rt.l};
-                        } else {
-                            acc = ds_add(acc, Rt);
-                        }
-                        own.Rh[k][d] = acc.h;
-                        own.Rl[k][d] = acc.l;
+                    const double Rt = 0.5 * (xa + xb) + (a == 0 ? A.cx : (a == 1 ? A.cy : A.cz));
+                    double acc = own.R[a][d];
+                    if ((k_local % A.avg_m) == 0) {
+                        acc += 0.5 * Rt;
+                        const int64_t kidx = k_local / A.avg_m - 1;
+                        if (kidx < A.avg_maxk) A.Rbar[kidx * 3 * A.S + 3 * (int64_t)s + a] = acc / (double)A.avg_m;
+                        acc = 0.5 * Rt;
+                    } else {
+                        acc += Rt;
                     }
+                    own.R[a][d] = acc;
                 }
+            }
+        } else if (warp == 3 && active && !dead) {
+            const ds sarg = ds_add(ds_mul({trig.x, trig.y}, {own.cph[d], own.cpl[d]}),
+                                   ds_mul({trig.z, trig.w}, {own.sph[d], own.spl[d]}));
+            const ds L = ds_add(ell, ds_mul({own.lamh[d], own.laml[d]}, sarg));
+            const ds L2 = ds_mul(L, L);
+            own.L[d] = make_float2(L.h, L.l);
+            own.L2[d] = make_float2(L2.h, L2.l);
+        }
+        __syncthreads();
+        if (warp == 0 && active && !dead) {
+            // Eq. (4): F_a = k0 (d - L) e/d with d - L = (d^2 - L^2)/(d + L)
+            const ds dd = ds_add(ds_add({own.ee[0][d].x, own.ee[0][d].y}, {own.ee[1][d].x, own.ee[1][d].y}),
+                                 {own.ee[2][d].x, own.ee[2][d].y});
+            const ds st2 = ds_add(dd, ds_neg({own.L2[d].x, own.L2[d].y}));
+            const float rd = rsqrtf(dd.h);
+            own.f[d] = k0f * __fdividef((st2.h + st2.l) * rd, dd.h * rd + own.L[d].x);
+        }
+        __syncthreads();
+        if (eax) {
+            const float f = own.f[d];
+            const float Fa = fmaf(f, eh, own.fext[a][d]), Fb = fmaf(-f, eh, own.fext[a + 3][d]);
+            own.F[a][d] = Fa;
+            own.F[a + 3][d] = Fb;
+            const float2 wp = make_float2(pa, pb), wg = make_float2(Fa * k8, Fb * k8);
+            float2 *tr = (float2 *)(tile + own_off + d);
+            tr[a] = wp;            // record word a: positions along a
+            tr[3 + a] = wg;        // record word 3 + a: G along a
+            if (ev + 1 < 2 * P.K) {
+                ulonglong2 *dst = P.rec + ((size_t)(par ^ 1) * Spad + s) * 6;
+                st_tagged(dst + a, wp.x, wp.y, tag + 1);
+                st_tagged(dst + 3 + a, wg.x, wg.y, tag + 1);
+            } else {
+                float2 *pk = (float2 *)(P.pack + s);   // the final state's records, for the grid path
+                pk[a] = wp;
+                pk[3 + a] = wg;
             }
         }
         __syncthreads();  // the tile's own records are complete before the next sweep
@@ -595,13 +610,12 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
         const int64_t o = 6 * (int64_t)s;
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            A.x[o + k] = ds_to_double({own.xh[k][lane], own.xl[k][lane]}) + cen[k % 3];
+            A.x[o + k] = own.x[k][lane] + cen[k % 3];
             A.Fd[o + k] = (double)own.F[k][lane];
         }
         if (A.avg_m > 0) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k)
-                A.Racc[3 * (int64_t)s + k] = ds_to_double({own.Rh[k][lane], own.Rl[k][lane]});
+            for (int k = 0; k < 3; ++k) A.Racc[3 * (int64_t)s + k] = own.R[k][lane];
         }
     }
     if (blockIdx.x == 0 && tid == 0) *A.step = P.n0 + P.K;
