@@ -167,6 +167,8 @@ def ensemble_measure(dbs, inputs, torch, stream, steps=1000, count=256):
     hs = [dbs.Suspension.from_inputs(s, precision="fp32c", stream=stream) for s in systems]
     pairs = sum(2 * (2 * s.S) * (2 * s.S - 1) for s in systems)
     ens = dbs.Ensemble(hs, stream=stream)
+    from paper_1004_1932_b300 import autotune
+    tuned = autotune.tune_ensemble(ens, hs)
     ens.step(16)
     ens.sync()
     t0 = time.perf_counter()
@@ -193,7 +195,11 @@ def ensemble_measure(dbs, inputs, torch, stream, steps=1000, count=256):
                         f"seeds 0..{count - 1}, RPY, FP32C",
             "batched": {"steps": steps, "seconds": el_b, "system_steps_per_s": b,
                         "pairs_per_s": pairs * steps / el_b,
-                        "clusters": {str(g): G.count(g) for g in sorted(set(G))}},
+                        "clusters": {str(g): G.count(g) for g in sorted(set(G))},
+                        "autotune": {"choice": tuned["choice"],
+                                     "s_per_step": tuned["s_per_step"]},
+                        "launch": "one resident launch per class per 1024 steps, replayed from a "
+                                  "captured CUDA graph"},
             "one_system_per_launch": {"steps": seq_steps, "seconds": el_s, "system_steps_per_s": sq,
                                       "pairs_per_s": pairs * seq_steps / el_s},
             "speedup": b / sq}

@@ -110,3 +110,52 @@ def choose_path(h: "dbs.Suspension", steps: int = 1024) -> dict:
     h.set_path(best)
     h.set_state(x0, n0)
     return {"path": best, "s_per_step": timings}
+
+
+def _pow2_at_least(v: int) -> int:
+    g = 1
+    while g < v:
+        g *= 2
+    return g
+
+
+def tune_ensemble(ens: "dbs.Ensemble", members, steps: int = 128) -> dict:
+    """Cluster sizes (the tile shape of the resident kernel: CTAs per member)
+    for an ensemble, chosen by timing.  Candidates: the built-in balance rule
+    (G proportional to each member's S^2), the rule scaled by 1/2 and by 2, and
+    the smallest clusters that fit.  Members' states are restored after every
+    trial, so the choice does not change the trajectories."""
+    import time
+    states = [h.get_state() for h in members]
+    ens.set_clusters(None)
+    base = ens.get_clusters()
+    gmin = [_pow2_at_least(max(1, -(-h.S // 512))) for h in members]
+    cands = {"balance": None,
+             "half": [max(m, g // 2) for g, m in zip(base, gmin)],
+             "double": [min(16, 2 * g) for g in base],
+             "smallest": gmin}
+    timings = {}
+    for name, G in cands.items():
+        try:
+            ens.set_clusters(G)
+            ens.step(8)
+            ens.sync()
+            t = time.perf_counter()
+            ens.step(steps)
+            ens.sync()
+            timings[name] = (time.perf_counter() - t) / steps
+        except dbs.DbsError:
+            pass
+        for h, (x, n) in zip(members, states):
+            h.set_state(x, n)
+    best = min(timings, key=timings.get)
+    ens.set_clusters(cands[best])
+    return {"choice": best, "s_per_step": timings,
+            "clusters": {str(g): c for g, c in sorted(_count(ens.get_clusters()).items())}}
+
+
+def _count(G):
+    out = {}
+    for g in G:
+        out[g] = out.get(g, 0) + 1
+    return out

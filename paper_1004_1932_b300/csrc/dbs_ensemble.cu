@@ -80,6 +80,7 @@ struct dbs_ensemble {
     std::map<ClassKey, Class> classes;
     cudaEvent_t fork = nullptr, joined = nullptr;
     bool classes_ready = false;
+    cudaGraphExec_t launches = nullptr;   // captured fork / class launches / join of one block
 };
 
 static int efail(dbs_ensemble *e, int st, const char *fmt, ...)
@@ -135,6 +136,8 @@ static void free_classes(dbs_ensemble *e)
     }
     e->classes.clear();
     e->classes_ready = false;
+    if (e->launches) cudaGraphExecDestroy(e->launches);
+    e->launches = nullptr;
 }
 
 static int build_classes(dbs_ensemble *e)
@@ -206,6 +209,64 @@ static ResSys make_sys(const dbs_suspension *h, int G)
 // null); all work is ordered after the members' pending work and before their
 // later work.  Blocks of at most K_BLOCK steps; a member whose count is used up
 // sits out the remaining blocks (K = 0 launches nothing for it).
+// One block of resident launches on the ensemble stream: fork to the class
+// streams, one launch per class (members read their K and state from d_sys),
+// join.  Captured once per class layout into a CUDA graph and replayed for every
+// block; what changes from block to block (step counts, buffers) is data in
+// d_sys, uploaded before each replay.
+static int enqueue_launches(dbs_ensemble *e)
+{
+    ECK(e, cudaEventRecord(e->fork, e->stream));
+    for (auto &kv : e->classes) {
+        Class &c = kv.second;
+        ECK(e, cudaStreamWaitEvent(c.stream, e->fork, 0));
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)(kv.first.G * c.members.size()));
+        cfg.blockDim = dim3((unsigned)kv.first.nt);
+        cfg.dynamicSmemBytes = c.smem;
+        cfg.stream = c.stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = kv.first.G;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const ResSys *ds = e->d_sys;
+        const int *cs = c.csys;
+        cudaError_t err;
+        if (kv.first.mob == DBS_OSEEN)
+            err = kv.first.nt == NT_BIG ? cudaLaunchKernelEx(&cfg, resident_kernel<0, NT_BIG>, ds, cs)
+                                        : cudaLaunchKernelEx(&cfg, resident_kernel<0, NT_SMALL>, ds, cs);
+        else
+            err = kv.first.nt == NT_BIG ? cudaLaunchKernelEx(&cfg, resident_kernel<1, NT_BIG>, ds, cs)
+                                        : cudaLaunchKernelEx(&cfg, resident_kernel<1, NT_SMALL>, ds, cs);
+        if (err != cudaSuccess)
+            return efail(e, DBS_E_CUDA, "resident launch (G=%d, %zu members): %s", kv.first.G,
+                         c.members.size(), cudaGetErrorString(err));
+        ECK(e, cudaEventRecord(c.done, c.stream));
+        ECK(e, cudaStreamWaitEvent(e->stream, c.done, 0));
+    }
+    return DBS_OK;
+}
+
+static int capture_launches(dbs_ensemble *e)
+{
+    ECK(e, cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue_launches(e);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(e->stream, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (ce != cudaSuccess) return efail(e, DBS_E_CUDA, "ensemble capture: %s", cudaGetErrorString(ce));
+    const cudaError_t ie = cudaGraphInstantiate(&e->launches, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return efail(e, DBS_E_CUDA, "ensemble graph: %s", cudaGetErrorString(ie));
+    return DBS_OK;
+}
+
 static int ensemble_step_v(dbs_ensemble *e, int64_t n, const int64_t *steps)
 {
     if (e->status != DBS_OK) return e->status;
@@ -239,37 +300,11 @@ static int ensemble_step_v(dbs_ensemble *e, int64_t n, const int64_t *steps)
         if (!e->d_sys) ECK(e, cudaMalloc(&e->d_sys, sizeof(ResSys) * M));
         ECK(e, cudaMemcpyAsync(e->d_sys, sys.data(), sizeof(ResSys) * M, cudaMemcpyHostToDevice,
                                e->stream));
-        ECK(e, cudaEventRecord(e->fork, e->stream));
-        for (auto &kv : e->classes) {
-            Class &c = kv.second;
-            ECK(e, cudaStreamWaitEvent(c.stream, e->fork, 0));
-            cudaLaunchConfig_t cfg{};
-            cfg.gridDim = dim3((unsigned)(kv.first.G * c.members.size()));
-            cfg.blockDim = dim3((unsigned)kv.first.nt);
-            cfg.dynamicSmemBytes = c.smem;
-            cfg.stream = c.stream;
-            cudaLaunchAttribute attr[1];
-            attr[0].id = cudaLaunchAttributeClusterDimension;
-            attr[0].val.clusterDim.x = kv.first.G;
-            attr[0].val.clusterDim.y = 1;
-            attr[0].val.clusterDim.z = 1;
-            cfg.attrs = attr;
-            cfg.numAttrs = 1;
-            const ResSys *ds = e->d_sys;
-            const int *cs = c.csys;
-            cudaError_t err;
-            if (kv.first.mob == DBS_OSEEN)
-                err = kv.first.nt == NT_BIG ? cudaLaunchKernelEx(&cfg, resident_kernel<0, NT_BIG>, ds, cs)
-                                            : cudaLaunchKernelEx(&cfg, resident_kernel<0, NT_SMALL>, ds, cs);
-            else
-                err = kv.first.nt == NT_BIG ? cudaLaunchKernelEx(&cfg, resident_kernel<1, NT_BIG>, ds, cs)
-                                            : cudaLaunchKernelEx(&cfg, resident_kernel<1, NT_SMALL>, ds, cs);
-            if (err != cudaSuccess)
-                return efail(e, DBS_E_CUDA, "resident launch (G=%d, %zu members): %s", kv.first.G,
-                             c.members.size(), cudaGetErrorString(err));
-            ECK(e, cudaEventRecord(c.done, c.stream));
-            ECK(e, cudaStreamWaitEvent(e->stream, c.done, 0));
+        if (!e->launches) {
+            int rc = capture_launches(e);
+            if (rc) return rc;
         }
+        ECK(e, cudaGraphLaunch(e->launches, e->stream));
         for (size_t i = 0; i < M; ++i) {
             const int K = (int)std::min<int64_t>(left[i], K_BLOCK);
             e->m[i]->n_host += K;
