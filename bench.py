@@ -415,20 +415,34 @@ def run_ours(args):
     h.close()
     sa.close()
 
-    # ---- the same kernel on the large single system (S=32768, N=65536) --------
+    # ---- the same kernel on large single systems: FP32C vs all-FP64 ----------------
+    # (S = 2048, 8192, 32768; one pair-sum launch of the grid path, CUDA events)
     large = None
     if not args.no_large:
-        sl = inputs.paper_scale(32768, seed=rank, mobility=args.mobility)
-        hl = dbs.Suspension.from_inputs(sl, precision="fp32c", stream=stream, device=local)
-        hl.step_timed(2)
-        ms_l = hl.step_timed(6)
-        hl.close()
-        Nl = 2 * 32768
-        ach_l = Nl * (Nl - 1) * FLOPS_PER_PAIR[args.mobility] / (ms_l / 1e3) / 1e12
+        fp64_peak = props.multi_processor_count * 2 * 2 * mhz_max * 1e6 / 1e12   # 2 DFMA/clk/SM
+        sweep = []
+        for Sl in (2048, 8192, 32768):
+            sl = inputs.paper_scale(Sl, seed=rank, mobility=args.mobility)
+            Nl = 2 * Sl
+            row = {"S": Sl, "N": Nl}
+            for prec, reps in (("fp32c", 6), ("fp64", 2)):
+                hl = dbs.Suspension.from_inputs(sl, precision=prec, stream=stream, device=local)
+                hl.step_timed(1)
+                ms_l = hl.step_timed(reps)
+                hl.close()
+                ach_l = Nl * (Nl - 1) * FLOPS_PER_PAIR[args.mobility] / (ms_l / 1e3) / 1e12
+                row[prec] = {"launch_ms": ms_l, "pairs_per_s": Nl * (Nl - 1) / (ms_l / 1e3),
+                             "achieved_tflops": ach_l,
+                             "frac_of_fp32_peak": ach_l / peak,
+                             **({"frac_of_fp64_peak": ach_l / fp64_peak} if prec == "fp64" else {})}
+            sweep.append(row)
+        top = sweep[-1]["fp32c"]
         large = {"workload": "single suspension S=32768 (N=65536), density 0.002, same kernel",
-                 "launch_ms": ms_l, "achieved": ach_l, "peak": peak, "unit": "TFLOP/s",
-                 "frac": ach_l / peak,
-                 "pairs_per_s": 2 * Nl * (Nl - 1) / (2 * ms_l / 1e3)}
+                 "launch_ms": top["launch_ms"], "achieved": top["achieved_tflops"], "peak": peak,
+                 "unit": "TFLOP/s", "frac": top["frac_of_fp32_peak"], "pairs_per_s": top["pairs_per_s"],
+                 "size_sweep": sweep,
+                 "fp64_peak_tflops": fp64_peak,
+                 "note": "one pair-sum launch (grid path); FP64 peak = SMs x 2 DFMA/clk x 2 x max clock"}
 
     # ---- end to end through the C-ABI with host buffers -----------------------
     e2e = None
