@@ -29,15 +29,20 @@
  *  - Handles are opaque and own their device memory (cudaMalloc at create,
  *    cudaFree at destroy).  A handle must not be used from two host threads
  *    at once.
- *  - Every call returns DBS_OK (0) or a negative DBS_E_* status.  Errors are
- *    sticky: once a handle has failed, every later call on it returns the
- *    same status until it is destroyed; dbs_last_error() describes it.
+ *  - Every call returns DBS_OK (0) or a negative DBS_E_* status.  Errors found
+ *    while computing (device faults, CUDA failures) are sticky: once a handle
+ *    has failed, every later call on it returns the same status until it is
+ *    destroyed; dbs_last_error() describes it.  Refused arguments (DBS_E_ARG)
+ *    and calls not valid in the handle's mode (DBS_E_STATE) leave it usable.
  *  - Time is t_n = n dt, computed in double precision from the step counter n.
  *
  * Arithmetic: FP32C evaluates the pair sum of Eq. (3b) in single precision
  * with per-target compensated (two-sum) accumulation across j-tiles, and
- * keeps positions, spring forces, the self term, the clock and the Heun
- * update in double precision.  FP64 does everything in double precision.
+ * keeps positions, the clock and the Heun update in double precision.  The
+ * spring force and the self term are double precision on the grid and
+ * cluster paths; the cooperative path forms them in single precision from a
+ * double-single d^2 - L^2 (the stretch d - L keeps single-precision relative
+ * accuracy).  FP64 does everything in double precision.
  */
 #ifndef DBS_H
 #define DBS_H
