@@ -478,17 +478,13 @@ int dbs_set_path(dbs_suspension *h, int32_t path, int32_t cluster_size)
     h->path = DBS_PATH_GRID;
     if (path == DBS_PATH_GRID) return DBS_OK;
     if (path == DBS_PATH_COOP) {
-        int rc = coop_setup(h);
-        if (rc) {
-            // a size the path cannot hold is an argument error, not a broken handle
-            if (rc == DBS_E_ARG) h->status = DBS_OK;
-            return rc;
-        }
+        int rc = coop_setup(h);   // a size the path cannot hold is refused, the handle stays usable
+        if (rc) return rc;
         h->path = DBS_PATH_COOP;
         return DBS_OK;
     }
     if (path != DBS_PATH_CLUSTER) return DBS_E_ARG;
-    if (!member_ok(h)) return fail(h, DBS_E_ARG, "cluster path needs FP32C and S small enough");
+    if (!member_ok(h)) return refuse(h, DBS_E_ARG, "cluster path needs FP32C and S small enough");
     if (h->solo) solo_destroy(h);
     dbs_suspension *one[1] = {h};
     dbs_ensemble *e = nullptr;

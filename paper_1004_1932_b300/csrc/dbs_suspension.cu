@@ -713,11 +713,11 @@ static void drop_flow(dbs_suspension *h)
 int coop_setup(dbs_suspension *h)
 {
     if (h->p.precision != DBS_FP32C || h->S > SMALL_S)
-        return fail(h, DBS_E_ARG, "cooperative path needs FP32C and S <= %lld", (long long)SMALL_S);
+        return refuse(h, DBS_E_ARG, "cooperative path needs FP32C and S <= 2048");
     int coop = 0, clusters = 0;
     CK(h, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device));
     CK(h, cudaDeviceGetAttribute(&clusters, cudaDevAttrClusterLaunch, h->device));
-    if (!coop || !clusters) return fail(h, DBS_E_ARG, "device without cooperative or cluster launch");
+    if (!coop || !clusters) return refuse(h, DBS_E_ARG, "device without cooperative or cluster launch");
     const int I = (int)((h->S + FLOW_IB - 1) / FLOW_IB);
     const int creq = std::min(h->flow_creq > 0 ? h->flow_creq : FLOW_MAX_C, 16);
     const void *k = flow_fn(h);
@@ -731,7 +731,7 @@ int coop_setup(dbs_suspension *h)
         int ncl = 0;
         CK(h, cudaOccupancyMaxActiveClusters(&ncl, k, &cfg));
         if (ncl >= I) break;
-        if (q >= I) return fail(h, DBS_E_ARG, "cooperative path: grid does not fit the device");
+        if (q >= I) return refuse(h, DBS_E_ARG, "cooperative path: grid does not fit the device");
     }
     CK(h, cudaStreamSynchronize(h->stream));
     drop_flow(h);

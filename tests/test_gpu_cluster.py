@@ -110,3 +110,18 @@ def test_ensemble_rejects_fp64_members():
         dbs.Ensemble([h])
     assert ei.value.status == dbs.E_ARG
     h.close()
+
+
+def test_cluster_path_refusal_leaves_handle_usable():
+    s = inputs.make_suspension(4000, seed=2, density=0.002)
+    h = dbs.Suspension(s.x0, a=s.a, mu=s.mu, k0=s.k0, ell=s.ell, omega=s.omega, dt=s.dt,
+                       precision="fp32c", lam=s.lam, phi=s.phi)
+    with pytest.raises(dbs.DbsError) as ei:
+        h.set_path("cluster")
+    assert ei.value.status == dbs.E_ARG
+    with pytest.raises(dbs.DbsError):
+        h.set_path("coop")
+    assert h.get_path()[0] == "grid"
+    h.step(2)
+    assert np.isfinite(h.positions()).all()
+    h.close()
