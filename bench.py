@@ -483,7 +483,8 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 pair math, f64 state",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "dtype_note": "FP32 pair math with two-sum compensation; FP64 positions, clock and Heun update",
         "data": "synthetic (seeded random suspension, no dataset)",
         "config": _workload_config(S, args.mobility, "flushed between timed steps (2x L2 write)"),
         "heun_steps_per_s": ws * m * args.steps / (ms / 1e3),
