@@ -22,10 +22,10 @@ using namespace dbs;
 namespace {
 
 #ifndef DBS_BT_LARGE
-#define DBS_BT_LARGE 128
+#define DBS_BT_LARGE 512
 #endif
 #ifndef DBS_TILE_LARGE
-#define DBS_TILE_LARGE 256
+#define DBS_TILE_LARGE 512
 #endif
 constexpr int BT32 = DBS_BT_LARGE;      // dumbbells per CTA (FP32C, large systems)
 constexpr int TILE32 = DBS_TILE_LARGE;  // dumbbell records per shared-memory tile (FP32C)

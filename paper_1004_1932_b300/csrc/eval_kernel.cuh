@@ -27,9 +27,11 @@
 
 // Tuning macros (defaults measured on B300 at N = 65536, see profiles/):
 //   DBS_RPY_W35           RPY coefficients as A = w + c2 w^3, B = (r.G)(w^3 + c3 w^5)
-//   DBS_UNROLL            unroll of the fast j-loop
+//   DBS_UNROLL            unroll of the fast j-loop for CTAs of fewer than 256 threads
+//                         (larger CTAs, the large-system configuration, unroll by 8)
 //   DBS_FP32_WARPS_PER_SM resident warps the FP32 kernels are register-capped for
 //   DBS_W2_RCP            w^2 from rcp.approx instead of w*w (slower on B300; off)
+//   DBS_UNIT_ORDER        1: work units in chunk-major order, 0: i-block-major
 #ifndef DBS_RPY_W35
 #define DBS_RPY_W35 1
 #endif
@@ -42,6 +44,9 @@
 #ifndef DBS_W2_RCP
 #define DBS_W2_RCP 0
 #endif
+#ifndef DBS_UNIT_ORDER
+#define DBS_UNIT_ORDER 1
+#endif
 
 namespace dbs {
 constexpr int kPairUnroll = DBS_UNROLL;  // unroll of the fast j-loop
@@ -52,8 +57,12 @@ namespace dbs {
 // ---- FP32 pair terms, two j-spheres per call ----------------------------------
 // Target sphere (px, py, pz), duplicated in both halves, against the two
 // spheres of one j-record (half .x = sphere 2r, half .y = sphere 2r + 1).
-// GUARD masks the self pair: w = 0 makes its term exactly zero.
-template <int MOB, bool GUARD>
+// GUARD masks the self pair: w = 0 makes its term exactly zero.  IMIN3 selects
+// how the overlap minimum of r^2 is kept: one three-input integer min on the
+// bit patterns (fewer issue slots: faster in the throughput-bound large-system
+// sweep) or two float mins (shorter latency: faster in the latency-bound
+// cooperative and cluster-resident kernels, measured on B300).
+template <int MOB, bool GUARD, bool IMIN3 = true>
 __device__ __forceinline__ void pair2(const float2 px, const float2 py, const float2 pz,
                                       const float2 jx, const float2 jy, const float2 jz,
                                       const float2 gx, const float2 gy, const float2 gz,
@@ -109,8 +118,15 @@ __device__ __forceinline__ void pair2(const float2 px, const float2 py, const fl
         if (GUARD) {
             r2min = fminf(r2min, skip_x ? 3.0e38f : r2.x);
             r2min = fminf(r2min, skip_y ? 3.0e38f : r2.y);
-        } else {
+        } else if (!IMIN3) {
             r2min = fminf(r2min, fminf(r2.x, r2.y));
+        } else {
+            // r2 >= 0, and non-negative floats order like their bit patterns read as
+            // unsigned integers: one three-input integer min instead of two float
+            // mins (a NaN pattern lies above every finite value, so it is ignored
+            // as fminf ignores it)
+            r2min = __uint_as_float(__vimin3_u32(__float_as_uint(r2min), __float_as_uint(r2.x),
+                                                 __float_as_uint(r2.y)));
         }
     }
 }
@@ -225,6 +241,10 @@ __device__ __forceinline__ void sweep_f32(const DbF32 *__restrict__ pin, DbF32 *
                                           float c2s, float c3s, float s_[6], float c_[6],
                                           float &r2min)
 {
+    // large CTAs (the throughput-bound large-system configuration): unroll by 8
+    // and the three-input integer min; small ones keep the latency-friendly forms
+    constexpr int kUnroll = BT >= 256 ? 8 : kPairUnroll;
+    constexpr bool kImin3 = BT >= 256;
     const int tid = threadIdx.x;
     float2 pax = make_float2(0.f, 0.f), pay = pax, paz = pax, pbx = pax, pby = pax, pbz = pax;
     if (active) {
@@ -246,15 +266,15 @@ __device__ __forceinline__ void sweep_f32(const DbF32 *__restrict__ pin, DbF32 *
         float2 qa[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         float2 qb[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         if (!diag) {
-#pragma unroll kPairUnroll
+#pragma unroll kUnroll
             for (int k = 0; k < len; ++k) {
                 const float4 ra = tile[k].a, rb = tile[k].b, rc = tile[k].c;
                 const float2 jx = make_float2(ra.x, ra.y), jy = make_float2(ra.z, ra.w);
                 const float2 jz = make_float2(rb.x, rb.y), gx = make_float2(rb.z, rb.w);
                 const float2 gy = make_float2(rc.x, rc.y), gz = make_float2(rc.z, rc.w);
-                pair2<MOB, false>(pax, pay, paz, jx, jy, jz, gx, gy, gz, c2, c3, qa[0], qa[1],
+                pair2<MOB, false, kImin3>(pax, pay, paz, jx, jy, jz, gx, gy, gz, c2, c3, qa[0], qa[1],
                                   qa[2], r2min, false, false);
-                pair2<MOB, false>(pbx, pby, pbz, jx, jy, jz, gx, gy, gz, c2, c3, qb[0], qb[1],
+                pair2<MOB, false, kImin3>(pbx, pby, pbz, jx, jy, jz, gx, gy, gz, c2, c3, qb[0], qb[1],
                                   qb[2], r2min, false, false);
             }
         } else {
@@ -316,7 +336,9 @@ __device__ __forceinline__ void sweep_f64(const DbF64 *__restrict__ pin, DbF64 *
 // (the host limits S to 2^29).
 //
 // FP32: registers capped so that DBS_FP32_WARPS_PER_SM warps stay resident
-// (20 warps: at most 102 registers).  FP64 keeps the compiler's choice.  Dynamic shared memory:
+// (20 warps: at most 102 registers) for CTAs of up to 640 threads; a 512-thread
+// CTA (the large-system configuration, one CTA per SM) may use up to 128.  FP64
+// keeps the compiler's choice.  Dynamic shared memory:
 // eval_smem_bytes(BT, TDB, C).
 template <typename Real, int BT>
 struct MinBlocks { static constexpr int value = sizeof(Real) == 4 ? 32 * DBS_FP32_WARPS_PER_SM / BT : 1; };
@@ -355,8 +377,17 @@ __device__ __forceinline__ void eval_units(const EvalArgs &A, const void *pack_i
     const int units = iblocks * C;
 
     for (int unit = blockIdx.x; unit < units; unit += gridDim.x) {
+#if DBS_UNIT_ORDER
+        // chunk-major: every i-block's last chunk falls in the last wave, so the
+        // i-blocks' fixups run side by side at the end of the launch instead of
+        // piling onto one CTA (a CTA that did a fixup lags and would arrive last,
+        // and do the fixup, in each of its following i-blocks)
+        const int c = unit / iblocks;
+        const int ib_ = unit - c * iblocks;
+#else
         const int ib_ = unit / C;
         const int c = unit - ib_ * C;
+#endif
         const int s = ib_ * BT + tid;
         const bool active = s < S;
         const int db = (int)(((int64_t)S * c) / C);

@@ -405,9 +405,9 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
                     const float2 jx = make_float2(ra.x, ra.y), jy = make_float2(ra.z, ra.w);
                     const float2 jz = make_float2(rb.x, rb.y), gx = make_float2(rb.z, rb.w);
                     const float2 gy = make_float2(rc.x, rc.y), gz = make_float2(rc.z, rc.w);
-                    pair2<MOB, false>(pax, pay, paz, jx, jy, jz, gx, gy, gz, c2, c3, qa[0], qa[1],
+                    pair2<MOB, false, false>(pax, pay, paz, jx, jy, jz, gx, gy, gz, c2, c3, qa[0], qa[1],
                                       qa[2], r2min, false, false);
-                    pair2<MOB, false>(pbx, pby, pbz, jx, jy, jz, gx, gy, gz, c2, c3, qb[0], qb[1],
+                    pair2<MOB, false, false>(pbx, pby, pbz, jx, jy, jz, gx, gy, gz, c2, c3, qb[0], qb[1],
                                       qb[2], r2min, false, false);
                 }
             } else {

@@ -78,9 +78,9 @@ __device__ __forceinline__ void res_sweep(const DbF32 *rec, int db, int de, int 
                 const float2 jx = make_float2(ra.x, ra.y), jy = make_float2(ra.z, ra.w);
                 const float2 jz = make_float2(rb.x, rb.y), gx = make_float2(rb.z, rb.w);
                 const float2 gy = make_float2(rc.x, rc.y), gz = make_float2(rc.z, rc.w);
-                pair2<MOB, false>(pa[0], pa[1], pa[2], jx, jy, jz, gx, gy, gz, c2, c3, qa[0],
+                pair2<MOB, false, false>(pa[0], pa[1], pa[2], jx, jy, jz, gx, gy, gz, c2, c3, qa[0],
                                   qa[1], qa[2], r2min, false, false);
-                pair2<MOB, false>(pb[0], pb[1], pb[2], jx, jy, jz, gx, gy, gz, c2, c3, qb[0],
+                pair2<MOB, false, false>(pb[0], pb[1], pb[2], jx, jy, jz, gx, gy, gz, c2, c3, qb[0],
                                   qb[1], qb[2], r2min, false, false);
             }
         } else {
