@@ -393,8 +393,9 @@ def run_ours(args):
         # one launch advances 1024 Heun steps (2048 pair sums)
         kname = ("resident_kernel (cluster-resident pair sums + Heun, 1024 steps per launch)"
                  if path_choice["path"] == "cluster" else
-                 "flow_kernel (cooperative dataflow: pair sums + Heun, tagged point-to-point "
-                 "exchange, 1024 steps per launch)")
+                 "flow_kernel (cooperative dataflow: each CTA owns T dumbbells and sums them "
+                 "over all records, fused Heun epilogue, tagged point-to-point exchange of "
+                 "records, 1024 steps per launch)")
         kev0, kev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         launches = []
         for _ in range(3):

@@ -197,9 +197,10 @@ DBS_API int dbs_step_timed(dbs_suspension *h, int64_t n, double *mean_ms);
 /*
  * Launch tuning of the pair-sum kernel (used by the autotuner): split the
  * j-range into `chunks` pieces (1 <= chunks <= max(1, S/8); 0 restores the
- * built-in choice).  Results change only in the rounding of the j-sum order.
+ * built-in choice; on the cooperative path the request is dumbbells per CTA,
+ * see DBS_PATH_COOP).  Results change only in the rounding of the j-sum order.
  * dbs_get_launch reports dumbbells per CTA, chunks and grid size (on the
- * cooperative path: dumbbells per i-block, j-chunks, CTAs).
+ * cooperative path: dumbbells per CTA, 1, CTAs).
  */
 DBS_API int dbs_set_chunks(dbs_suspension *h, int32_t chunks);
 DBS_API int dbs_get_launch(dbs_suspension *h, int32_t *bt, int32_t *chunks, int32_t *grid);
@@ -329,15 +330,18 @@ DBS_API int dbs_pair_distance_error(int64_t S, const double *A0_dev, const doubl
 #define DBS_PATH_GRID 0
 #define DBS_PATH_CLUSTER 1
 /*
- *  DBS_PATH_COOP     one cooperative launch over all SMs advances up to 1024
- *                    Heun steps.  CTAs exchange records and partial sums
- *                    through flag-tagged words in device memory, point to
- *                    point, with no grid-wide barrier.  Every wait is bounded
- *                    (about one second): a launch whose exchange cannot
- *                    complete ends with DBS_E_TIMEOUT instead of hanging.
- *                    FP32C, S <= 2048.  dbs_set_chunks on this path sets the
- *                    number of j-chunks (default 8, fewer if the grid would
- *                    not be co-resident).
+ *  DBS_PATH_COOP     one cooperative launch of up to one CTA per SM advances up
+ *                    to 1024 Heun steps.  Each CTA owns T dumbbells and sums
+ *                    their pair terms over all records itself; CTAs exchange
+ *                    only the records, through flag-tagged words in device
+ *                    memory, point to point, with no grid-wide barrier.  Every
+ *                    wait is bounded (about one second): a launch whose
+ *                    exchange cannot complete ends with DBS_E_TIMEOUT instead
+ *                    of hanging.  FP32C, S <= 2048.  dbs_set_chunks(c) on this
+ *                    path (1 <= c <= 16) asks for T = the largest power of two
+ *                    not above c, raised until ceil(S / T) CTAs fit the SMs;
+ *                    0 restores the built-in choice (the smallest T that fits;
+ *                    16 for S <= 16).
  */
 #define DBS_PATH_COOP 2
 DBS_API int dbs_set_path(dbs_suspension *h, int32_t path, int32_t cluster_size);

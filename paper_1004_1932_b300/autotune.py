@@ -94,22 +94,43 @@ def choose_path(h: "dbs.Suspension", steps: int = 1024) -> dict:
     import time
     x0, n0 = h.get_state()
     timings = {}
-    for path in ("grid", "cluster", "coop"):
-        try:
-            h.set_path(path)
-        except dbs.DbsError:
-            continue
+    coop_split = {}
+
+    def _time():
         h.step(64)
         h.sync()
         t = time.perf_counter()
         h.step(steps)
         h.sync()
-        timings[path] = (time.perf_counter() - t) / steps
+        el = (time.perf_counter() - t) / steps
         h.set_state(x0, n0)
+        return el
+
+    for path in ("grid", "cluster", "coop"):
+        try:
+            h.set_path(path)
+        except dbs.DbsError:
+            continue
+        if path != "coop":
+            timings[path] = _time()
+            continue
+        # cooperative path: also the split (dumbbells per CTA) around the built-in one
+        for req in (0, 4, 8, 16):
+            h.set_chunks(req)
+            T = h.get_launch()["bt"]
+            if T not in coop_split:
+                coop_split[T] = _time()
+        timings[path] = min(coop_split.values())
     best = min(timings, key=timings.get)
     h.set_path(best)
+    out = {"path": best, "s_per_step": timings}
+    if best == "coop":
+        T = min(coop_split, key=coop_split.get)
+        h.set_chunks(T)
+        out["coop_dumbbells_per_cta"] = T
+        out["coop_split_s_per_step"] = coop_split
     h.set_state(x0, n0)
-    return {"path": best, "s_per_step": timings}
+    return out
 
 
 def _pow2_at_least(v: int) -> int:

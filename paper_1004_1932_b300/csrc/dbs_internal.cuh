@@ -19,7 +19,8 @@ struct dbs_suspension {
     double *sd_buf = nullptr;      // shape-driven work arrays (see dbs_shape.cu)
     // cooperative dataflow path: tagged record buffer, split, next tag
     ulonglong2 *ll_rec = nullptr;
-    int flow_I = 0, flow_q = 0, flow_C = 0, flow_creq = 0;
+    int flow_T = 0, flow_G = 0;    // dumbbells per CTA, CTAs
+    int flow_creq = 0;             // dbs_set_chunks request (dumbbells per CTA), 0 = built-in
     unsigned flow_base = 1;
     dbs_params p{};
     int device = 0;

@@ -661,46 +661,8 @@ int dbs_set_external_force(dbs_suspension *h, const double *F)
 // ---------------------------------------------------------------------------
 // cooperative dataflow path (flow_kernel)
 // ---------------------------------------------------------------------------
-#ifndef DBS_FLOW_WARPS
-#define DBS_FLOW_WARPS 8
-#endif
-constexpr int FLOW_W = DBS_FLOW_WARPS;     // warps per CTA
-constexpr int FLOW_MAX_C = 8;              // j-chunks per i-block by default
-constexpr int FLOW_MAX_STEPS = 1024;       // Heun steps per launch
-
-static const void *flow_fn(const dbs_suspension *h)
-{
-    const bool noise = h->noise_sigma > 0.0;
-    if (h->p.mobility == DBS_OSEEN)
-        return noise ? (const void *)flow_kernel<0, FLOW_W, true> : (const void *)flow_kernel<0, FLOW_W, false>;
-    return noise ? (const void *)flow_kernel<1, FLOW_W, true> : (const void *)flow_kernel<1, FLOW_W, false>;
-}
-
-// dynamic shared memory of flow_kernel: the chunk's records and the owner's
-// table of chunk pairs
-static size_t flow_smem(int q, int C)
-{
-    return (size_t)q * FLOW_IB * sizeof(DbF32) + (size_t)C * 6 * FLOW_IB * sizeof(ulonglong2);
-}
-
-static cudaLaunchConfig_t flow_config(const dbs_suspension *h, int q, int C, cudaLaunchAttribute *attr)
-{
-    const int I = (int)((h->S + FLOW_IB - 1) / FLOW_IB);
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(I * C);
-    cfg.blockDim = dim3(32 * FLOW_W);
-    cfg.dynamicSmemBytes = flow_smem(q, C);
-    cfg.stream = h->stream;
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    attr[1].id = cudaLaunchAttributeClusterDimension;
-    attr[1].val.clusterDim.x = C;
-    attr[1].val.clusterDim.y = 1;
-    attr[1].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 2;
-    return cfg;
-}
+constexpr int FLOW_MAX_T = 16;        // dumbbells per CTA at most
+constexpr int FLOW_MAX_STEPS = 1024;  // Heun steps per launch
 
 static void drop_flow(dbs_suspension *h)
 {
@@ -708,46 +670,85 @@ static void drop_flow(dbs_suspension *h)
     h->ll_rec = nullptr;
 }
 
-// Split: the most j-chunks (up to the requested count, at most 16: one
-// thread-block cluster per i-block) for which all I clusters are co-resident.
+template <int MOB, bool NOISE>
+static const void *flow_pick(int T)
+{
+    switch (T) {
+    case 1: return (const void *)flow_kernel<MOB, 1, NOISE>;
+    case 2: return (const void *)flow_kernel<MOB, 2, NOISE>;
+    case 4: return (const void *)flow_kernel<MOB, 4, NOISE>;
+    case 8: return (const void *)flow_kernel<MOB, 8, NOISE>;
+    case 16: return (const void *)flow_kernel<MOB, 16, NOISE>;
+    default: return nullptr;
+    }
+}
+
+static const void *flow_fn(const dbs_suspension *h, int T)
+{
+    const bool noise = h->noise_sigma > 0.0;
+    if (h->p.mobility == DBS_OSEEN) return noise ? flow_pick<0, true>(T) : flow_pick<0, false>(T);
+    return noise ? flow_pick<1, true>(T) : flow_pick<1, false>(T);
+}
+
+// dynamic shared memory of flow_kernel: every record of the suspension
+static size_t flow_smem(int G, int T) { return (size_t)G * T * sizeof(DbF32); }
+
+static cudaLaunchConfig_t flow_config(const dbs_suspension *h, int G, int T, cudaLaunchAttribute *attr)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(FLOW_NT);
+    cfg.dynamicSmemBytes = flow_smem(G, T);
+    cfg.stream = h->stream;
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+// Split: T dumbbells per CTA, the smallest power of two (at least the largest
+// one not above a dbs_set_chunks request; 16 for S <= 16, so that one CTA holds
+// a tiny system) for which all ceil(S / T) CTAs fit the SMs, one CTA each.
 int coop_setup(dbs_suspension *h)
 {
     if (h->p.precision != DBS_FP32C || h->S > SMALL_S)
         return refuse(h, DBS_E_ARG, "cooperative path needs FP32C and S <= 2048");
-    int coop = 0, clusters = 0;
+    int coop = 0, sms = 0;
     CK(h, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device));
-    CK(h, cudaDeviceGetAttribute(&clusters, cudaDevAttrClusterLaunch, h->device));
-    if (!coop || !clusters) return refuse(h, DBS_E_ARG, "device without cooperative or cluster launch");
-    const int I = (int)((h->S + FLOW_IB - 1) / FLOW_IB);
-    const int creq = std::min(h->flow_creq > 0 ? h->flow_creq : FLOW_MAX_C, 16);
-    const void *k = flow_fn(h);
-    CK(h, cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    int q = std::max(1, (I + creq - 1) / creq), C = 0;
-    for (;; ++q) {
-        C = (I + q - 1) / q;
-        CK(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)flow_smem(q, C)));
-        cudaLaunchAttribute attr[2];
-        cudaLaunchConfig_t cfg = flow_config(h, q, C, attr);
-        int ncl = 0;
-        CK(h, cudaOccupancyMaxActiveClusters(&ncl, k, &cfg));
-        if (ncl >= I) break;
-        if (q >= I) return refuse(h, DBS_E_ARG, "cooperative path: grid does not fit the device");
+    CK(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    if (!coop) return refuse(h, DBS_E_ARG, "device without cooperative launch");
+    // tiny systems: one CTA holds all dumbbells and no record leaves it
+    int T = h->S <= FLOW_MAX_T ? FLOW_MAX_T : 1;
+    if (h->flow_creq > 0) {
+        T = 1;
+        while (2 * T <= std::min(h->flow_creq, FLOW_MAX_T)) T *= 2;
+    }
+    int G = 0;
+    for (;; T *= 2) {
+        if (T > FLOW_MAX_T) return refuse(h, DBS_E_ARG, "cooperative path: grid does not fit the device");
+        G = (int)((h->S + T - 1) / T);
+        if (G > sms) continue;
+        const void *k = flow_fn(h, T);
+        CK(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)flow_smem(G, T)));
+        int occ = 0;
+        CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, FLOW_NT, flow_smem(G, T)));
+        if ((int64_t)occ * sms >= G) break;
     }
     CK(h, cudaStreamSynchronize(h->stream));
     drop_flow(h);
-    const size_t spad = (size_t)I * FLOW_IB;
-    CK(h, cudaMalloc(&h->ll_rec, 2 * spad * 6 * sizeof(ulonglong2)));
-    CK(h, cudaMemsetAsync(h->ll_rec, 0, 2 * spad * 6 * sizeof(ulonglong2), h->stream));
-    h->flow_I = I;
-    h->flow_q = q;
-    h->flow_C = C;
+    const size_t words = 2 * (size_t)G * T * 6;
+    CK(h, cudaMalloc(&h->ll_rec, words * sizeof(ulonglong2)));
+    CK(h, cudaMemsetAsync(h->ll_rec, 0, words * sizeof(ulonglong2), h->stream));
+    h->flow_T = T;
+    h->flow_G = G;
     h->flow_base = 1;
     return DBS_OK;
 }
 
 static int coop_step(dbs_suspension *h, int64_t n)
 {
-    const size_t spad = (size_t)h->flow_I * FLOW_IB;
+    const size_t words = 2 * (size_t)h->flow_G * h->flow_T * 6;
     int64_t left = n;
     while (left > 0) {
         const int K = (int)std::min<int64_t>(left, FLOW_MAX_STEPS);
@@ -755,7 +756,7 @@ static int coop_step(dbs_suspension *h, int64_t n)
         if (rc) return rc;
         if (h->flow_base > 0xffffffffu - (unsigned)(2 * K + 2)) {
             // tags are about to wrap: clear the buffers so that no old tag can match
-            CK(h, cudaMemsetAsync(h->ll_rec, 0, 2 * spad * 6 * sizeof(ulonglong2), h->stream));
+            CK(h, cudaMemsetAsync(h->ll_rec, 0, words * sizeof(ulonglong2), h->stream));
             h->flow_base = 1;
         }
         const EvalArgs A = base_args(h);
@@ -763,16 +764,14 @@ static int coop_step(dbs_suspension *h, int64_t n)
         P.rec = h->ll_rec;
         P.pack = (DbF32 *)h->packA;
         P.n0 = h->n_host;
-        P.I = h->flow_I;
-        P.q = h->flow_q;
-        P.C = h->flow_C;
+        P.G = h->flow_G;
         P.K = K;
         P.base = h->flow_base;
         P.timeout_ns = 1000000000ull;
-        cudaLaunchAttribute attr[2];
-        const cudaLaunchConfig_t cfg = flow_config(h, h->flow_q, h->flow_C, attr);
+        cudaLaunchAttribute attr[1];
+        const cudaLaunchConfig_t cfg = flow_config(h, h->flow_G, h->flow_T, attr);
         void *args[] = {(void *)&A, (void *)&P};
-        cudaError_t e = cudaLaunchKernelExC(&cfg, flow_fn(h), args);
+        cudaError_t e = cudaLaunchKernelExC(&cfg, flow_fn(h, h->flow_T), args);
         if (e != cudaSuccess) return fail(h, DBS_E_CUDA, "cooperative launch: %s", cudaGetErrorString(e));
         h->flow_base += (unsigned)(2 * K + 1);
         h->n_host += K;
@@ -780,6 +779,7 @@ static int coop_step(dbs_suspension *h, int64_t n)
     }
     return DBS_OK;
 }
+
 
 extern "C" {
 
@@ -859,7 +859,9 @@ int dbs_mobility_apply(dbs_suspension *h, const double *F, double *v)
 int dbs_set_chunks(dbs_suspension *h, int32_t chunks)
 {
     GUARD(h);
-    const int64_t cmax = std::max<int64_t>(1, h->S / 8);
+    // grid path: at least 8 dumbbell records per chunk; cooperative path: the
+    // split request (j-chunks, or dumbbells per CTA) is at most 16
+    const int64_t cmax = h->path == DBS_PATH_COOP ? 16 : std::max<int64_t>(1, h->S / 8);
     if (chunks < 0 || chunks > cmax) return DBS_E_ARG;
     CK(h, cudaStreamSynchronize(h->stream));
     drop_graph(h);
@@ -888,9 +890,9 @@ int dbs_get_launch(dbs_suspension *h, int32_t *bt, int32_t *chunks, int32_t *gri
 {
     GUARD(h);
     const bool coop = h->path == DBS_PATH_COOP;
-    if (bt) *bt = coop ? FLOW_IB : h->bt;
-    if (chunks) *chunks = coop ? h->flow_C : h->chunks;
-    if (grid) *grid = coop ? h->flow_I * h->flow_C : h->grid;
+    if (bt) *bt = coop ? h->flow_T : h->bt;
+    if (chunks) *chunks = coop ? 1 : h->chunks;
+    if (grid) *grid = coop ? h->flow_G : h->grid;
     return DBS_OK;
 }
 

@@ -1,84 +1,45 @@
 // Cooperative dataflow kernel: K Heun steps of one small suspension in one
-// launch over all SMs, with no grid-wide barrier.
+// launch over up to one CTA per SM, one exchange per evaluation and no
+// grid-wide barrier.
 //
-// Work split.  Dumbbells form i-blocks of 32 (one per lane); q consecutive
-// i-blocks form a j-chunk; CTA (ib, c) sums, for the 32 targets of i-block ib,
-// the pair terms of Eq. (3b) over the records of chunk c.  Its W warps split
-// the chunk's records, and their sums are folded with FP32 two-sum.  The CTA
-// whose chunk holds its own i-block is the i-block's owner: it keeps the
-// dumbbells' state (FP64 positions, forces, Heun velocity, stroke-average
-// accumulators) in shared memory for the whole launch and runs the epilogue
-// (self term of Eq. (3a), Heun step of Sec. IV, spring force of Eq. (4),
-// record repack, stroke average).
+// Work split.  CTA g owns the T consecutive dumbbells [gT, gT + T) and, for
+// each evaluation, sums the pair terms of Eq. (3b) for its own 2T target
+// spheres over ALL S records: thread tid takes target t = tid / P and the
+// records r = (tid mod P) + P k (P = NT / T slices per target), so the
+// threads of a warp read different records (consecutive 48-byte records are
+// free of shared-memory bank conflicts for 16-byte loads).  The slice sums are
+// folded with FP32 two-sum, first across the lanes of a warp (shuffles), then
+// across the warps of a target in warp order, so no partial sum leaves the
+// CTA: the CTA then runs the epilogue of its dumbbells (self term of Eq. (3a),
+// Heun step of Sec. IV, spring force of Eq. (4), stroke average) and
+// publishes their next records.
 //
-// Exchange.  Records and partial sums travel through global memory as
-// flag-tagged 64-bit words (low half: the FP32 value, high half: the number of
-// the evaluation they belong to).  A naturally aligned 64-bit access is
-// single-copy atomic, so a reader that sees the expected tag in every word it
-// reads has the value of that evaluation: no fence, ticket or barrier sits on
-// the critical path.  Each evaluation:
-//   1. every CTA polls the records of its chunk (and, off the owner, the
-//      positions of its targets) for tag e, into shared memory;
-//   2. sweeps them (W warps, one record range each) and folds the W sums;
-//   3. the C CTAs of an i-block form one thread-block cluster: a non-owner
-//      writes its (sum, compensation) pairs, tagged the same way, straight
-//      into the owner's shared memory (DSMEM); the owner polls its own shared
-//      memory for the C-1 tags, folds all C pairs in chunk order, runs the
-//      epilogue and publishes the next records with tag e + 1.
-// Records and partials are double-buffered by the parity of e; the dependence
-// chain of the algorithm guarantees that a slot is rewritten only after every
-// reader of its previous contents is done (the owner's table of pairs needs
-// no second buffer: a non-owner can only start the next sweep once the owner
-// has published records it folded from this table).  Every wait is bounded
-// (global timer); a wait that runs out raises FLAG_TIMEOUT, the CTA stops
-// working but keeps to the protocol (no early exit, so no CTA leaves while a
-// cluster peer may still write its shared memory), and the others then give up
-// too: a launch always ends.
+// Exchange.  Records travel through global memory as tagged 64-bit words
+// (FP32 value, 32-bit evaluation tag; a naturally aligned 64-bit access is
+// single-copy atomic), double-buffered by evaluation parity.  Each evaluation
+// every CTA polls the S - T records it does not own into shared memory.  A
+// slot is rewritten (evaluation e + 2) only after its owner has finished
+// evaluation e + 1, which needed every CTA's records of e + 1, which each CTA
+// publishes only after it copied all records of evaluation e into shared
+// memory: no reader can still be reading the old contents.  Every wait is
+// bounded (global timer and the shared abort flag); a CTA whose wait runs
+// out raises FLAG_TIMEOUT and stops, the others then give up too.  No CTA
+// touches another CTA's shared memory, so a CTA may leave early.
 //
-// Precision (FP32C).  Pair sums as in eval_kernel (FP32 pair math, two-sum
-// across ranges).  Positions (relative to the suspension's centre) and the
-// stroke-average sums are FP64 and the Heun update is FP64.  An FP64
-// instruction holds its sub-partition for 64 cycles on this part, so the
-// owner spreads that work over three warps, one per axis, each on its own
-// sub-partition.  The rest length L and d^2 = |x_b - x_a|^2 (from the FP64
-// difference) are formed as unevaluated FP32 pairs hi + lo (double-single:
-// Dekker's two-sum and the FMA two-product), so the small stretch
-// d - L = (d^2 - L^2)/(d + L) keeps FP32 relative accuracy; the force and the
-// velocity are FP32, as in the records.
+// Precision (FP32C).  Pair sums in FP32 with two-sum folding, as in
+// eval_kernel.  Positions (relative to the suspension's centre), the Heun
+// update and the stroke-average sums are FP64.  An FP64 instruction holds its
+// sub-partition for 64 cycles on this part, so the epilogue spreads that work
+// over three warps, one per axis, each on its own sub-partition.  The rest
+// length L and d^2 = |x_b - x_a|^2 (from the FP64 difference) are formed as
+// unevaluated FP32 pairs hi + lo (double-single: Dekker's two-sum and the FMA
+// two-product), so the small stretch d - L = (d^2 - L^2)/(d + L) keeps FP32
+// relative accuracy; the force and the velocity are FP32, as in the records.
 #pragma once
-#include <cooperative_groups.h>
-
 #include "dbs_common.cuh"
 #include "eval_kernel.cuh"
 
 namespace dbs {
-
-constexpr int FLOW_IB = 32;  // dumbbells per i-block (one per lane)
-
-struct FlowArgs {
-    ulonglong2 *rec;   // tagged records [2][Spad][6]: word w holds record floats 2w, 2w+1
-    DbF32 *pack;       // plain records of the final state (the grid path's input)
-    int64_t n0;        // step number at launch
-    int I, q, C, K;    // i-blocks, i-blocks per chunk, chunks, Heun steps
-    unsigned base;     // tag of evaluation 0
-    unsigned long long timeout_ns;
-};
-
-// Owner state of one i-block, in shared memory (component-major: lane d reads
-// column d).  Positions are relative to the centre; all pairs are double-single.
-struct FlowOwner {
-    double x[6][FLOW_IB];                   // x - centre, spheres 2s (0..2) and 2s+1 (3..5)
-    double R[3][FLOW_IB];                   // stroke-average sums (trapezoid rule)
-    float lamh[FLOW_IB], laml[FLOW_IB], sph[FLOW_IB], spl[FLOW_IB], cph[FLOW_IB], cpl[FLOW_IB];
-    float F[6][FLOW_IB];                    // force at the current evaluation point
-    float v0[6][FLOW_IB];                   // Heun predictor velocity
-    float fext[6][FLOW_IB];
-    float z[6][FLOW_IB];                    // additive-noise normals of the current step
-    float2 e[3][FLOW_IB];                   // x_b - x_a per axis (double-single)
-    float2 ee[3][FLOW_IB];                  // its square (double-single)
-    float2 L[FLOW_IB], L2[FLOW_IB];         // rest length at t_{n+1} and its square
-    float f[FLOW_IB];                       // k0 (d - L) / d
-};
 
 __device__ __forceinline__ ulonglong2 ld_tagged(const ulonglong2 *p)
 {
@@ -210,317 +171,245 @@ __device__ __forceinline__ void publish_record(ulonglong2 *dst, const float r[12
     for (int w = 0; w < 6; ++w) st_tagged(dst + w, r[2 * w], r[2 * w + 1], tag);
 }
 
-// A tagged pair into the shared memory of cluster rank `rank` (the local
-// address `local` mapped there).
-__device__ __forceinline__ void st_tagged_peer(const void *local, unsigned rank, float a, float b,
-                                               unsigned tag)
+__device__ __forceinline__ bool finite_f(float v) { return ((__float_as_uint(v) >> 23) & 0xffu) != 0xffu; }
+
+constexpr int FLOW_NT = 256;      // threads per CTA (8 warps)
+constexpr int FLOW_POLL = 16;     // tagged words polled per thread per round
+
+struct FlowArgs {
+    ulonglong2 *rec;   // tagged records [2][Spad][6]: word w holds record floats 2w, 2w+1
+    DbF32 *pack;       // plain records of the final state (the grid path's input)
+    int64_t n0;        // step number at launch
+    int G, K;          // CTAs (owners of T dumbbells each), Heun steps
+    unsigned base;     // tag of evaluation 0
+    unsigned long long timeout_ns;
+};
+
+// State of the T owned dumbbells, component-major (lane d reads column d).
+template <int T>
+struct FlowOwner {
+    double x[6][T];                   // x - centre, spheres 2s (0..2) and 2s+1 (3..5)
+    double R[3][T];                   // stroke-average sums (trapezoid rule)
+    float lamh[T], laml[T], sph[T], spl[T], cph[T], cpl[T];
+    float F[6][T];                    // force at the current evaluation point
+    float v0[6][T];                   // Heun predictor velocity
+    float fext[6][T];
+    float z[6][T];                    // additive-noise normals of the current step
+    float2 ee[3][T];                  // (x_b - x_a)^2 per axis (double-single)
+    float2 L[T], L2[T];               // rest length at t_{n+1} and its square
+    float2 u[6][T];                   // folded pair sums (sum, compensation)
+};
+
+// (s, c) += (s2, c2) with Knuth's two-sum on the sums (exact error, any order).
+__device__ __forceinline__ void ts_merge(float &s, float &c, float s2, float c2)
 {
-    unsigned r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
-                 : "=r"(r) : "r"((unsigned)__cvta_generic_to_shared(local)), "r"(rank));
-    const unsigned long long hi = (unsigned long long)tag << 32;
-    asm volatile("st.relaxed.cluster.shared::cluster.v2.u64 [%0], {%1, %2};" ::"r"(r),
-                 "l"(hi | __float_as_uint(a)), "l"(hi | __float_as_uint(b))
-                 : "memory");
+    const float t = s + s2;
+    const float z = t - s;
+    c += c2 + ((s - (t - z)) + (s2 - z));
+    s = t;
 }
 
-__device__ __forceinline__ ulonglong2 ld_tagged_local(const ulonglong2 *p)
-{
-    ulonglong2 v;
-    asm volatile("ld.relaxed.cluster.shared::cta.v2.u64 {%0, %1}, [%2];"
-                 : "=l"(v.x), "=l"(v.y) : "r"((unsigned)__cvta_generic_to_shared(p)) : "memory");
-    return v;
-}
-
-// The three normals of one sphere at step n into z[0], z[32], z[64] (kept out of
-// line: the kernel's per-evaluation code stays short).
+// The three normals of one sphere at step n into z[0], z[stride], z[2 stride]
+// (out of line: the per-evaluation code stays short).
 __device__ __noinline__ void draw_sphere_normals(unsigned long long seed, int64_t n, int64_t sphere,
-                                                 float *z)
+                                                   float *z, int stride)
 {
     float w[3];
     sphere_normals(seed, n, sphere, w);
     z[0] = w[0];
-    z[FLOW_IB] = w[1];
-    z[2 * FLOW_IB] = w[2];
+    z[stride] = w[1];
+    z[2 * stride] = w[2];
 }
 
-__device__ __forceinline__ bool finite_f(float v) { return ((__float_as_uint(v) >> 23) & 0xffu) != 0xffu; }
-
-template <int W>
-struct FlowMinBlocks { static constexpr int value = W <= 4 ? 4 : (W <= 8 ? 2 : 1); };
-
-// NOISE: additive Brownian noise on (a separate instantiation, so that the
-// deterministic kernel carries none of its code).
-template <int MOB, int W, bool NOISE>
-__global__ void __launch_bounds__(32 * W, FlowMinBlocks<W>::value)
-flow_kernel(const EvalArgs A, const FlowArgs P)
+// NOISE: additive Brownian noise on (a separate instantiation).
+template <int MOB, int T, bool NOISE>
+__global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, const FlowArgs P)
 {
-    constexpr int NT = 32 * W;
-    namespace cg = cooperative_groups;
-    // dynamic: the chunk's records (q x 32 DbF32), then the owner's table of
-    // tagged chunk pairs [C][6][32]
-    extern __shared__ float4 flow_smem[];
-    __shared__ FlowOwner own;
-    __shared__ float red[W][6][FLOW_IB];
-    __shared__ float2 pairs[6][FLOW_IB];    // owner: the C pairs folded
-    __shared__ float tgt[FLOW_IB][6];       // non-owner: target positions (x0 x1 y0 y1 z0 z1)
+    constexpr int NT = FLOW_NT;
+    constexpr int PS = NT / T;                 // slices (threads) per target dumbbell
+    constexpr int LW = PS < 32 ? PS : 32;      // lanes of one target within a warp
+    constexpr int WPT = PS > 32 ? PS / 32 : 1; // warps per target
+    extern __shared__ float4 flow_smem[];     // all S records (Spad x DbF32)
+    __shared__ FlowOwner<T> own;
+    __shared__ float2 red[NT / 32][6];         // per-warp folded sums (WPT > 1)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int ib = blockIdx.x / P.C, c = blockIdx.x - ib * P.C;
-    const int c_own = ib / P.q;
-    const bool owner = (c == c_own);
+    const int g = blockIdx.x;
     const int S = (int)A.S;
-    const int Spad = P.I * FLOW_IB;
-    const int s = ib * FLOW_IB + lane;
-    const bool active = s < S;
-    const int g_ib0 = ib * FLOW_IB;   // first dumbbell of the i-block
-    const int db = c * P.q * FLOW_IB;
-    const int m = min(db + P.q * FLOW_IB, S) - db;    // records in the chunk
-    const int own_off = ib * FLOW_IB - db;           // owner: own i-block's place in the tile
-    const int n_ib = min(FLOW_IB, S - ib * FLOW_IB);  // dumbbells of i-block ib
+    const int Spad = P.G * T;
+    const int st0 = g * T;                     // first owned dumbbell
+    const int nown = min(T, S - st0);          // owned dumbbells (the last CTA may hold fewer)
     DbF32 *tile = (DbF32 *)flow_smem;
-    ulonglong2 *ptab = (ulonglong2 *)(tile + P.q * FLOW_IB);
     const float k8 = A.inv8pimu_f;
     const float inv6 = (float)A.inv6pimua, k0f = (float)A.k0;
     const double cen[3] = {A.cx, A.cy, A.cz};
     const ds ell = ds_of(A.ell);
-    cg::cluster_group cluster = cg::this_cluster();   // the C CTAs of i-block ib, rank c
-    // The exchange addresses cluster ranks 0..C-1: a launch without that shape
-    // (one the host did not make) must not touch a peer's shared memory.  The
-    // shape is the same for every CTA, so all of them leave here together.
-    if (cluster.num_blocks() != (unsigned)P.C || cluster.block_rank() != (unsigned)c ||
-        gridDim.x != (unsigned)(P.I * P.C)) {
+    if (gridDim.x != (unsigned)P.G || blockDim.x != (unsigned)NT) {   // not the shape the host made
         if (tid == 0) atomicOr(A.flags, FLAG_LAUNCH);
         return;
     }
-    for (int i = tid; i < P.C * 6 * FLOW_IB; i += NT) ptab[i] = make_ulonglong2(0ull, 0ull);  // no tag is 0
-    cluster.sync();   // every CTA of the cluster runs, and its table is clear, before a peer writes it
 
-    // ---- owner: load the state, publish the records of evaluation 0 ----------
-    if (owner && warp == 0 && active) {
+    // ---- load the owned state, publish the records of evaluation 0 -----------
+    if (warp == 0 && lane < nown) {
+        const int d = lane, s = st0 + d;
         const int64_t o = 6 * (int64_t)s;
         float r[12];
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            own.x[k][lane] = A.x[o + k] - cen[k % 3];
-            own.F[k][lane] = (float)A.Fd[o + k];
-            own.fext[k][lane] = A.Fext ? (float)A.Fext[o + k] : 0.f;
+            own.x[k][d] = A.x[o + k] - cen[k % 3];
+            own.F[k][d] = (float)A.Fd[o + k];
+            own.fext[k][d] = A.Fext ? (float)A.Fext[o + k] : 0.f;
         }
         ds t = ds_of(A.lam[s]);
-        own.lamh[lane] = t.h; own.laml[lane] = t.l;
+        own.lamh[d] = t.h; own.laml[d] = t.l;
         t = ds_of(A.sinphi[s]);
-        own.sph[lane] = t.h; own.spl[lane] = t.l;
+        own.sph[d] = t.h; own.spl[d] = t.l;
         t = ds_of(A.cosphi[s]);
-        own.cph[lane] = t.h; own.cpl[lane] = t.l;
+        own.cph[d] = t.h; own.cpl[d] = t.l;
         if (A.avg_m > 0) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) own.R[k][lane] = A.Racc[3 * (int64_t)s + k];
+            for (int k = 0; k < 3; ++k) own.R[k][d] = A.Racc[3 * (int64_t)s + k];
         }
-        r[0] = (float)own.x[0][lane]; r[1] = (float)own.x[3][lane]; r[2] = (float)own.x[1][lane];
-        r[3] = (float)own.x[4][lane]; r[4] = (float)own.x[2][lane]; r[5] = (float)own.x[5][lane];
-        r[6] = own.F[0][lane] * k8; r[7] = own.F[3][lane] * k8; r[8] = own.F[1][lane] * k8;
-        r[9] = own.F[4][lane] * k8; r[10] = own.F[2][lane] * k8; r[11] = own.F[5][lane] * k8;
-        put_record(tile + own_off + lane, r);
+        r[0] = (float)own.x[0][d]; r[1] = (float)own.x[3][d]; r[2] = (float)own.x[1][d];
+        r[3] = (float)own.x[4][d]; r[4] = (float)own.x[2][d]; r[5] = (float)own.x[5][d];
+        r[6] = own.F[0][d] * k8; r[7] = own.F[3][d] * k8; r[8] = own.F[1][d] * k8;
+        r[9] = own.F[4][d] * k8; r[10] = own.F[2][d] * k8; r[11] = own.F[5][d] * k8;
+        put_record(tile + s, r);
         publish_record(P.rec + (size_t)s * 6, r, P.base);
     }
-
-    // words polled in step 1: the chunk's records (own i-block excepted on the
-    // owner), then, off the owner, the targets' positions (3 words each)
-    const int n_chunk = (m - (owner ? n_ib : 0)) * 6;
-    const int n_words = n_chunk + (owner ? 0 : 3 * n_ib);
     const float2 c2 = make_float2(A.c2, A.c2), c3 = make_float2(A.c3, A.c3);
+    const int nwords = 6 * S;
+    const int own_w0 = 6 * st0, own_w1 = 6 * (st0 + nown);   // words not polled (own records)
+    const int t_me = tid / PS, sl = tid - t_me * PS;         // sweep: target and slice
+    const int s_me = st0 + t_me;
+    const bool act = t_me < nown;
 
-    bool dead = false;   // a wait ran out: stop working, keep the protocol
-    for (int ev = 0; ev < 2 * P.K; ++ev) {
+    bool dead = false;
+    for (int ev = 0; ev < 2 * P.K && !dead; ++ev) {
         const unsigned tag = P.base + (unsigned)ev;
         const int par = ev & 1;
         const bool corr = (ev & 1) != 0;
         const int64_t n = P.n0 + (ev >> 1);
         const ulonglong2 *R = P.rec + (size_t)par * Spad * 6;
         float4 trig = make_float4(0.f, 0.f, 1.f, 0.f);
-        if (owner && warp == 3) trig = A.trig_df[(n + 1) & A.trig_mask];   // rest length, epilogue warp 3
+        if (warp == 3) trig = A.trig_df[(n + 1) & A.trig_mask];   // rest length (epilogue warp 3)
 
-        // 1. poll the words of this evaluation, up to 8 per thread in flight
-        bool ok = !dead;
-        for (int b0 = 0; b0 < n_words && ok; b0 += 8 * NT) {
-            const ulonglong2 *pp[8];
+        // the normals of step n, drawn once (predictor) by the last 2T threads while
+        // the other CTAs' records are on their way
+        if (NOISE && !corr) {
+            const int q = tid - (NT - 2 * T);
+            if (q >= 0) {
+                const int d = q >> 1, h = q & 1;
+                if (d < nown)
+                    draw_sphere_normals(A.noise_seed, n, 2 * ((int64_t)st0 + d) + h, &own.z[3 * h][d], T);
+            }
+        }
+
+        // 1. poll the S - T records this CTA does not own, FLOW_POLL words per
+        // thread in flight, into shared memory
+        bool ok = true;
+        for (int b0 = 0; b0 < nwords && ok; b0 += FLOW_POLL * NT) {
+            const ulonglong2 *pp[FLOW_POLL];
             unsigned pend = 0;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            for (int j = 0; j < FLOW_POLL; ++j) {
                 const int idx = b0 + j * NT + tid;
                 pp[j] = R;
-                if (idx < n_chunk) {
-                    const int jj = idx / 6, w = idx - jj * 6;
-                    const int jr = (owner && jj >= own_off) ? jj + n_ib : jj;
-                    pp[j] = R + (size_t)(db + jr) * 6 + w;
-                    pend |= 1u << j;
-                } else if (idx < n_words) {
-                    const int t = idx - n_chunk, d = t / 3, w = t - d * 3;
-                    pp[j] = R + (size_t)(ib * FLOW_IB + d) * 6 + w;
+                if (idx < nwords && (idx < own_w0 || idx >= own_w1)) {
+                    pp[j] = R + idx;
                     pend |= 1u << j;
                 }
             }
-            ulonglong2 v[8];
-            ok = wait_batch<8>(pp, pend, tag, v, A.flags, P.timeout_ns);
+            ulonglong2 v[FLOW_POLL];
+            ok = wait_batch<FLOW_POLL>(pp, pend, tag, v, A.flags, P.timeout_ns);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            for (int j = 0; j < FLOW_POLL; ++j) {
                 if (!((pend >> j) & 1u)) continue;
-                const int idx = b0 + j * NT + tid;
-                float *dst;
-                if (idx < n_chunk) {
-                    const int jj = idx / 6, w = idx - jj * 6;
-                    const int jr = (owner && jj >= own_off) ? jj + n_ib : jj;
-                    dst = (float *)(tile + jr) + 2 * w;
-                } else {
-                    const int t = idx - n_chunk, d = t / 3, w = t - d * 3;
-                    dst = &tgt[d][2 * w];
-                }
+                float *dst = (float *)tile + 2 * (b0 + j * NT + tid);   // word w = floats 2w, 2w+1
                 dst[0] = lo_float(v[j].x);
                 dst[1] = lo_float(v[j].y);
             }
         }
         dead = __syncthreads_or(!ok);
+        if (dead) break;
 
-        // 2. sweep: warp `warp` takes records [j0, j1) of the chunk
+        // 2. sweep: target t_me against records sl, sl + PS, ... (self pair masked)
         float2 qa[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         float2 qb[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        if (active && !dead) {
-            float p[6];
-            if (owner) {
-                const float4 a4 = tile[own_off + lane].a, b4 = tile[own_off + lane].b;
-                p[0] = a4.x; p[1] = a4.y; p[2] = a4.z; p[3] = a4.w; p[4] = b4.x; p[5] = b4.y;
-            } else {
-#pragma unroll
-                for (int k = 0; k < 6; ++k) p[k] = tgt[lane][k];
-            }
-            const float2 pax = make_float2(p[0], p[0]), pay = make_float2(p[2], p[2]);
-            const float2 paz = make_float2(p[4], p[4]), pbx = make_float2(p[1], p[1]);
-            const float2 pby = make_float2(p[3], p[3]), pbz = make_float2(p[5], p[5]);
-            const int j0 = (m * warp) / W, j1 = (m * (warp + 1)) / W;
+        if (act) {
+            const float4 a4 = tile[s_me].a, b4 = tile[s_me].b;
+            const float2 pax = make_float2(a4.x, a4.x), pay = make_float2(a4.z, a4.z);
+            const float2 paz = make_float2(b4.x, b4.x), pbx = make_float2(a4.y, a4.y);
+            const float2 pby = make_float2(a4.w, a4.w), pbz = make_float2(b4.y, b4.y);
             float r2min = 3.0e38f;
-            if (!owner) {
 #pragma unroll 2
-                for (int k = j0; k < j1; ++k) {
-                    const float4 ra = tile[k].a, rb = tile[k].b, rc = tile[k].c;
-                    const float2 jx = make_float2(ra.x, ra.y), jy = make_float2(ra.z, ra.w);
-                    const float2 jz = make_float2(rb.x, rb.y), gx = make_float2(rb.z, rb.w);
-                    const float2 gy = make_float2(rc.x, rc.y), gz = make_float2(rc.z, rc.w);
-                    pair2<MOB, false, false>(pax, pay, paz, jx, jy, jz, gx, gy, gz, c2, c3, qa[0], qa[1],
-                                      qa[2], r2min, false, false);
-                    pair2<MOB, false, false>(pbx, pby, pbz, jx, jy, jz, gx, gy, gz, c2, c3, qb[0], qb[1],
-                                      qb[2], r2min, false, false);
-                }
-            } else {
-                // the owner's chunk holds its own dumbbells: mask the self pairs
-                for (int k = j0; k < j1; ++k) {
-                    const float4 ra = tile[k].a, rb = tile[k].b, rc = tile[k].c;
-                    const float2 jx = make_float2(ra.x, ra.y), jy = make_float2(ra.z, ra.w);
-                    const float2 jz = make_float2(rb.x, rb.y), gx = make_float2(rb.z, rb.w);
-                    const float2 gy = make_float2(rc.x, rc.y), gz = make_float2(rc.z, rc.w);
-                    const bool self = (db + k == s);
-                    pair2<MOB, true>(pax, pay, paz, jx, jy, jz, gx, gy, gz, c2, c3, qa[0], qa[1],
-                                     qa[2], r2min, self, false);
-                    pair2<MOB, true>(pbx, pby, pbz, jx, jy, jz, gx, gy, gz, c2, c3, qb[0], qb[1],
-                                     qb[2], r2min, false, self);
-                }
+            for (int k = sl; k < S; k += PS) {
+                const float4 ra = tile[k].a, rb = tile[k].b, rc = tile[k].c;
+                const float2 jx = make_float2(ra.x, ra.y), jy = make_float2(ra.z, ra.w);
+                const float2 jz = make_float2(rb.x, rb.y), gx = make_float2(rb.z, rb.w);
+                const float2 gy = make_float2(rc.x, rc.y), gz = make_float2(rc.z, rc.w);
+                const bool self = (k == s_me);
+                pair2<MOB, true>(pax, pay, paz, jx, jy, jz, gx, gy, gz, c2, c3, qa[0], qa[1], qa[2],
+                                 r2min, self, false);
+                pair2<MOB, true>(pbx, pby, pbz, jx, jy, jz, gx, gy, gz, c2, c3, qb[0], qb[1], qb[2],
+                                 r2min, false, self);
             }
             if (MOB == 1 && r2min < A.overlap_r2) atomicOr(A.flags, FLAG_OVERLAP);
         }
+
+        // 3. fold the slices of each target: FP32 two-sum across the LW lanes of a
+        // warp (butterfly: every lane ends with the same pair), then across the
+        // WPT warps of a target in warp order
+        float sv[6], cv[6];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            red[warp][k][lane] = qa[k].x + qa[k].y;
-            red[warp][3 + k][lane] = qb[k].x + qb[k].y;
+            sv[k] = qa[k].x + qa[k].y;
+            sv[3 + k] = qb[k].x + qb[k].y;
+            cv[k] = 0.f;
+            cv[3 + k] = 0.f;
+        }
+#pragma unroll
+        for (int off = LW / 2; off >= 1; off >>= 1) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const float s2 = __shfl_xor_sync(0xffffffffu, sv[k], off);
+                const float cc2 = __shfl_xor_sync(0xffffffffu, cv[k], off);
+                ts_merge(sv[k], cv[k], s2, cc2);
+            }
+        }
+        if (WPT == 1) {
+            if (sl == 0) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) own.u[k][t_me] = make_float2(sv[k], cv[k]);
+            }
+        } else {
+            if (lane == 0) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) red[warp][k] = make_float2(sv[k], cv[k]);
+            }
+            __syncthreads();
+            if (tid < 6 * T) {
+                const int t = tid % T, k = tid / T;
+                float2 acc = red[t * WPT][k];
+#pragma unroll
+                for (int w = 1; w < WPT; ++w) ts_merge(acc.x, acc.y, red[t * WPT + w][k].x, red[t * WPT + w][k].y);
+                own.u[k][t] = acc;
+            }
         }
         __syncthreads();
 
-        // 3a. fold the W warp sums into this chunk's pair; a non-owner writes
-        // it, tagged, into the owner's table through DSMEM and is done
-        float2 mine0 = {0.f, 0.f}, mine1 = {0.f, 0.f};   // owner: its own pairs (items tid, tid + NT)
-        for (int it = tid, j = 0; it < 6 * FLOW_IB; it += NT, ++j) {
-            const int k = it >> 5, d = it & 31;
-            if (d >= n_ib || dead) continue;
-            float sum = red[0][k][d], cmp = 0.f;
-#pragma unroll
-            for (int w = 1; w < W; ++w) two_sum_acc(sum, cmp, red[w][k][d]);
-            if (owner) (j == 0 ? mine0 : mine1) = make_float2(sum, cmp);
-            else st_tagged_peer(&ptab[(c * 6 + k) * FLOW_IB + d], (unsigned)c_own, sum, cmp, tag);
-        }
-        if (!owner) continue;
-
-        // the normals of step n, drawn once (predictor) by the threads that have
-        // no pair to poll, for the 2 x 32 spheres of the i-block
-        if (NOISE && !corr) {
-            for (int q = tid - (NT >= 256 ? 6 * FLOW_IB : 0); q >= 0 && q < 2 * FLOW_IB;
-                 q += (NT >= 256 ? 2 * FLOW_IB : NT)) {
-                const int d = q >> 1, h = q & 1;
-                if (d < n_ib)
-                    draw_sphere_normals(A.noise_seed, n, 2 * ((int64_t)g_ib0 + d) + h, &own.z[3 * h][d]);
-            }
-        }
-
-        // 3b. owner: the other chunks' pairs, polled in its own shared memory
-        // (all loads of a round in flight together), folded in chunk order
-        ok = !dead;
-        for (int it = tid, j = 0; it < 6 * FLOW_IB && ok; it += NT, ++j) {
-            const int k = it >> 5, d = it & 31;
-            if (d >= n_ib) continue;
-            float sum = 0.f, cmp = 0.f;
-            for (int cb = 0; cb < P.C && ok; cb += 8) {
-                ulonglong2 v[8];
-                unsigned pend = 0;
-#pragma unroll
-                for (int q8 = 0; q8 < 8; ++q8)
-                    if (cb + q8 < P.C && cb + q8 != c) pend |= 1u << q8;
-                unsigned long long t0 = 0;   // read the global timer only once a wait begins
-                for (unsigned round = 0; pend; ++round) {
-#pragma unroll
-                    for (int q8 = 0; q8 < 8; ++q8)
-                        if ((pend >> q8) & 1u) v[q8] = ld_tagged_local(&ptab[((cb + q8) * 6 + k) * FLOW_IB + d]);
-#pragma unroll
-                    for (int q8 = 0; q8 < 8; ++q8)
-                        if (((pend >> q8) & 1u) && tagged(v[q8], tag)) pend &= ~(1u << q8);
-                    if (pend && round == 0) t0 = flow_ns();
-                    if (pend && (round & 63u) == 63u) {
-                        if ((*(volatile int *)A.flags & FLAG_TIMEOUT) || flow_ns() - t0 > P.timeout_ns) {
-                            atomicOr(A.flags, FLAG_TIMEOUT);
-                            ok = false;
-                            break;
-                        }
-                    }
-                }
-#pragma unroll
-                for (int q8 = 0; q8 < 8; ++q8) {
-                    const int cc = cb + q8;
-                    if (cc < P.C) {
-                        const float2 mp = j == 0 ? mine0 : mine1;
-                        const float ps = cc == c ? mp.x : lo_float(v[q8].x);
-                        const float pc = cc == c ? mp.y : lo_float(v[q8].y);
-                        if (cc == 0) {
-                            sum = ps;
-                            cmp = pc;
-                        } else {
-                            two_sum_acc(sum, cmp, ps);
-                            cmp += pc;
-                        }
-                    }
-                }
-            }
-            pairs[k][d] = make_float2(sum, cmp);
-        }
-        dead = __syncthreads_or(!ok);
-
-        // 3c. owner epilogue.  Warps 0-2 take axis a = warp of the i-block's
-        // dumbbells (lane d): self term of Eq. (3a), FP64 Heun update of both
-        // spheres (Sec. IV), the axis component of e = x_b - x_a; warp 3 the rest
-        // length L(t_{n+1}) of Eq. (4).  Then warp 0 the spring magnitude, and
-        // warps 0-2 the forces, records and their publication.
+        // 4. epilogue.  Warps 0-2 take axis a = warp of the owned dumbbells (lane d):
+        // self term of Eq. (3a), FP64 Heun update of both spheres (Sec. IV), the
+        // axis component of e = x_b - x_a; warp 3 the rest length L(t_{n+1}) of
+        // Eq. (4).  Then each axis warp forms the spring magnitude (the same
+        // value in the three warps, which saves a barrier), its force component,
+        // and writes and publishes its record words.
         const int a = warp, d = lane;
-        const bool eax = warp < 3 && active && !dead;
-        float pa = 0.f, pb = 0.f;   // record positions along a (FP32, centre-relative)
-        float eh = 0.f;
+        const bool eax = warp < 3 && d < nown;
+        float pa = 0.f, pb = 0.f, eh = 0.f;
         if (eax) {
-            const float va = fmaf(own.F[a][d], inv6, pairs[a][d].x + pairs[a][d].y);           // Eq. (3a)
-            const float vb = fmaf(own.F[a + 3][d], inv6, pairs[a + 3][d].x + pairs[a + 3][d].y);
+            const float va = fmaf(own.F[a][d], inv6, own.u[a][d].x + own.u[a][d].y);           // Eq. (3a)
+            const float vb = fmaf(own.F[a + 3][d], inv6, own.u[a + 3][d].x + own.u[a + 3][d].y);
             double xa = own.x[a][d], xb = own.x[a + 3][d];
             if (!corr) {
                 own.v0[a][d] = va;
@@ -542,7 +431,6 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
             if (!(finite1(xa) && finite1(xb))) atomicOr(A.flags, FLAG_NONFINITE);
             const ds e = ds_of(xb - xa);
             const ds e2 = ds_mul(e, e);
-            own.e[a][d] = make_float2(e.h, e.l);
             own.ee[a][d] = make_float2(e2.h, e2.l);
             eh = e.h;
             pa = (float)xa;
@@ -556,7 +444,7 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
                     if ((k_local % A.avg_m) == 0) {
                         acc += 0.5 * Rt;
                         const int64_t kidx = k_local / A.avg_m - 1;
-                        if (kidx < A.avg_maxk) A.Rbar[kidx * 3 * A.S + 3 * (int64_t)s + a] = acc / (double)A.avg_m;
+                        if (kidx < A.avg_maxk) A.Rbar[kidx * 3 * A.S + 3 * (int64_t)(st0 + d) + a] = acc / (double)A.avg_m;
                         acc = 0.5 * Rt;
                     } else {
                         acc += Rt;
@@ -564,7 +452,7 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
                     own.R[a][d] = acc;
                 }
             }
-        } else if (warp == 3 && active && !dead) {
+        } else if (warp == 3 && d < nown) {
             const ds sarg = ds_add(ds_mul({trig.x, trig.y}, {own.cph[d], own.cpl[d]}),
                                    ds_mul({trig.z, trig.w}, {own.sph[d], own.spl[d]}));
             const ds L = ds_add(ell, ds_mul({own.lamh[d], own.laml[d]}, sarg));
@@ -573,22 +461,19 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
             own.L2[d] = make_float2(L2.h, L2.l);
         }
         __syncthreads();
-        if (warp == 0 && active && !dead) {
+        if (eax) {
             // Eq. (4): F_a = k0 (d - L) e/d with d - L = (d^2 - L^2)/(d + L)
             const ds dd = ds_add(ds_add({own.ee[0][d].x, own.ee[0][d].y}, {own.ee[1][d].x, own.ee[1][d].y}),
                                  {own.ee[2][d].x, own.ee[2][d].y});
             const ds st2 = ds_add(dd, ds_neg({own.L2[d].x, own.L2[d].y}));
             const float rd = rsqrtf(dd.h);
-            own.f[d] = k0f * __fdividef((st2.h + st2.l) * rd, dd.h * rd + own.L[d].x);
-        }
-        __syncthreads();
-        if (eax) {
-            const float f = own.f[d];
+            const float f = k0f * __fdividef((st2.h + st2.l) * rd, dd.h * rd + own.L[d].x);
             const float Fa = fmaf(f, eh, own.fext[a][d]), Fb = fmaf(-f, eh, own.fext[a + 3][d]);
             own.F[a][d] = Fa;
             own.F[a + 3][d] = Fb;
             const float2 wp = make_float2(pa, pb), wg = make_float2(Fa * k8, Fb * k8);
-            float2 *tr = (float2 *)(tile + own_off + d);
+            const int s = st0 + d;
+            float2 *tr = (float2 *)(tile + s);
             tr[a] = wp;            // record word a: positions along a
             tr[3 + a] = wg;        // record word 3 + a: G along a
             if (ev + 1 < 2 * P.K) {
@@ -601,24 +486,26 @@ flow_kernel(const EvalArgs A, const FlowArgs P)
                 pk[3 + a] = wg;
             }
         }
-        __syncthreads();  // the tile's own records are complete before the next sweep
+        // no barrier here: the next poll writes only records this CTA does not own,
+        // and the next sweep starts after the poll's barrier
     }
-    cluster.sync();   // no CTA leaves while a peer may still write its shared memory
 
-    // ---- owner: write the state back ------------------------------------------
-    if (owner && warp == 0 && active) {
+    // ---- write the owned state back ----------------------------------------------
+    __syncthreads();
+    if (warp == 0 && lane < nown) {
+        const int d = lane, s = st0 + d;
         const int64_t o = 6 * (int64_t)s;
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            A.x[o + k] = own.x[k][lane] + cen[k % 3];
-            A.Fd[o + k] = (double)own.F[k][lane];
+            A.x[o + k] = own.x[k][d] + cen[k % 3];
+            A.Fd[o + k] = (double)own.F[k][d];
         }
         if (A.avg_m > 0) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) A.Racc[3 * (int64_t)s + k] = own.R[k][lane];
+            for (int k = 0; k < 3; ++k) A.Racc[3 * (int64_t)s + k] = own.R[k][d];
         }
     }
-    if (blockIdx.x == 0 && tid == 0) *A.step = P.n0 + P.K;
+    if (g == 0 && tid == 0) *A.step = P.n0 + P.K;
 }
 
 // Test of the bounded wait: polls a word that nothing writes.

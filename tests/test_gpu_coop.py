@@ -5,7 +5,8 @@
 * It ends where the grid path ends, to well inside the oracle tolerance (its
   spring force and Heun average are FP32, the grid path's FP64; both keep FP64
   positions).
-* Every j-chunk count (1 .. one chunk per i-block) gives the same trajectory.
+* Every split request (dumbbells per CTA, 1 .. 16; raised where the grid
+  would not fit the SMs) gives the same trajectory.
 * Runs longer than one launch (1024 steps) and than the clock ring (4096 steps)
   continue the clock and the step counter; stroke averages accumulated on the
   cooperative path match the oracle's.
@@ -77,7 +78,8 @@ def test_coop_long_run_crosses_launches_and_clock_ring():
     assert np.abs(xc - xg).max() <= 1e-5 * s.ell
 
 
-@pytest.mark.parametrize("S,chunks", [(100, 1), (100, 2), (100, 4), (700, 3), (700, 22), (2048, 5)])
+@pytest.mark.parametrize("S,chunks", [(100, 1), (100, 2), (100, 4), (100, 16), (700, 3), (700, 8),
+                                      (700, 16), (2048, 5)])
 def test_coop_chunk_counts_agree(S, chunks):
     s = inputs.paper_scale(S, seed=9)
     nsteps = 200
