@@ -39,7 +39,13 @@
 #include "dbs_common.cuh"
 #include "eval_kernel.cuh"
 
+#ifndef DBS_FLOW_UNROLL
+#define DBS_FLOW_UNROLL 4
+#endif
+
 namespace dbs {
+
+constexpr int kFlowUnroll = DBS_FLOW_UNROLL;   // unroll of the sweep over a thread's records
 
 __device__ __forceinline__ ulonglong2 ld_tagged(const ulonglong2 *p)
 {
@@ -197,7 +203,6 @@ struct FlowOwner {
     float z[6][T];                    // additive-noise normals of the current step
     float2 ee[3][T];                  // (x_b - x_a)^2 per axis (double-single)
     float2 L[T], L2[T];               // rest length at t_{n+1} and its square
-    float2 u[6][T];                   // folded pair sums (sum, compensation)
 };
 
 // (s, c) += (s2, c2) with Knuth's two-sum on the sums (exact error, any order).
@@ -231,7 +236,7 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
     constexpr int WPT = PS > 32 ? PS / 32 : 1; // warps per target
     extern __shared__ float4 flow_smem[];     // all S records (Spad x DbF32)
     __shared__ FlowOwner<T> own;
-    __shared__ float2 red[NT / 32][6];         // per-warp folded sums (WPT > 1)
+    __shared__ float2 red[WPT == 1 ? T : NT / 32][6];   // folded sums per (target, warp)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = blockIdx.x;
@@ -342,7 +347,7 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
             const float2 paz = make_float2(b4.x, b4.x), pbx = make_float2(a4.y, a4.y);
             const float2 pby = make_float2(a4.w, a4.w), pbz = make_float2(b4.y, b4.y);
             float r2min = 3.0e38f;
-#pragma unroll 2
+#pragma unroll kFlowUnroll
             for (int k = sl; k < S; k += PS) {
                 const float4 ra = tile[k].a, rb = tile[k].b, rc = tile[k].c;
                 const float2 jx = make_float2(ra.x, ra.y), jy = make_float2(ra.z, ra.w);
@@ -377,24 +382,10 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
                 ts_merge(sv[k], cv[k], s2, cc2);
             }
         }
-        if (WPT == 1) {
-            if (sl == 0) {
+        // one pair per (target, warp): the epilogue folds the WPT warps of a target
+        if (WPT == 1 ? sl == 0 : lane == 0) {
 #pragma unroll
-                for (int k = 0; k < 6; ++k) own.u[k][t_me] = make_float2(sv[k], cv[k]);
-            }
-        } else {
-            if (lane == 0) {
-#pragma unroll
-                for (int k = 0; k < 6; ++k) red[warp][k] = make_float2(sv[k], cv[k]);
-            }
-            __syncthreads();
-            if (tid < 6 * T) {
-                const int t = tid % T, k = tid / T;
-                float2 acc = red[t * WPT][k];
-#pragma unroll
-                for (int w = 1; w < WPT; ++w) ts_merge(acc.x, acc.y, red[t * WPT + w][k].x, red[t * WPT + w][k].y);
-                own.u[k][t] = acc;
-            }
+            for (int k = 0; k < 6; ++k) red[WPT == 1 ? t_me : warp][k] = make_float2(sv[k], cv[k]);
         }
         __syncthreads();
 
@@ -407,10 +398,19 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
         const int a = warp, d = lane;
         const bool eax = warp < 3 && d < nown;
         float pa = 0.f, pb = 0.f, eh = 0.f;
+        double xa = 0.0, xb = 0.0;   // new FP64 positions along a of spheres 2s, 2s + 1
         if (eax) {
-            const float va = fmaf(own.F[a][d], inv6, own.u[a][d].x + own.u[a][d].y);           // Eq. (3a)
-            const float vb = fmaf(own.F[a + 3][d], inv6, own.u[a + 3][d].x + own.u[a + 3][d].y);
-            double xa = own.x[a][d], xb = own.x[a + 3][d];
+            // the target's pair sums along a: its warps' pairs folded in warp order
+            float2 ua = red[d * WPT][a], ub = red[d * WPT][a + 3];
+#pragma unroll
+            for (int w = 1; w < WPT; ++w) {
+                ts_merge(ua.x, ua.y, red[d * WPT + w][a].x, red[d * WPT + w][a].y);
+                ts_merge(ub.x, ub.y, red[d * WPT + w][a + 3].x, red[d * WPT + w][a + 3].y);
+            }
+            const float va = fmaf(own.F[a][d], inv6, ua.x + ua.y);           // Eq. (3a)
+            const float vb = fmaf(own.F[a + 3][d], inv6, ub.x + ub.y);
+            xa = own.x[a][d];
+            xb = own.x[a + 3][d];
             if (!corr) {
                 own.v0[a][d] = va;
                 own.v0[a + 3][d] = vb;
@@ -435,23 +435,6 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
             eh = e.h;
             pa = (float)xa;
             pb = (float)xb;
-            // stroke average of the geometric centre along a (corrector), trapezoid rule
-            if (corr && A.avg_m > 0) {
-                const int64_t k_local = n + 1 - A.avg_n0;
-                if (k_local > 0) {
-                    const double Rt = 0.5 * (xa + xb) + (a == 0 ? A.cx : (a == 1 ? A.cy : A.cz));
-                    double acc = own.R[a][d];
-                    if ((k_local % A.avg_m) == 0) {
-                        acc += 0.5 * Rt;
-                        const int64_t kidx = k_local / A.avg_m - 1;
-                        if (kidx < A.avg_maxk) A.Rbar[kidx * 3 * A.S + 3 * (int64_t)(st0 + d) + a] = acc / (double)A.avg_m;
-                        acc = 0.5 * Rt;
-                    } else {
-                        acc += Rt;
-                    }
-                    own.R[a][d] = acc;
-                }
-            }
         } else if (warp == 3 && d < nown) {
             const ds sarg = ds_add(ds_mul({trig.x, trig.y}, {own.cph[d], own.cpl[d]}),
                                    ds_mul({trig.z, trig.w}, {own.sph[d], own.spl[d]}));
@@ -484,6 +467,24 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
                 float2 *pk = (float2 *)(P.pack + s);   // the final state's records, for the grid path
                 pk[a] = wp;
                 pk[3 + a] = wg;
+            }
+            // off the critical path, once the records are out: the stroke average
+            // of the geometric centre along a (corrector), trapezoid rule
+            if (corr && A.avg_m > 0) {
+                const int64_t k_local = n + 1 - A.avg_n0;
+                if (k_local > 0) {
+                    const double Rt = 0.5 * (xa + xb) + (a == 0 ? A.cx : (a == 1 ? A.cy : A.cz));
+                    double acc = own.R[a][d];
+                    if ((k_local % A.avg_m) == 0) {
+                        acc += 0.5 * Rt;
+                        const int64_t kidx = k_local / A.avg_m - 1;
+                        if (kidx < A.avg_maxk) A.Rbar[kidx * 3 * A.S + 3 * (int64_t)(st0 + d) + a] = acc / (double)A.avg_m;
+                        acc = 0.5 * Rt;
+                    } else {
+                        acc += Rt;
+                    }
+                    own.R[a][d] = acc;
+                }
             }
         }
         // no barrier here: the next poll writes only records this CTA does not own,
