@@ -38,6 +38,9 @@ sys.path.insert(0, ROOT)
 STEPS_PER_PERIOD = 1000
 SA_STEPS_PER_PERIOD = 10
 FLOPS_PER_PAIR = {"oseen": 27, "rpy": 34}   # algorithmic FP32 flops (FMA = 2), rsqrt not counted
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture of
+# the same launch (profiles/flow_kernel_rpy_s512_n1024.md): 1024 Heun steps, S = 512, RPY
+NCU_TRAFFIC = {("coop", 512, "rpy"): 177664 + 33536}
 METRIC = "sphere-pair interactions/s"
 
 
@@ -492,7 +495,8 @@ def run_ours(args):
         "path": path_choice,
         "roofline": {"bound": "alu", "kernel": kname,
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": NCU_TRAFFIC.get((path_choice["path"], S, args.mobility)),
                      "launch_ms": mean_ms, "flops_per_launch": flops_launch,
                      "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
                                    f"{mhz_max:.0f} MHz (max SM clock)"},

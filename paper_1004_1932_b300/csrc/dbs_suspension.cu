@@ -463,7 +463,7 @@ int check_flags(dbs_suspension *h)
         return fail(h, DBS_E_OVERLAP, "two spheres closer than 2a (RPY) or coincident");
     if (f & FLAG_NONFINITE) return fail(h, DBS_E_NONFINITE, "non-finite velocity or position");
     if (f & FLAG_TIMEOUT) return fail(h, DBS_E_TIMEOUT, "device-side wait timed out");
-    if (f & FLAG_LAUNCH) return fail(h, DBS_E_CUDA, "kernel launched without its cluster shape");
+    if (f & FLAG_LAUNCH) return fail(h, DBS_E_CUDA, "kernel launched in a grid or cluster shape it cannot run");
     return DBS_OK;
 }
 
