@@ -196,6 +196,7 @@ template <int T>
 struct FlowOwner {
     double x[6][T];                   // x - centre, spheres 2s (0..2) and 2s+1 (3..5)
     double R[3][T];                   // stroke-average sums (trapezoid rule)
+    float2 xs[6][T];                  // x as double-single (hi, lo): the critical path's copy
     float lamh[T], laml[T], sph[T], spl[T], cph[T], cpl[T];
     float F[6][T];                    // force at the current evaluation point
     float v0[6][T];                   // Heun predictor velocity
@@ -249,6 +250,7 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
     const float inv6 = (float)A.inv6pimua, k0f = (float)A.k0;
     const double cen[3] = {A.cx, A.cy, A.cz};
     const ds ell = ds_of(A.ell);
+    const ds dt_ds = ds_of(A.dt), hdt_ds = ds_of(0.5 * A.dt), sig_ds = ds_of(A.noise_sigma);
     if (gridDim.x != (unsigned)P.G || blockDim.x != (unsigned)NT) {   // not the shape the host made
         if (tid == 0) atomicOr(A.flags, FLAG_LAUNCH);
         return;
@@ -262,6 +264,8 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             own.x[k][d] = A.x[o + k] - cen[k % 3];
+            const ds xk = ds_of(own.x[k][d]);
+            own.xs[k][d] = make_float2(xk.h, xk.l);
             own.F[k][d] = (float)A.Fd[o + k];
             own.fext[k][d] = A.Fext ? (float)A.Fext[o + k] : 0.f;
         }
@@ -390,15 +394,16 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
         __syncthreads();
 
         // 4. epilogue.  Warps 0-2 take axis a = warp of the owned dumbbells (lane d):
-        // self term of Eq. (3a), FP64 Heun update of both spheres (Sec. IV), the
-        // axis component of e = x_b - x_a; warp 3 the rest length L(t_{n+1}) of
-        // Eq. (4).  Then each axis warp forms the spring magnitude (the same
-        // value in the three warps, which saves a barrier), its force component,
-        // and writes and publishes its record words.
+        // self term of Eq. (3a), Heun update of both spheres (Sec. IV) on the
+        // double-single copy of the positions, the axis component of
+        // e = x_b - x_a; warp 3 the rest length L(t_{n+1}) of Eq. (4).  Then each
+        // axis warp forms the spring magnitude (the same value in the three
+        // warps, which saves a barrier), its force component, writes and
+        // publishes its record words, and only then updates the FP64 state.
         const int a = warp, d = lane;
         const bool eax = warp < 3 && d < nown;
         float pa = 0.f, pb = 0.f, eh = 0.f;
-        double xa = 0.0, xb = 0.0;   // new FP64 positions along a of spheres 2s, 2s + 1
+        float va1 = 0.f, vb1 = 0.f;  // corrector velocities along a (the FP64 update uses them)
         if (eax) {
             // the target's pair sums along a: its warps' pairs folded in warp order
             float2 ua = red[d * WPT][a], ub = red[d * WPT][a + 3];
@@ -409,32 +414,32 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
             }
             const float va = fmaf(own.F[a][d], inv6, ua.x + ua.y);           // Eq. (3a)
             const float vb = fmaf(own.F[a + 3][d], inv6, ub.x + ub.y);
-            xa = own.x[a][d];
-            xb = own.x[a + 3][d];
+            // the new positions of both spheres along a in double-single (the
+            // records and the spring need FP32 accuracy; the FP64 state takes the
+            // same Heun update once the records are out)
+            ds na = {own.xs[a][d].x, own.xs[a][d].y}, nb = {own.xs[a + 3][d].x, own.xs[a + 3][d].y};
             if (!corr) {
                 own.v0[a][d] = va;
                 own.v0[a + 3][d] = vb;
-                xa = fma(A.dt, (double)va, xa);                                   // x~ = x_n + dt v0
-                xb = fma(A.dt, (double)vb, xb);
+                na = ds_add(na, ds_mul_f(dt_ds, va));                             // x~ = x_n + dt v0
+                nb = ds_add(nb, ds_mul_f(dt_ds, vb));
             } else {
-                xa = fma(0.5 * A.dt, (double)(own.v0[a][d] + va), xa);           // x_n + dt/2 (v0 + v1)
-                xb = fma(0.5 * A.dt, (double)(own.v0[a + 3][d] + vb), xb);
+                va1 = va;
+                vb1 = vb;
+                na = ds_add(na, ds_mul_f(hdt_ds, own.v0[a][d] + va));            // x_n + dt/2 (v0 + v1)
+                nb = ds_add(nb, ds_mul_f(hdt_ds, own.v0[a + 3][d] + vb));
             }
             if (NOISE) {
-                xa = fma(A.noise_sigma, (double)own.z[a][d], xa);
-                xb = fma(A.noise_sigma, (double)own.z[a + 3][d], xb);
+                na = ds_add(na, ds_mul_f(sig_ds, own.z[a][d]));
+                nb = ds_add(nb, ds_mul_f(sig_ds, own.z[a + 3][d]));
             }
-            if (corr) {
-                own.x[a][d] = xa;
-                own.x[a + 3][d] = xb;
-            }
-            if (!(finite1(xa) && finite1(xb))) atomicOr(A.flags, FLAG_NONFINITE);
-            const ds e = ds_of(xb - xa);
+            const ds e = ds_add(nb, ds_neg(na));
             const ds e2 = ds_mul(e, e);
             own.ee[a][d] = make_float2(e2.h, e2.l);
             eh = e.h;
-            pa = (float)xa;
-            pb = (float)xb;
+            pa = na.h + na.l;
+            pb = nb.h + nb.l;
+            if (!(finite_f(pa) && finite_f(pb))) atomicOr(A.flags, FLAG_NONFINITE);
         } else if (warp == 3 && d < nown) {
             const ds sarg = ds_add(ds_mul({trig.x, trig.y}, {own.cph[d], own.cpl[d]}),
                                    ds_mul({trig.z, trig.w}, {own.sph[d], own.spl[d]}));
@@ -468,8 +473,25 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
                 pk[a] = wp;
                 pk[3 + a] = wg;
             }
-            // off the critical path, once the records are out: the stroke average
-            // of the geometric centre along a (corrector), trapezoid rule
+            // off the critical path, once the records are out: the FP64 Heun update
+            // x_{n+1} = x_n + dt/2 (v0 + v1) (+ noise) of the state, the shadow
+            // resynchronised from it, and the stroke average of the geometric
+            // centre along a (trapezoid rule)
+            double xa = 0.0, xb = 0.0;
+            if (corr) {
+                xa = fma(0.5 * A.dt, (double)(own.v0[a][d] + va1), own.x[a][d]);
+                xb = fma(0.5 * A.dt, (double)(own.v0[a + 3][d] + vb1), own.x[a + 3][d]);
+                if (NOISE) {
+                    xa = fma(A.noise_sigma, (double)own.z[a][d], xa);
+                    xb = fma(A.noise_sigma, (double)own.z[a + 3][d], xb);
+                }
+                own.x[a][d] = xa;
+                own.x[a + 3][d] = xb;
+                const ds ya = ds_of(xa), yb = ds_of(xb);
+                own.xs[a][d] = make_float2(ya.h, ya.l);
+                own.xs[a + 3][d] = make_float2(yb.h, yb.l);
+                if (!(finite1(xa) && finite1(xb))) atomicOr(A.flags, FLAG_NONFINITE);
+            }
             if (corr && A.avg_m > 0) {
                 const int64_t k_local = n + 1 - A.avg_n0;
                 if (k_local > 0) {
