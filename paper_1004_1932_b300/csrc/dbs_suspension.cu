@@ -661,6 +661,10 @@ int dbs_set_external_force(dbs_suspension *h, const double *F)
 // ---------------------------------------------------------------------------
 // cooperative dataflow path (flow_kernel)
 // ---------------------------------------------------------------------------
+#ifndef DBS_FLOW_THREADS
+#define DBS_FLOW_THREADS 256
+#endif
+constexpr int FLOW_THREADS = DBS_FLOW_THREADS;   // threads per CTA of flow_kernel
 constexpr int FLOW_MAX_T = 16;        // dumbbells per CTA at most
 constexpr int FLOW_MAX_STEPS = 1024;  // Heun steps per launch
 
@@ -674,11 +678,11 @@ template <int MOB, bool NOISE>
 static const void *flow_pick(int T)
 {
     switch (T) {
-    case 1: return (const void *)flow_kernel<MOB, 1, NOISE>;
-    case 2: return (const void *)flow_kernel<MOB, 2, NOISE>;
-    case 4: return (const void *)flow_kernel<MOB, 4, NOISE>;
-    case 8: return (const void *)flow_kernel<MOB, 8, NOISE>;
-    case 16: return (const void *)flow_kernel<MOB, 16, NOISE>;
+    case 1: return (const void *)flow_kernel<MOB, 1, NOISE, FLOW_THREADS>;
+    case 2: return (const void *)flow_kernel<MOB, 2, NOISE, FLOW_THREADS>;
+    case 4: return (const void *)flow_kernel<MOB, 4, NOISE, FLOW_THREADS>;
+    case 8: return (const void *)flow_kernel<MOB, 8, NOISE, FLOW_THREADS>;
+    case 16: return (const void *)flow_kernel<MOB, 16, NOISE, FLOW_THREADS>;
     default: return nullptr;
     }
 }
@@ -697,7 +701,7 @@ static cudaLaunchConfig_t flow_config(const dbs_suspension *h, int G, int T, cud
 {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(G);
-    cfg.blockDim = dim3(FLOW_NT);
+    cfg.blockDim = dim3(FLOW_THREADS);
     cfg.dynamicSmemBytes = flow_smem(G, T);
     cfg.stream = h->stream;
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -732,7 +736,7 @@ int coop_setup(dbs_suspension *h)
         const void *k = flow_fn(h, T);
         CK(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)flow_smem(G, T)));
         int occ = 0;
-        CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, FLOW_NT, flow_smem(G, T)));
+        CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, FLOW_THREADS, flow_smem(G, T)));
         if ((int64_t)occ * sms >= G) break;
     }
     CK(h, cudaStreamSynchronize(h->stream));

@@ -39,6 +39,9 @@
 #include "dbs_common.cuh"
 #include "eval_kernel.cuh"
 
+#ifndef DBS_FLOW_STAGGER
+#define DBS_FLOW_STAGGER 300   // cycles between the two rounds of a poll
+#endif
 #ifndef DBS_FLOW_UNROLL
 #define DBS_FLOW_UNROLL 4
 #endif
@@ -47,10 +50,12 @@ namespace dbs {
 
 constexpr int kFlowUnroll = DBS_FLOW_UNROLL;   // unroll of the sweep over a thread's records
 
+// Tagged words are read and written with relaxed accesses at GPU scope (the
+// exchange is between CTAs of one grid): each 64-bit half is single-copy atomic.
 __device__ __forceinline__ ulonglong2 ld_tagged(const ulonglong2 *p)
 {
     ulonglong2 v;
-    asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p) : "memory");
     return v;
 }
 
@@ -58,7 +63,7 @@ __device__ __forceinline__ void st_tagged(ulonglong2 *p, float a, float b, unsig
 {
     const unsigned long long hi = (unsigned long long)tag << 32;
     const unsigned long long x = hi | __float_as_uint(a), y = hi | __float_as_uint(b);
-    asm volatile("st.volatile.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(x), "l"(y) : "memory");
+    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(x), "l"(y) : "memory");
 }
 
 __device__ __forceinline__ bool tagged(const ulonglong2 &v, unsigned tag)
@@ -135,25 +140,52 @@ __device__ __forceinline__ double ds_to_double(ds a) { return (double)a.h + (dou
 
 __device__ __forceinline__ ds ds_neg(ds a) { return {-a.h, -a.l}; }
 
-// Poll the tagged words p[j] (bit j of `pending`) until all carry `tag`; every round issues the
-// loads of all words still missing, so a round costs one memory round trip
-// however many words it waits for.  False on timeout or abort (see wait_tagged).
-template <int NB>
-__device__ __forceinline__ bool wait_batch(const ulonglong2 *const (&p)[NB], unsigned pending,
-                                           unsigned tag, ulonglong2 (&v)[NB], int *flags,
-                                           unsigned long long timeout_ns)
+// Poll the tagged words base[j NT] (bit j of `pending`) until each carries
+// `tag`, and store its two values to dst[2 j NT], dst[2 j NT + 1].  Two rounds of
+// loads are kept in flight, the second issued `stagger` cycles after the first,
+// so every word is read twice per memory round trip: a word that becomes
+// visible just after one round passed it is seen by the other about half a
+// round trip later.  False on timeout or abort (see wait_tagged).
+template <int NB, int NT>
+__device__ __forceinline__ bool poll_staggered(const ulonglong2 *base, float *dst, unsigned pending,
+                                               unsigned tag, int *flags, unsigned long long timeout_ns,
+                                               int stagger)
 {
+    ulonglong2 va[NB], vb[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        if ((pending >> j) & 1u) va[j] = ld_tagged(base + j * NT);
+    const long long c0 = clock64();
+    while (clock64() - c0 < stagger) {
+    }
     unsigned long long t0 = 0;
     for (unsigned it = 0;; ++it) {
+        const unsigned pb = pending;
 #pragma unroll
         for (int j = 0; j < NB; ++j)
-            if ((pending >> j) & 1u) v[j] = ld_tagged(p[j]);
+            if ((pb >> j) & 1u) vb[j] = ld_tagged(base + j * NT);
 #pragma unroll
         for (int j = 0; j < NB; ++j)
-            if (((pending >> j) & 1u) && tagged(v[j], tag)) pending &= ~(1u << j);
+            if (((pending >> j) & 1u) && tagged(va[j], tag)) {
+                dst[2 * j * NT] = lo_float(va[j].x);
+                dst[2 * j * NT + 1] = lo_float(va[j].y);
+                pending &= ~(1u << j);
+            }
+        if (!pending) return true;
+        const unsigned pa = pending;
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+            if ((pa >> j) & 1u) va[j] = ld_tagged(base + j * NT);
+#pragma unroll
+        for (int j = 0; j < NB; ++j)   // pending is within pb: vb[j] was loaded
+            if (((pending >> j) & 1u) && tagged(vb[j], tag)) {
+                dst[2 * j * NT] = lo_float(vb[j].x);
+                dst[2 * j * NT + 1] = lo_float(vb[j].y);
+                pending &= ~(1u << j);
+            }
         if (!pending) return true;
         if (it == 0) t0 = flow_ns();
-        if ((it & 15u) == 15u) {
+        if ((it & 7u) == 7u) {
             if (*(volatile int *)flags & FLAG_TIMEOUT) return false;
             if (flow_ns() - t0 > timeout_ns) {
                 atomicOr(flags, FLAG_TIMEOUT);
@@ -180,7 +212,7 @@ __device__ __forceinline__ void publish_record(ulonglong2 *dst, const float r[12
 __device__ __forceinline__ bool finite_f(float v) { return ((__float_as_uint(v) >> 23) & 0xffu) != 0xffu; }
 
 constexpr int FLOW_NT = 256;      // threads per CTA (8 warps)
-constexpr int FLOW_POLL = 16;     // tagged words polled per thread per round
+constexpr int FLOW_POLL = 12;     // tagged words polled per thread per round (two rounds in flight)
 
 struct FlowArgs {
     ulonglong2 *rec;   // tagged records [2][Spad][6]: word w holds record floats 2w, 2w+1
@@ -228,10 +260,10 @@ __device__ __noinline__ void draw_sphere_normals(unsigned long long seed, int64_
 }
 
 // NOISE: additive Brownian noise on (a separate instantiation).
-template <int MOB, int T, bool NOISE>
-__global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, const FlowArgs P)
+template <int MOB, int T, bool NOISE, int NT = FLOW_NT>
+__global__ void __launch_bounds__(NT, 1) flow_kernel(const EvalArgs A, const FlowArgs P)
 {
-    constexpr int NT = FLOW_NT;
+    constexpr int POLL = NT >= 512 ? FLOW_POLL / 2 : FLOW_POLL;   // words per thread in flight
     constexpr int PS = NT / T;                 // slices (threads) per target dumbbell
     constexpr int LW = PS < 32 ? PS : 32;      // lanes of one target within a warp
     constexpr int WPT = PS > 32 ? PS / 32 : 1; // warps per target
@@ -314,30 +346,18 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
             }
         }
 
-        // 1. poll the S - T records this CTA does not own, FLOW_POLL words per
-        // thread in flight, into shared memory
+        // 1. poll the S - T records this CTA does not own, POLL words per thread
+        // in two staggered rounds of loads, into shared memory
         bool ok = true;
-        for (int b0 = 0; b0 < nwords && ok; b0 += FLOW_POLL * NT) {
-            const ulonglong2 *pp[FLOW_POLL];
+        for (int b0 = 0; b0 < nwords && ok; b0 += POLL * NT) {
             unsigned pend = 0;
 #pragma unroll
-            for (int j = 0; j < FLOW_POLL; ++j) {
+            for (int j = 0; j < POLL; ++j) {
                 const int idx = b0 + j * NT + tid;
-                pp[j] = R;
-                if (idx < nwords && (idx < own_w0 || idx >= own_w1)) {
-                    pp[j] = R + idx;
-                    pend |= 1u << j;
-                }
+                if (idx < nwords && (idx < own_w0 || idx >= own_w1)) pend |= 1u << j;
             }
-            ulonglong2 v[FLOW_POLL];
-            ok = wait_batch<FLOW_POLL>(pp, pend, tag, v, A.flags, P.timeout_ns);
-#pragma unroll
-            for (int j = 0; j < FLOW_POLL; ++j) {
-                if (!((pend >> j) & 1u)) continue;
-                float *dst = (float *)tile + 2 * (b0 + j * NT + tid);   // word w = floats 2w, 2w+1
-                dst[0] = lo_float(v[j].x);
-                dst[1] = lo_float(v[j].y);
-            }
+            ok = poll_staggered<POLL, NT>(R + b0 + tid, (float *)tile + 2 * (b0 + tid), pend, tag,
+                                          A.flags, P.timeout_ns, DBS_FLOW_STAGGER);
         }
         dead = __syncthreads_or(!ok);
         if (dead) break;
