@@ -228,7 +228,8 @@ template <int T>
 struct FlowOwner {
     double x[6][T];                   // x - centre, spheres 2s (0..2) and 2s+1 (3..5)
     double R[3][T];                   // stroke-average sums (trapezoid rule)
-    float2 xs[6][T];                  // x as double-single (hi, lo): the critical path's copy
+    float2 xs[6][T];                  // x as double-single (hi, lo): the critical path's copy,
+                                      // set from x at launch, then advanced with x
     float lamh[T], laml[T], sph[T], spl[T], cph[T], cpl[T];
     float F[6][T];                    // force at the current evaluation point
     float v0[6][T];                   // Heun predictor velocity
@@ -459,6 +460,10 @@ __global__ void __launch_bounds__(NT, 1) flow_kernel(const EvalArgs A, const Flo
             eh = e.h;
             pa = na.h + na.l;
             pb = nb.h + nb.l;
+            if (corr) {   // x_{n+1}; the copy is refreshed from the FP64 state at every launch
+                own.xs[a][d] = make_float2(na.h, na.l);
+                own.xs[a + 3][d] = make_float2(nb.h, nb.l);
+            }
             if (!(finite_f(pa) && finite_f(pb))) atomicOr(A.flags, FLAG_NONFINITE);
         } else if (warp == 3 && d < nown) {
             const ds sarg = ds_add(ds_mul({trig.x, trig.y}, {own.cph[d], own.cpl[d]}),
@@ -494,9 +499,8 @@ __global__ void __launch_bounds__(NT, 1) flow_kernel(const EvalArgs A, const Flo
                 pk[3 + a] = wg;
             }
             // off the critical path, once the records are out: the FP64 Heun update
-            // x_{n+1} = x_n + dt/2 (v0 + v1) (+ noise) of the state, the shadow
-            // resynchronised from it, and the stroke average of the geometric
-            // centre along a (trapezoid rule)
+            // x_{n+1} = x_n + dt/2 (v0 + v1) (+ noise) of the state and the stroke
+            // average of the geometric centre along a (trapezoid rule)
             double xa = 0.0, xb = 0.0;
             if (corr) {
                 xa = fma(0.5 * A.dt, (double)(own.v0[a][d] + va1), own.x[a][d]);
@@ -507,9 +511,6 @@ __global__ void __launch_bounds__(NT, 1) flow_kernel(const EvalArgs A, const Flo
                 }
                 own.x[a][d] = xa;
                 own.x[a + 3][d] = xb;
-                const ds ya = ds_of(xa), yb = ds_of(xb);
-                own.xs[a][d] = make_float2(ya.h, ya.l);
-                own.xs[a + 3][d] = make_float2(yb.h, yb.l);
                 if (!(finite1(xa) && finite1(xb))) atomicOr(A.flags, FLAG_NONFINITE);
             }
             if (corr && A.avg_m > 0) {
