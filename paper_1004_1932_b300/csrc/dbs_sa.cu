@@ -1,10 +1,10 @@
 // Stroke-averaged far-field model, Eqs. (9a)-(9e) (Sec. III.B), and the
 // pair-distance comparison of the averaged model against the microscopic one.
 //
-// A CTA owns 32 dumbbells s (one per lane); its 8 warps split every
-// shared-memory tile of packed source records r (centre relative to the system
-// centre, amplitude, orientation, sin/cos of the phase) and their partial sums
-// are folded in warp order.  Per pair, with D = R^s - R^r,
+// A CTA owns TL dumbbells s (TL a power of two, about 128 CTAs in all); its
+// threads split, per target, every shared-memory tile of packed source records r
+// (centre relative to the system centre, amplitude, orientation, sin/cos of
+// the phase), and their partial sums are folded in a fixed order.  Per pair, with D = R^s - R^r,
 // Dh = D/|D|, s = Dh.N^s, r = Dh.N^r, q = N^s.N^r and
 // sin(phi^s - phi^r) = sin phi^s cos phi^r - cos phi^s sin phi^r:
 //   J = (9/64) a w ell^2 lam^s lam^r sin(dphi) |D|^-4
@@ -30,8 +30,7 @@ using namespace dbs;
 
 namespace {
 
-constexpr int SA_LANES = 32;  // target dumbbells per CTA (one per lane)
-constexpr int SA_W = 8;       // warps per CTA; each takes 1/SA_W of every tile
+constexpr int SA_NT = 256;    // threads per CTA
 constexpr int SA_TILE = 256;
 thread_local char g_sa_create_error[256] = "";
 
@@ -123,18 +122,41 @@ __device__ __forceinline__ void sa_pair(bool self, T Rx, T Ry, T Rz, T lam_s, T 
     K[2] += ck * hz;
 }
 
+// (s, c) += (s2, c2): FP32 with Knuth's two-sum on the sums, FP64 plain sums.
 template <typename T>
-__global__ void __launch_bounds__(SA_LANES * SA_W) sa_eval_kernel(SaArgs A)
+__device__ __forceinline__ void sa_merge(T &s, T &c, T s2, T c2)
+{
+    if constexpr (sizeof(T) == 4) {
+        const T u = s + s2;
+        const T z = u - s;
+        c += c2 + ((s - (u - z)) + (s2 - z));
+        s = u;
+    } else {
+        s += s2;
+        c += c2;
+    }
+}
+
+// TL target dumbbells per CTA; thread tid takes target tid / NSL and, of every
+// tile, the records k = (tid mod NSL) + NSL i.  The slice sums of a target are
+// folded across the lanes of a warp (shuffles) and then across its warps in
+// warp order; thread t < TL runs the epilogue of target t.
+template <typename T, int TL>
+__global__ void __launch_bounds__(SA_NT) sa_eval_kernel(SaArgs A)
 {
     using Rec = typename SaRecOf<T>::type;
+    constexpr int NSL = SA_NT / TL;               // slices (threads) per target
+    constexpr int LW = NSL < 32 ? NSL : 32;       // lanes of a target within a warp
+    constexpr int WPT = NSL > 32 ? NSL / 32 : 1;  // warps per target
     __shared__ Rec tile[SA_TILE];
-    __shared__ T red[SA_W][12][SA_LANES];   // per warp: J sum, J comp., K sum, K comp. (x, y, z)
+    __shared__ T red[WPT == 1 ? TL : SA_NT / 32][12];   // J sum, J comp., K sum, K comp. (x, y, z)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t sg = (int64_t)blockIdx.x * SA_LANES + lane;
-    const bool active = sg < A.S;
+    const int t = tid / NSL, sl = tid - t * NSL;
+    const int64_t st = (int64_t)blockIdx.x * TL + t;
+    const bool act = st < A.S;
     const Rec *in = (const Rec *)A.rec_in;
     Rec me{};
-    if (active) me = in[sg];
+    if (act) me = in[st];
     T Rx, Ry, Rz, lam, Nx, Ny, Nz, sn, cs;
     if constexpr (sizeof(T) == 4) {
         Rx = me.R.x; Ry = me.R.y; Rz = me.R.z; lam = me.R.w;
@@ -148,47 +170,56 @@ __global__ void __launch_bounds__(SA_LANES * SA_W) sa_eval_kernel(SaArgs A)
     for (int64_t t0 = 0; t0 < A.S; t0 += SA_TILE) {
         const int len = (int)min((int64_t)SA_TILE, A.S - t0);
         __syncthreads();
-        for (int k = tid; k < len; k += SA_LANES * SA_W) tile[k] = in[t0 + k];
+        for (int k = tid; k < len; k += SA_NT) tile[k] = in[t0 + k];
         __syncthreads();
-        const int k0 = (len * warp) / SA_W, k1 = (len * (warp + 1)) / SA_W;
         T J[3] = {0, 0, 0}, K[3] = {0, 0, 0};
-        for (int k = k0; k < k1; ++k)
-            sa_pair<T, Rec>(t0 + k == sg, Rx, Ry, Rz, lam, Nx, Ny, Nz, sn, cs, tile[k], J, K);
-        if constexpr (sizeof(T) == 4) {
-            for (int k = 0; k < 3; ++k) {
-                two_sum_acc(Js[k], Jc[k], J[k]);
-                two_sum_acc(Ks[k], Kc[k], K[k]);
-            }
-        } else {
-            for (int k = 0; k < 3; ++k) {
-                Js[k] += J[k];
-                Ks[k] += K[k];
-            }
+        if (act)
+            for (int k = sl; k < len; k += NSL)
+                sa_pair<T, Rec>(t0 + k == st, Rx, Ry, Rz, lam, Nx, Ny, Nz, sn, cs, tile[k], J, K);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            sa_merge(Js[k], Jc[k], J[k], T(0));
+            sa_merge(Ks[k], Kc[k], K[k], T(0));
         }
     }
-    for (int k = 0; k < 3; ++k) {
-        red[warp][k][lane] = Js[k];
-        red[warp][3 + k][lane] = Jc[k];
-        red[warp][6 + k][lane] = Ks[k];
-        red[warp][9 + k][lane] = Kc[k];
+#pragma unroll
+    for (int off = LW / 2; off >= 1; off >>= 1) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const T js = __shfl_xor_sync(0xffffffffu, Js[k], off), jc = __shfl_xor_sync(0xffffffffu, Jc[k], off);
+            const T ks = __shfl_xor_sync(0xffffffffu, Ks[k], off), kc = __shfl_xor_sync(0xffffffffu, Kc[k], off);
+            sa_merge(Js[k], Jc[k], js, jc);
+            sa_merge(Ks[k], Kc[k], ks, kc);
+        }
+    }
+    if (WPT == 1 ? sl == 0 : lane == 0) {
+        const int row = WPT == 1 ? t : warp;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            red[row][k] = Js[k];
+            red[row][3 + k] = Jc[k];
+            red[row][6 + k] = Ks[k];
+            red[row][9 + k] = Kc[k];
+        }
     }
     __syncthreads();
-    if (warp != 0) return;
-    // the SA_W warp partials, in warp order
-    for (int w = 1; w < SA_W; ++w) {
+    if (tid >= TL) return;
+    const int64_t sg = (int64_t)blockIdx.x * TL + tid;
+    if (sg >= A.S) return;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        Js[k] = red[tid * WPT][k];
+        Jc[k] = red[tid * WPT][3 + k];
+        Ks[k] = red[tid * WPT][6 + k];
+        Kc[k] = red[tid * WPT][9 + k];
+    }
+    for (int w = 1; w < WPT; ++w) {   // the target's warps, in warp order
+#pragma unroll
         for (int k = 0; k < 3; ++k) {
-            if constexpr (sizeof(T) == 4) {
-                two_sum_acc(Js[k], Jc[k], red[w][k][lane]);
-                Jc[k] += red[w][3 + k][lane];
-                two_sum_acc(Ks[k], Kc[k], red[w][6 + k][lane]);
-                Kc[k] += red[w][9 + k][lane];
-            } else {
-                Js[k] += red[w][k][lane];
-                Ks[k] += red[w][6 + k][lane];
-            }
+            sa_merge(Js[k], Jc[k], red[tid * WPT + w][k], red[tid * WPT + w][3 + k]);
+            sa_merge(Ks[k], Kc[k], red[tid * WPT + w][6 + k], red[tid * WPT + w][9 + k]);
         }
     }
-    if (!active) return;
     double Jd[3], Kd[3];
     for (int k = 0; k < 3; ++k) {
         Jd[k] = A.CJ * ((double)Js[k] + (double)Jc[k]);
@@ -440,11 +471,31 @@ static SaArgs sa_args(const dbs_sa *h)
     return A;
 }
 
+template <typename T, int TL>
+static void sa_launch_t(const dbs_sa *h, const SaArgs &A)
+{
+    const int blocks = (int)((h->p.S + TL - 1) / TL);
+    sa_eval_kernel<T, TL><<<blocks, SA_NT, 0, h->stream>>>(A);
+}
+
+// Targets per CTA: the smallest power of two that keeps the grid within about
+// 128 CTAs (one wave on the SMs), at most 32.
+template <typename T>
+static void sa_launch_p(const dbs_sa *h, const SaArgs &A)
+{
+    const int64_t S = h->p.S;
+    if (S <= 128) sa_launch_t<T, 1>(h, A);
+    else if (S <= 256) sa_launch_t<T, 2>(h, A);
+    else if (S <= 512) sa_launch_t<T, 4>(h, A);
+    else if (S <= 1024) sa_launch_t<T, 8>(h, A);
+    else if (S <= 2048) sa_launch_t<T, 16>(h, A);
+    else sa_launch_t<T, 32>(h, A);
+}
+
 static void sa_launch(const dbs_sa *h, const SaArgs &A)
 {
-    const int blocks = (int)((h->p.S + SA_LANES - 1) / SA_LANES);
-    if (sa_f64(h)) sa_eval_kernel<double><<<blocks, SA_LANES * SA_W, 0, h->stream>>>(A);
-    else sa_eval_kernel<float><<<blocks, SA_LANES * SA_W, 0, h->stream>>>(A);
+    if (sa_f64(h)) sa_launch_p<double>(h, A);
+    else sa_launch_p<float>(h, A);
 }
 
 static int sa_repack(dbs_sa *h)

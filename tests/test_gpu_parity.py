@@ -213,6 +213,22 @@ def test_stroke_averaged_rates_and_steps(prec):
     np.testing.assert_allclose(np.linalg.norm(N, axis=1), 1.0, rtol=1e-14)
 
 
+@pytest.mark.parametrize("prec", ["fp32c", "fp64"])
+@pytest.mark.parametrize("S", [2, 33, 129, 300, 1000, 2500])
+def test_stroke_averaged_rates_sizes(S, prec):
+    # every split of the averaged-model kernel (1 .. 32 targets per CTA), ragged
+    # last CTAs and tiles, against the oracle's rates
+    s = inputs.paper_scale(S, seed=21 + S)
+    kw = dict(a=s.a, ell=s.ell, omega=s.omega)
+    Rd_ref, Nd_ref = oracle.sa_rates(s.R0, s.N0, s.phi, s.lam, **kw)
+    h = dbs.StrokeAveraged(s.R0, s.N0, s.phi, s.lam, dt=0.1, precision=prec, **kw)
+    Rd, Nd = h.rates()
+    h.close()
+    tol = 1e-5 if prec == "fp32c" else 1e-12
+    assert _relerr(Rd, Rd_ref) <= tol
+    assert _relerr(Nd, Nd_ref) <= tol
+
+
 @pytest.mark.parametrize("S", [2, 33, 300, 1000])
 def test_pair_distance_error_matches_oracle(S):
     import torch
