@@ -718,9 +718,10 @@ int coop_setup(dbs_suspension *h)
 {
     if (h->p.precision != DBS_FP32C || h->S > SMALL_S)
         return refuse(h, DBS_E_ARG, "cooperative path needs FP32C and S <= 2048");
-    int coop = 0, sms = 0;
+    int coop = 0, sms = 0, optin = 0;
     CK(h, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device));
     CK(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    CK(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     if (!coop) return refuse(h, DBS_E_ARG, "device without cooperative launch");
     // tiny systems: one CTA holds all dumbbells and no record leaves it
     int T = h->S <= FLOW_MAX_T ? FLOW_MAX_T : 1;
@@ -734,7 +735,14 @@ int coop_setup(dbs_suspension *h)
         G = (int)((h->S + T - 1) / T);
         if (G > sms) continue;
         const void *k = flow_fn(h, T);
-        CK(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)flow_smem(G, T)));
+        // the limit is a property of the kernel, shared by every handle that launches
+        // it: set it to all the device allows (never to this handle's need, which
+        // would shrink it under a larger suspension set up earlier)
+        cudaFuncAttributes fa{};
+        CK(h, cudaFuncGetAttributes(&fa, k));
+        if (flow_smem(G, T) + fa.sharedSizeBytes > (size_t)optin) continue;
+        CK(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   optin - (int)fa.sharedSizeBytes));
         int occ = 0;
         CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, FLOW_THREADS, flow_smem(G, T)));
         if ((int64_t)occ * sms >= G) break;

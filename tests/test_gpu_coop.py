@@ -95,6 +95,21 @@ def test_coop_chunk_counts_agree(S, chunks):
     assert np.abs(x - ref).max() <= 1e-6 * s.ell
 
 
+def test_coop_handles_of_one_split_coexist():
+    # two suspensions on the same kernel instantiation (16 dumbbells per CTA) with
+    # different record arrays: setting up the smaller one second must not stop the
+    # larger one from launching
+    big = inputs.paper_scale(2000, seed=31)
+    small = inputs.paper_scale(1500, seed=32)
+    with _handle(big) as hb, _handle(small) as hs:
+        hb.set_path("coop")
+        hs.set_path("coop")
+        assert hb.get_launch()["bt"] == hs.get_launch()["bt"] == 16
+        hb.step(20)
+        hs.step(20)
+        assert np.isfinite(hb.positions()).all() and np.isfinite(hs.positions()).all()
+
+
 def test_coop_period_averages_match_oracle():
     s = inputs.make_suspension(12, seed=6, side=8.0)
     m, periods = 100, 3
