@@ -386,11 +386,12 @@ DBS_API const char *dbs_ensemble_last_error(const dbs_ensemble *e);
  * A request is one simulation: parameters, initial positions, stroke and a
  * number of Heun steps; its result is the positions after those steps.  The
  * engine keeps requests resident on the device as independent suspensions and
- * advances all of them together on every dbs_engine_tick (continuous
- * batching): requests that arrive while others run are admitted at the next
- * tick as soon as the device-memory budget and the slot limit allow, members
- * that fit the cluster path run as one ensemble and the others on the grid
- * path concurrently, and finished requests are copied out and freed.
+ * advances them concurrently, block by block, through dbs_engine_tick
+ * (continuous batching): requests that arrive while others run are admitted
+ * at the next tick as soon as the device-memory budget and the slot limit
+ * allow, members that fit the cluster path run as one ensemble and the others
+ * on the grid path, each on its own stream, and finished requests are copied
+ * out and freed.
  */
 typedef struct {
     size_t hbm_budget_bytes; /* admission budget for resident request state, 0 = unlimited */
@@ -421,8 +422,13 @@ DBS_API int dbs_engine_submit(dbs_engine *e, const dbs_params *p, const double *
                               const double *lambda, const double *phase, int64_t steps,
                               int64_t *id);
 
-/* Admit, advance every resident request by up to block_steps, retire finished ones.
- * Reports the numbers of resident and queued requests afterwards. */
+/* Admit queued requests; wait until some block in flight completes (the one
+ * ensemble of all cluster-path requests, or one grid-path request's block)
+ * and count its steps; retire finished requests; launch the next block of up
+ * to block_steps Heun steps of every idle resident request.  Blocks complete
+ * independently, so a small request never waits for a large one's block.
+ * Reports the numbers of resident and queued requests afterwards.
+ * DBS_E_TIMEOUT if no block completes within 600 s. */
 DBS_API int dbs_engine_tick(dbs_engine *e, int32_t *active, int32_t *pending);
 
 /*

@@ -3,11 +3,15 @@
 //
 // Each tick: (1) admit queued requests in arrival order while the budget and
 // the slot limit allow (a request becomes a suspension handle with its own
-// stream); (2) give every resident request min(block_steps, remaining) Heun
-// steps -- those that fit the cluster path as one ensemble (rebuilt when the
-// resident set changes), the others on the grid path, all concurrently;
-// (3) wait, then copy out and free the finished ones.  Requests that arrive
-// while others run join at the next tick: continuous batching.
+// stream); (2) wait until some block in flight completes -- the one ensemble
+// of all cluster-path requests, or one grid-path request's block on its own
+// stream -- and count its steps; (3) copy out and free the finished requests;
+// (4) launch the next min(block_steps, remaining) Heun steps of everything
+// idle: the cluster-path requests as one ensemble (rebuilt when the resident
+// set changes), each other request on its own stream, all concurrently.
+// Blocks complete independently, so a small request does not wait for a large
+// one's block.  Requests that arrive while others run join at the next tick:
+// continuous batching.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -16,6 +20,7 @@
 #include <cstdio>
 #include <deque>
 #include <new>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -42,6 +47,8 @@ struct Request {
     size_t bytes = 0;
     double t_submit = 0, t_done = 0;
     bool cluster = false;
+    int64_t inflight = 0;          // grid path: steps launched, not yet accounted
+    cudaEvent_t ev = nullptr;      // grid path: recorded after the last launch
 };
 
 size_t request_bytes(int64_t S, int32_t precision)
@@ -66,6 +73,9 @@ struct dbs_engine {
     int64_t next_id = 1;
     dbs_ensemble *ens = nullptr;
     std::vector<int64_t> ens_ids;  // members of ens, in order
+    std::vector<int64_t> ens_k;    // steps of the ensemble block in flight, per member
+    bool ens_busy = false;
+    cudaEvent_t ens_ev = nullptr;  // recorded after the block in flight
 };
 
 static int engfail(dbs_engine *e, int st, const char *fmt, ...)
@@ -86,15 +96,37 @@ static void release(dbs_engine *e, Request &r)
         r.h = nullptr;
         e->used -= r.bytes;
     }
+    if (r.ev) {
+        cudaEventDestroy(r.ev);
+        r.ev = nullptr;
+    }
+    r.inflight = 0;
 }
 
+// The ensemble block in flight has completed: its members' steps count.
+static void ens_settle(dbs_engine *e)
+{
+    if (!e->ens_busy) return;
+    for (size_t i = 0; i < e->ens_ids.size(); ++i) {
+        auto it = e->req.find(e->ens_ids[i]);
+        if (it != e->req.end()) it->second.remaining -= e->ens_k[i];
+    }
+    e->ens_busy = false;
+}
+
+// Wait for the ensemble block in flight (if any), count it, and drop the ensemble.
 static void drop_ensemble(dbs_engine *e)
 {
+    if (e->ens_busy) {
+        cudaEventSynchronize(e->ens_ev);
+        ens_settle(e);
+    }
     if (e->ens) {
         ens_destroy(e->ens);
         e->ens = nullptr;
     }
     e->ens_ids.clear();
+    e->ens_k.clear();
 }
 
 extern "C" {
@@ -130,6 +162,7 @@ int dbs_engine_destroy(dbs_engine *e)
     cudaSetDevice(e->device);
     drop_ensemble(e);
     for (auto &kv : e->req) release(e, kv.second);
+    if (e->ens_ev) cudaEventDestroy(e->ens_ev);
     delete e;
     return DBS_OK;
 }
@@ -175,7 +208,6 @@ int dbs_engine_tick(dbs_engine *e, int32_t *active, int32_t *pending)
 {
     if (!e) return DBS_E_ARG;
     if (cudaSetDevice(e->device) != cudaSuccess) return engfail(e, DBS_E_CUDA, "cudaSetDevice");
-    bool changed = false;
     // (1) admission, arrival order
     while (!e->queue.empty()) {
         Request &r = e->req[e->queue.front()];
@@ -188,9 +220,10 @@ int dbs_engine_tick(dbs_engine *e, int32_t *active, int32_t *pending)
         e->queue.pop_front();
         int rc = dbs_create_suspension(&r.p, r.x0.data(), &r.h);
         if (rc == DBS_OK) rc = dbs_set_stroke(r.h, r.lam.data(), r.phi.data());
+        if (rc == DBS_OK && cudaEventCreateWithFlags(&r.ev, cudaEventDisableTiming) != cudaSuccess)
+            rc = DBS_E_CUDA;
         if (rc != DBS_OK) {
-            if (r.h) dbs_destroy(r.h);
-            r.h = nullptr;
+            release(e, r);
             r.state = DBS_REQ_FAILED;
             r.t_done = now_s();
             continue;
@@ -199,68 +232,103 @@ int dbs_engine_tick(dbs_engine *e, int32_t *active, int32_t *pending)
         r.state = DBS_REQ_RUNNING;
         r.cluster = ens_member_ok(r.h);
         e->active.push_back(r.id);
-        changed = true;
         if (r.remaining == 0) {  // nothing to do: done at once
             finish(e, r);
             e->active.pop_back();
         }
     }
-    // (2) advance: cluster members as one ensemble, the rest on the grid path
-    std::vector<int64_t> cl, gr;
-    for (int64_t id : e->active) (e->req[id].cluster ? cl : gr).push_back(id);
-    if (changed || cl != e->ens_ids) {
-        drop_ensemble(e);
-        if (!cl.empty()) {
-            std::vector<dbs_suspension *> hs;
-            for (int64_t id : cl) hs.push_back(e->req[id].h);
-            int rc = ens_create((int32_t)hs.size(), hs.data(), nullptr, &e->ens);
-            if (rc != DBS_OK) return engfail(e, rc, "ensemble: %s", ens_error(nullptr));
-            e->ens_ids = cl;
+    // (2) wait until some work in flight completes (the ensemble's block, or one
+    // grid-path request's block), polling without blocking the others
+    bool inflight = e->ens_busy;
+    for (int64_t id : e->active) inflight |= e->req[id].inflight > 0;
+    const double t_wait = now_s();
+    while (inflight) {
+        bool progress = false;
+        if (e->ens_busy) {
+            const cudaError_t q = cudaEventQuery(e->ens_ev);
+            if (q == cudaSuccess) {
+                ens_settle(e);
+                progress = true;
+            } else if (q != cudaErrorNotReady) {
+                return engfail(e, DBS_E_CUDA, "ensemble: %s", cudaGetErrorString(q));
+            }
         }
-    }
-    std::vector<int64_t> ksteps;
-    for (int64_t id : cl) ksteps.push_back(std::min<int64_t>(e->req[id].remaining, e->P.block_steps));
-    if (e->ens) {
-        int rc = ens_step_v(e->ens, ksteps.data());
-        if (rc != DBS_OK) return engfail(e, rc, "ensemble step: %s", ens_error(e->ens));
-    }
-    for (int64_t id : gr) {
-        Request &r = e->req[id];
-        const int64_t k = std::min<int64_t>(r.remaining, e->P.block_steps);
-        if (dbs_step(r.h, k) != DBS_OK) {
-            r.state = DBS_REQ_FAILED;
-            r.t_done = now_s();
+        for (int64_t id : e->active) {
+            Request &r = e->req[id];
+            if (r.inflight == 0) continue;
+            const cudaError_t q = cudaEventQuery(r.ev);
+            if (q == cudaSuccess) {
+                r.remaining -= r.inflight;
+                r.inflight = 0;
+                progress = true;
+            } else if (q != cudaErrorNotReady) {
+                r.state = DBS_REQ_FAILED;
+                r.t_done = now_s();
+                r.inflight = 0;
+                progress = true;
+            }
         }
+        if (progress) break;
+        if (now_s() - t_wait > 600.0) return engfail(e, DBS_E_TIMEOUT, "no block completed in 600 s");
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
-    // (3) wait, account, retire
+    // (3) retire: failed requests, and finished ones that nothing still runs
     std::vector<int64_t> still;
-    for (size_t i = 0; i < cl.size(); ++i) {
-        Request &r = e->req[cl[i]];
-        r.remaining -= ksteps[i];
-    }
-    for (int64_t id : gr) {
+    for (int64_t id : e->active) {
         Request &r = e->req[id];
-        if (r.state == DBS_REQ_RUNNING) r.remaining -= std::min<int64_t>(r.remaining, e->P.block_steps);
+        const bool in_ens = e->ens_busy && std::find(e->ens_ids.begin(), e->ens_ids.end(), id) != e->ens_ids.end();
+        if (r.state == DBS_REQ_FAILED && !in_ens) {
+            if (r.inflight == 0) release(e, r);
+            else still.push_back(id);
+            continue;
+        }
+        if (r.remaining == 0 && r.inflight == 0 && !in_ens) finish(e, r);
+        else still.push_back(id);
+    }
+    e->active.swap(still);
+    // (4) launch the next block of everything idle: the cluster-path requests as
+    // one ensemble (rebuilt when its membership changes), the others each on its
+    // own stream; all run concurrently
+    if (!e->ens_busy) {
+        std::vector<int64_t> cl;
+        for (int64_t id : e->active) {
+            const Request &r = e->req[id];
+            if (r.cluster && r.state == DBS_REQ_RUNNING && r.remaining > 0) cl.push_back(id);
+        }
+        if (cl != e->ens_ids) {
+            drop_ensemble(e);
+            if (!cl.empty()) {
+                std::vector<dbs_suspension *> hs;
+                for (int64_t id : cl) hs.push_back(e->req[id].h);
+                int rc = ens_create((int32_t)hs.size(), hs.data(), nullptr, &e->ens);
+                if (rc != DBS_OK) return engfail(e, rc, "ensemble: %s", ens_error(nullptr));
+                e->ens_ids = cl;
+            }
+        }
+        if (e->ens) {
+            e->ens_k.clear();
+            for (int64_t id : cl) e->ens_k.push_back(std::min<int64_t>(e->req[id].remaining, e->P.block_steps));
+            int rc = ens_step_v(e->ens, e->ens_k.data());
+            if (rc != DBS_OK) return engfail(e, rc, "ensemble step: %s", ens_error(e->ens));
+            if (!e->ens_ev && cudaEventCreateWithFlags(&e->ens_ev, cudaEventDisableTiming) != cudaSuccess)
+                return engfail(e, DBS_E_CUDA, "event");
+            // the members' streams wait for the ensemble's block: an event on one of them
+            if (cudaEventRecord(e->ens_ev, e->req[cl[0]].h->stream) != cudaSuccess)
+                return engfail(e, DBS_E_CUDA, "event record");
+            e->ens_busy = true;
+        }
     }
     for (int64_t id : e->active) {
         Request &r = e->req[id];
-        if (r.state == DBS_REQ_FAILED) {
-            release(e, r);
-            continue;
-        }
-        if (dbs_sync(r.h) != DBS_OK) {
+        if (r.cluster || r.state != DBS_REQ_RUNNING || r.inflight > 0 || r.remaining == 0) continue;
+        const int64_t k = std::min<int64_t>(r.remaining, e->P.block_steps);
+        if (dbs_step(r.h, k) != DBS_OK || cudaEventRecord(r.ev, r.h->stream) != cudaSuccess) {
             r.state = DBS_REQ_FAILED;
             r.t_done = now_s();
-            release(e, r);
             continue;
         }
-        if (r.remaining == 0) {
-            finish(e, r);
-        } else {
-            still.push_back(id);
-        }
+        r.inflight = k;
     }
-    e->active.swap(still);
     if (active) *active = (int32_t)e->active.size();
     if (pending) *pending = (int32_t)e->queue.size();
     return DBS_OK;
@@ -290,9 +358,9 @@ int dbs_engine_cancel(dbs_engine *e, int64_t id)
         r.state = DBS_REQ_CANCELLED;
         return DBS_OK;
     }
-    if (r.state == DBS_REQ_RUNNING) {
+    if (r.state == DBS_REQ_RUNNING || r.state == DBS_REQ_FAILED) {
         cudaSetDevice(e->device);
-        drop_ensemble(e);
+        drop_ensemble(e);   // waits for an ensemble block in flight
         if (r.h) dbs_sync(r.h);
         release(e, r);
         r.state = DBS_REQ_CANCELLED;
