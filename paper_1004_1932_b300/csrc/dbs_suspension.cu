@@ -36,6 +36,9 @@ constexpr int TILE64 = 64;   // dumbbell records per tile (FP64, 6 KB)
 constexpr int BT64S = 32;
 constexpr int TILE64S = 32;
 constexpr int64_t SMALL_S = 2048;
+constexpr int BT32M = 256;    // dumbbells per CTA (FP32C, SMALL_S < S <= MID_S)
+constexpr int TILE32M = 256;
+constexpr int64_t MID_S = 8192;
 constexpr int TRIG_RING = kTrigRing;  // entries of the (sin, cos)(omega t_k) ring (power of two)
 constexpr int GRAPH_STEPS = 32;  // Heun steps per captured CUDA graph
 
@@ -165,6 +168,18 @@ static void launch_pdl(K kern, int grid, int bt, size_t smem, cudaStream_t st, c
     cudaLaunchKernelEx(&cfg, kern, A);
 }
 
+// FP32C launch configuration by size: dumbbells per CTA and records per tile
+// (measured on B300: 32 for small systems, where latency rules; 256 up to
+// S = 8192; 512, one CTA per SM, for the largest)
+static int fp32_bt(int64_t S) { return S <= SMALL_S ? BT32S : (S <= MID_S ? BT32M : BT32); }
+static int fp32_tile(int bt) { return bt == BT32S ? TILE32S : (bt == BT32M ? TILE32M : TILE32); }
+static const void *fp32_occ_kernel(int bt)
+{
+    if (bt == BT32S) return (const void *)eval_kernel<float, 1, PHASE_CORRECT, BT32S, TILE32S>;
+    if (bt == BT32M) return (const void *)eval_kernel<float, 1, PHASE_CORRECT, BT32M, TILE32M>;
+    return (const void *)eval_kernel<float, 1, PHASE_CORRECT, BT32, TILE32>;
+}
+
 template <typename Real, int MOB, int PHASE>
 static void launch_eval_t(const EvalArgs &A, int grid, int bt, cudaStream_t st)
 {
@@ -172,6 +187,9 @@ static void launch_eval_t(const EvalArgs &A, int grid, int bt, cudaStream_t st)
         if (bt == BT32S)
             launch_pdl(eval_kernel<float, MOB, PHASE, BT32S, TILE32S>, grid, BT32S,
                        eval_smem_bytes<float>(BT32S, TILE32S, A.chunks), st, A);
+        else if (bt == BT32M)
+            launch_pdl(eval_kernel<float, MOB, PHASE, BT32M, TILE32M>, grid, BT32M,
+                       eval_smem_bytes<float>(BT32M, TILE32M, A.chunks), st, A);
         else
             launch_pdl(eval_kernel<float, MOB, PHASE, BT32, TILE32>, grid, BT32,
                        eval_smem_bytes<float>(BT32, TILE32, A.chunks), st, A);
@@ -319,8 +337,8 @@ static void choose_launch(dbs_suspension *h)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     const bool small = h->S <= SMALL_S;
     const bool f64 = is_f64(h);
-    const int bt = f64 ? (small ? BT64S : BT64) : (small ? BT32S : BT32);
-    const int tdb = f64 ? (small ? TILE64S : TILE64) : (small ? TILE32S : TILE32);
+    const int bt = f64 ? (small ? BT64S : BT64) : fp32_bt(h->S);
+    const int tdb = f64 ? (small ? TILE64S : TILE64) : fp32_tile(bt);
     h->bt = bt;
     auto occ_for = [&](int64_t c) {
         int occ = 0;
@@ -333,10 +351,7 @@ static void choose_launch(dbs_suspension *h)
                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                             &occ, eval_kernel<double, 1, PHASE_CORRECT, BT64, TILE64>, bt, smem);
         else
-            e = small ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                            &occ, eval_kernel<float, 1, PHASE_CORRECT, BT32S, TILE32S>, bt, smem)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                            &occ, eval_kernel<float, 1, PHASE_CORRECT, BT32, TILE32>, bt, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp32_occ_kernel(bt), bt, smem);
         return (e == cudaSuccess && occ > 0) ? occ : 1;
     };
     const int64_t iblocks = (h->S + bt - 1) / bt;
@@ -375,7 +390,7 @@ static int grid_for(dbs_suspension *h, int C)
     const bool f64 = is_f64(h);
     const bool small = h->S <= SMALL_S;
     const int bt = h->bt;
-    const int tdb = f64 ? (small ? TILE64S : TILE64) : (small ? TILE32S : TILE32);
+    const int tdb = f64 ? (small ? TILE64S : TILE64) : fp32_tile(bt);
     const size_t smem = f64 ? eval_smem_bytes<double>(bt, tdb, C) : eval_smem_bytes<float>(bt, tdb, C);
     int occ = 0;
     if (f64)
@@ -383,9 +398,7 @@ static int grid_for(dbs_suspension *h, int C)
             &occ, small ? (const void *)eval_kernel<double, 1, PHASE_CORRECT, BT64S, TILE64S>
                         : (const void *)eval_kernel<double, 1, PHASE_CORRECT, BT64, TILE64>, bt, smem);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &occ, small ? (const void *)eval_kernel<float, 1, PHASE_CORRECT, BT32S, TILE32S>
-                        : (const void *)eval_kernel<float, 1, PHASE_CORRECT, BT32, TILE32>, bt, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp32_occ_kernel(bt), bt, smem);
     occ = std::max(1, occ);
     const int64_t iblocks = (h->S + bt - 1) / bt;
     return (int)std::min<int64_t>((int64_t)h->sms * occ, iblocks * C);

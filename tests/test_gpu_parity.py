@@ -41,7 +41,7 @@ def _jittered(s, seed, scale=0.05):
 
 @pytest.mark.parametrize("prec", ["fp32c", "fp64"])
 @pytest.mark.parametrize("mob", ["oseen", "rpy"])
-@pytest.mark.parametrize("S", [1, 2, 16, 37, 129, 300, 1000])
+@pytest.mark.parametrize("S", [1, 2, 16, 37, 129, 300, 1000, 3001])
 def test_velocities_ragged_sizes(prec, mob, S):
     s = inputs.make_suspension(S, seed=S, density=0.002, mobility=mob)
     x = _jittered(s, S)
