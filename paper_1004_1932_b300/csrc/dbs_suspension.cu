@@ -977,11 +977,13 @@ int dbs_step_timed(dbs_suspension *h, int64_t n, double *mean_ms)
         A.pack_out = h->packB;
         CK(h, cudaEventRecord(ev[0], h->stream));
         launch_eval(h, PHASE_PREDICT, A);
+        CK(h, cudaGetLastError());
         CK(h, cudaEventRecord(ev[1], h->stream));
         A.pack_in = h->packB;
         A.pack_out = h->packA;
         CK(h, cudaEventRecord(ev[2], h->stream));
         launch_eval(h, PHASE_CORRECT, A);
+        CK(h, cudaGetLastError());
         CK(h, cudaEventRecord(ev[3], h->stream));
         CK(h, cudaEventSynchronize(ev[3]));
         float a = 0, b = 0;

@@ -28,7 +28,7 @@
 // Tuning macros (defaults measured on B300 at N = 65536, see profiles/):
 //   DBS_RPY_W35           RPY coefficients as A = w + c2 w^3, B = (r.G)(w^3 + c3 w^5)
 //   DBS_UNROLL            unroll of the fast j-loop for CTAs of fewer than 256 threads
-//                         (larger CTAs, the large-system configuration, unroll by 8)
+//   DBS_UNROLL_LARGE      the same for CTAs of 256 threads or more (large systems)
 //   DBS_FP32_WARPS_PER_SM resident warps the FP32 kernels are register-capped for
 //   DBS_W2_RCP            w^2 from rcp.approx instead of w*w (slower on B300; off)
 //   DBS_UNIT_ORDER        1: work units in chunk-major order, 0: i-block-major
@@ -37,6 +37,9 @@
 #endif
 #ifndef DBS_UNROLL
 #define DBS_UNROLL 2
+#endif
+#ifndef DBS_UNROLL_LARGE
+#define DBS_UNROLL_LARGE 8
 #endif
 #ifndef DBS_FP32_WARPS_PER_SM
 #define DBS_FP32_WARPS_PER_SM 20
@@ -243,7 +246,7 @@ __device__ __forceinline__ void sweep_f32(const DbF32 *__restrict__ pin, DbF32 *
 {
     // large CTAs (the throughput-bound large-system configuration): unroll by 8
     // and the three-input integer min; small ones keep the latency-friendly forms
-    constexpr int kUnroll = BT >= 256 ? 8 : kPairUnroll;
+    constexpr int kUnroll = BT >= 256 ? DBS_UNROLL_LARGE : kPairUnroll;
     constexpr bool kImin3 = BT >= 256;
     const int tid = threadIdx.x;
     float2 pax = make_float2(0.f, 0.f), pay = pax, paz = pax, pbx = pax, pby = pax, pbz = pax;
