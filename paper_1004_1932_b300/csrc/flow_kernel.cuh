@@ -43,7 +43,7 @@
 #define DBS_FLOW_STAGGER 300   // cycles between the two rounds of a poll
 #endif
 #ifndef DBS_FLOW_UNROLL
-#define DBS_FLOW_UNROLL 4
+#define DBS_FLOW_UNROLL 8
 #endif
 
 namespace dbs {
