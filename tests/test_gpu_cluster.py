@@ -8,6 +8,8 @@
   stroke averages accumulated inside the resident kernel match the oracle's.
 * Chunks of steps larger than one resident launch (1024 steps) continue the
   clock and the step counter exactly.
+* The benchmark's 256-system ensemble: sampled members (smallest, median,
+  largest) follow the oracle over 20 steps, every member stays finite.
 """
 import numpy as np
 import pytest
@@ -83,6 +85,28 @@ def test_ensemble_members_match_alone():
         e.step(50)
         e.sync()
     for h in hs:
+        h.close()
+
+
+def test_full_ensemble_sampled_members_follow_oracle():
+    # the batched-ensemble workload the benchmark times: 256 systems, S log-uniform
+    # in [8, 2048], amplitudes in [0.1, 0.3], built-in cluster sizes; the smallest,
+    # median-sized and largest members against the oracle, every member finite
+    systems = inputs.ensemble(256)
+    nsteps = 20
+    hs = [_handle(s) for s in systems]
+    with dbs.Ensemble(hs) as e:
+        e.step(nsteps)
+        e.sync()
+    order = sorted(range(len(systems)), key=lambda i: systems[i].S)
+    for i in order[:2] + order[127:129] + order[-1:]:
+        s = systems[i]
+        ref = oracle.heun(s.x0, 0, nsteps, dt=s.dt, mobility=MOB[s.mobility], **s.phys())
+        x = hs[i].positions()
+        assert hs[i].get_time()[0] == nsteps
+        assert np.abs(x - ref).max() <= 1e-6 * s.ell
+    for h in hs:
+        assert np.isfinite(h.positions()).all()
         h.close()
 
 
