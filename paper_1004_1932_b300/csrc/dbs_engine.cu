@@ -49,6 +49,7 @@ struct Request {
     bool cluster = false;
     int64_t inflight = 0;          // grid path: steps launched, not yet accounted
     cudaEvent_t ev = nullptr;      // grid path: recorded after the last launch
+    cudaStream_t stream = nullptr; // the request's stream (least priority), owned by the engine
 };
 
 size_t request_bytes(int64_t S, int32_t precision)
@@ -99,6 +100,10 @@ static void release(dbs_engine *e, Request &r)
     if (r.ev) {
         cudaEventDestroy(r.ev);
         r.ev = nullptr;
+    }
+    if (r.stream) {
+        cudaStreamDestroy(r.stream);
+        r.stream = nullptr;
     }
     r.inflight = 0;
 }
@@ -218,7 +223,14 @@ int dbs_engine_tick(dbs_engine *e, int32_t *active, int32_t *pending)
         if (e->P.max_active > 0 && (int32_t)e->active.size() >= e->P.max_active) break;
         if (e->P.hbm_budget_bytes > 0 && e->used + r.bytes > e->P.hbm_budget_bytes) break;
         e->queue.pop_front();
-        int rc = dbs_create_suspension(&r.p, r.x0.data(), &r.h);
+        // each request on a stream of the least priority: the ensemble of the
+        // small ones (greatest priority) is scheduled ahead of large single systems
+        int rc = DBS_OK, least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&r.stream, cudaStreamNonBlocking, least) != cudaSuccess)
+            rc = DBS_E_CUDA;
+        r.p.stream = r.stream;
+        if (rc == DBS_OK) rc = dbs_create_suspension(&r.p, r.x0.data(), &r.h);
         if (rc == DBS_OK) rc = dbs_set_stroke(r.h, r.lam.data(), r.phi.data());
         if (rc == DBS_OK && cudaEventCreateWithFlags(&r.ev, cudaEventDisableTiming) != cudaSuccess)
             rc = DBS_E_CUDA;

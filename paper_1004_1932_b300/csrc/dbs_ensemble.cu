@@ -159,7 +159,11 @@ static int build_classes(dbs_ensemble *e)
         Class &c = kv.second;
         ECK(e, cudaMalloc(&c.csys, sizeof(int) * c.members.size()));
         ECK(e, cudaMemcpy(c.csys, c.members.data(), sizeof(int) * c.members.size(), cudaMemcpyHostToDevice));
-        ECK(e, cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
+        // the greatest priority: where an ensemble shares the device with large
+        // single systems (the serving engine), its blocks are scheduled first
+        int least = 0, greatest = 0;
+        ECK(e, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        ECK(e, cudaStreamCreateWithPriority(&c.stream, cudaStreamNonBlocking, greatest));
         ECK(e, cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming));
         const void *k = pick_kernel(kv.first.mob, kv.first.nt);
         ECK(e, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT));
