@@ -31,6 +31,11 @@ namespace {
 
 thread_local char g_eng_error[256] = "";
 
+#ifndef DBS_ENGINE_GRID_INFLIGHT
+#define DBS_ENGINE_GRID_INFLIGHT 2
+#endif
+constexpr int kGridInflight = DBS_ENGINE_GRID_INFLIGHT;   // grid-path blocks in flight at once
+
 double now_s()
 {
     using namespace std::chrono;
@@ -330,9 +335,24 @@ int dbs_engine_tick(dbs_engine *e, int32_t *active, int32_t *pending)
             e->ens_busy = true;
         }
     }
+    // grid-path requests (each fills the device on its own): at most kGridInflight
+    // of them have a block in flight, the ones with the least remaining work first
+    std::vector<int64_t> idle;
+    int busy = 0;
     for (int64_t id : e->active) {
+        const Request &r = e->req[id];
+        if (r.cluster || r.state != DBS_REQ_RUNNING) continue;
+        if (r.inflight > 0) ++busy;
+        else if (r.remaining > 0) idle.push_back(id);
+    }
+    auto work = [&](int64_t id) {
+        const Request &r = e->req[id];
+        return (double)r.remaining * (double)r.p.S * (double)r.p.S;
+    };
+    std::stable_sort(idle.begin(), idle.end(), [&](int64_t a, int64_t b) { return work(a) < work(b); });
+    for (int64_t id : idle) {
+        if (busy >= kGridInflight) break;
         Request &r = e->req[id];
-        if (r.cluster || r.state != DBS_REQ_RUNNING || r.inflight > 0 || r.remaining == 0) continue;
         const int64_t k = std::min<int64_t>(r.remaining, e->P.block_steps);
         if (dbs_step(r.h, k) != DBS_OK || cudaEventRecord(r.ev, r.h->stream) != cudaSuccess) {
             r.state = DBS_REQ_FAILED;
@@ -340,6 +360,7 @@ int dbs_engine_tick(dbs_engine *e, int32_t *active, int32_t *pending)
             continue;
         }
         r.inflight = k;
+        ++busy;
     }
     if (active) *active = (int32_t)e->active.size();
     if (pending) *pending = (int32_t)e->queue.size();
