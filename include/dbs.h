@@ -425,8 +425,11 @@ DBS_API int dbs_engine_submit(dbs_engine *e, const dbs_params *p, const double *
 /* Admit queued requests; wait until some block in flight completes (the one
  * ensemble of all cluster-path requests, or one grid-path request's block)
  * and count its steps; retire finished requests; launch the next block of up
- * to block_steps Heun steps of every idle resident request.  Blocks complete
- * independently, so a small request never waits for a large one's block.
+ * to block_steps Heun steps of every idle resident request (of the requests on
+ * the grid path, each of which fills the device, at most two have a block in
+ * flight at a time, the least remaining work -- steps x S^2 -- first).  Blocks
+ * complete independently, so a small request never waits for a large one's
+ * block.
  * Reports the numbers of resident and queued requests afterwards.
  * DBS_E_TIMEOUT if no block completes within 600 s. */
 DBS_API int dbs_engine_tick(dbs_engine *e, int32_t *active, int32_t *pending);
