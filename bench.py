@@ -365,11 +365,15 @@ def run_ours(args):
     else:
         path_choice = {"path": args.path, "s_per_step": None}
 
+    # the averaged model is independent of the microscopic one until the comparison:
+    # it runs on a stream of its own, on the SMs the microscopic model leaves free
+    sa_stream = torch.cuda.Stream(device=dev)
+
     def make():
         h = dbs.Suspension.from_inputs(s, precision="fp32c", stream=stream, device=local)
         h.set_path(path_choice["path"])
         sa = dbs.StrokeAveraged(s.R0, s.N0, s.phi, s.lam, a=s.a, ell=s.ell, omega=s.omega,
-                                dt=dt_sa, precision="fp32c", stream=stream, device=local)
+                                dt=dt_sa, precision="fp32c", stream=sa_stream, device=local)
         h.enable_period_average(m, max_periods=total_periods)
         return h, sa
 
@@ -377,11 +381,19 @@ def run_ours(args):
     errs = []
 
     def period(h, sa, k):
-        """One benchmark step: stroke period k of the full hot path."""
+        """One benchmark step: stroke period k of the full hot path (the microscopic
+        model on `stream`, the averaged model forked onto `sa_stream` and joined back
+        before the comparison)."""
+        fork = torch.cuda.Event()
+        fork.record(stream)
         h.step(m)
+        sa_stream.wait_event(fork)
         sa.step(SA_STEPS_PER_PERIOD // 2 if k == 0 else SA_STEPS_PER_PERIOD)
         if k == 1:
             sa.copy_centres(sa_ref)
+        join = torch.cuda.Event()
+        join.record(sa_stream)
+        stream.wait_event(join)
         if k >= 2:
             e = dbs.pair_distance_error(S, h.period_average_device(1), h.period_average_device(k),
                                         sa_ref.data_ptr(), sa.centres_device(), stream=stream)
