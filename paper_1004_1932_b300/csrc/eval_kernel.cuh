@@ -31,7 +31,7 @@
 //   DBS_UNROLL_LARGE      the same for CTAs of 256 threads or more (large systems)
 //   DBS_FP32_WARPS_PER_SM resident warps the FP32 kernels are register-capped for
 //   DBS_W2_RCP            w^2 from rcp.approx instead of w*w (slower on B300; off)
-//   DBS_UNIT_ORDER        1: work units in chunk-major order, 0: i-block-major
+//   DBS_UNIT_ORDER        1: work units of large CTAs in chunk-major order, 0: i-block-major
 #ifndef DBS_RPY_W35
 #define DBS_RPY_W35 1
 #endif
@@ -380,17 +380,15 @@ __device__ __forceinline__ void eval_units(const EvalArgs &A, const void *pack_i
     const int units = iblocks * C;
 
     for (int unit = blockIdx.x; unit < units; unit += gridDim.x) {
-#if DBS_UNIT_ORDER
-        // chunk-major: every i-block's last chunk falls in the last wave, so the
-        // i-blocks' fixups run side by side at the end of the launch instead of
-        // piling onto one CTA (a CTA that did a fixup lags and would arrive last,
-        // and do the fixup, in each of its following i-blocks)
-        const int c = unit / iblocks;
-        const int ib_ = unit - c * iblocks;
-#else
-        const int ib_ = unit / C;
-        const int c = unit - ib_ * C;
-#endif
+        // Large CTAs (one per SM): chunk-major, so that every i-block's last chunk
+        // falls in the last wave and the i-blocks' fixups run side by side at the
+        // end of the launch instead of piling onto one CTA (a CTA that did a fixup
+        // lags and would arrive last, and do the fixup, in each of its following
+        // i-blocks).  Smaller CTAs, several per SM, keep i-block-major order (the
+        // other order costs the FP64 kernel 8 registers and one CTA per SM).
+        constexpr bool kChunkMajor = DBS_UNIT_ORDER && BT >= 256;
+        const int c = kChunkMajor ? unit / iblocks : unit % C;
+        const int ib_ = kChunkMajor ? unit - c * iblocks : unit / C;
         const int s = ib_ * BT + tid;
         const bool active = s < S;
         const int db = (int)(((int64_t)S * c) / C);
