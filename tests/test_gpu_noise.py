@@ -47,6 +47,27 @@ def test_noisy_trajectory_matches_oracle(path, precision, tol):
     assert np.abs(x - ref).max() <= tol * s.ell
 
 
+@pytest.mark.parametrize("S", [12, 300, 1000])
+def test_cooperative_noise_every_split_matches_grid_path(S):
+    # the noise instantiation of the cooperative kernel at 16, 4 and 8 dumbbells
+    # per CTA: the same increments as the grid path, trajectories within 1e-6 ell
+    s = inputs.make_suspension(S, seed=40 + S, density=0.002, mobility="rpy") if S > 40 \
+        else inputs.make_suspension(S, seed=40, side=8.0, mobility="rpy")
+    kT, seed, nsteps = _kT_for(s), 777, 200
+    with _handle(s, "fp32c") as hg:
+        hg.set_noise(kT, seed)
+        hg.step(nsteps)
+        xg = hg.positions()
+    with _handle(s, "fp32c") as hc:
+        hc.set_path("coop")
+        hc.set_noise(kT, seed)
+        hc.step(nsteps)
+        xc = hc.positions()
+        T = hc.get_launch()["bt"]
+    assert T == {12: 16, 300: 4, 1000: 8}[S]
+    assert np.abs(xc - xg).max() <= 1e-6 * s.ell
+
+
 def test_zero_temperature_is_the_deterministic_path():
     s = inputs.make_suspension(24, seed=6, side=9.0)
     with _handle(s) as h:
