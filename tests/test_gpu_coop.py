@@ -46,7 +46,7 @@ def test_coop_path_follows_oracle(S, mob):
     assert np.abs(x - ref).max() <= 1e-4 * s.ell
 
 
-@pytest.mark.parametrize("S", [64, 512, 2048])
+@pytest.mark.parametrize("S", [64, 256, 512, 1024, 2048])   # 1, 2, 4, 8, 16 dumbbells per CTA
 def test_coop_path_matches_grid_path(S):
     s = inputs.paper_scale(S, seed=5)
     nsteps = 300
