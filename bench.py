@@ -269,11 +269,11 @@ def serving_measure(dbs, inputs, n_req=48, rate=200.0, steps_lo=1e3, steps_hi=1e
         busy += run
         lat_seq.append(t_free - arr)
     lat_seq.sort()
-    # the same, each request on its fastest single-system path (cooperative for S <= 2048)
+    # the same, each request on its fastest single-system path (cooperative for S <= 4096)
     t_free_c, lat_c, busy_c = 0.0, [], 0.0
     for arr, S, n, rid in trace:
         with dbs.Suspension.from_inputs(susp[rid], precision="fp32c") as h:
-            if S <= 2048:
+            if S <= 4096:
                 h.set_path("coop")
             h.sync()
             ts = time.perf_counter()
@@ -294,7 +294,7 @@ def serving_measure(dbs, inputs, n_req=48, rate=200.0, steps_lo=1e3, steps_hi=1e
                        "p50_latency_s": q(lat, 0.5), "p99_latency_s": q(lat, 0.99)},
             "one_at_a_time": {"path": "grid", "makespan_s": t_free, "system_steps_per_s": total_steps / busy,
                               "p50_latency_s": q(lat_seq, 0.5), "p99_latency_s": q(lat_seq, 0.99)},
-            "one_at_a_time_fastest_path": {"path": "cooperative (S <= 2048), grid", "makespan_s": t_free_c,
+            "one_at_a_time_fastest_path": {"path": "cooperative (S <= 4096), grid", "makespan_s": t_free_c,
                                            "system_steps_per_s": total_steps / busy_c,
                                            "p50_latency_s": q(lat_c, 0.5), "p99_latency_s": q(lat_c, 0.99)}}
 

@@ -337,11 +337,12 @@ DBS_API int dbs_pair_distance_error(int64_t S, const double *A0_dev, const doubl
  *                    memory, point to point, with no grid-wide barrier.  Every
  *                    wait is bounded (about one second): a launch whose
  *                    exchange cannot complete ends with DBS_E_TIMEOUT instead
- *                    of hanging.  FP32C, S <= 2048.  dbs_set_chunks(c) on this
+ *                    of hanging.  FP32C, S <= 4096 (every CTA holds all
+ *                    records in shared memory).  dbs_set_chunks(c) on this
  *                    path (1 <= c <= 16) asks for T = the largest power of two
- *                    not above c, raised until ceil(S / T) CTAs fit the SMs;
- *                    0 restores the built-in choice (the smallest T that fits;
- *                    16 for S <= 16).
+ *                    not above c, raised until ceil(S / T) CTAs fit the SMs
+ *                    (T <= 32); 0 restores the built-in choice (the smallest T
+ *                    that fits; 16 for S <= 16).
  */
 #define DBS_PATH_COOP 2
 DBS_API int dbs_set_path(dbs_suspension *h, int32_t path, int32_t cluster_size);

@@ -678,7 +678,8 @@ int dbs_set_external_force(dbs_suspension *h, const double *F)
 #define DBS_FLOW_THREADS 256
 #endif
 constexpr int FLOW_THREADS = DBS_FLOW_THREADS;   // threads per CTA of flow_kernel
-constexpr int FLOW_MAX_T = 16;        // dumbbells per CTA at most
+constexpr int FLOW_MAX_T = 32;        // dumbbells per CTA at most
+constexpr int64_t FLOW_MAX_S = 4096;  // all records of a suspension in one CTA's shared memory
 constexpr int FLOW_MAX_STEPS = 1024;  // Heun steps per launch
 
 static void drop_flow(dbs_suspension *h)
@@ -696,6 +697,7 @@ static const void *flow_pick(int T)
     case 4: return (const void *)flow_kernel<MOB, 4, NOISE, FLOW_THREADS>;
     case 8: return (const void *)flow_kernel<MOB, 8, NOISE, FLOW_THREADS>;
     case 16: return (const void *)flow_kernel<MOB, 16, NOISE, FLOW_THREADS>;
+    case 32: return (const void *)flow_kernel<MOB, 32, NOISE, FLOW_THREADS>;
     default: return nullptr;
     }
 }
@@ -729,15 +731,15 @@ static cudaLaunchConfig_t flow_config(const dbs_suspension *h, int G, int T, cud
 // a tiny system) for which all ceil(S / T) CTAs fit the SMs, one CTA each.
 int coop_setup(dbs_suspension *h)
 {
-    if (h->p.precision != DBS_FP32C || h->S > SMALL_S)
-        return refuse(h, DBS_E_ARG, "cooperative path needs FP32C and S <= 2048");
+    if (h->p.precision != DBS_FP32C || h->S > FLOW_MAX_S)
+        return refuse(h, DBS_E_ARG, "cooperative path needs FP32C and S <= 4096");
     int coop = 0, sms = 0, optin = 0;
     CK(h, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device));
     CK(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
     CK(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     if (!coop) return refuse(h, DBS_E_ARG, "device without cooperative launch");
     // tiny systems: one CTA holds all dumbbells and no record leaves it
-    int T = h->S <= FLOW_MAX_T ? FLOW_MAX_T : 1;
+    int T = h->S <= 16 ? 16 : 1;
     if (h->flow_creq > 0) {
         T = 1;
         while (2 * T <= std::min(h->flow_creq, FLOW_MAX_T)) T *= 2;

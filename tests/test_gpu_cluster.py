@@ -137,7 +137,7 @@ def test_ensemble_rejects_fp64_members():
 
 
 def test_cluster_path_refusal_leaves_handle_usable():
-    s = inputs.make_suspension(4000, seed=2, density=0.002)
+    s = inputs.make_suspension(5000, seed=2, density=0.002)   # beyond both the cluster and cooperative paths
     h = dbs.Suspension(s.x0, a=s.a, mu=s.mu, k0=s.k0, ell=s.ell, omega=s.omega, dt=s.dt,
                        precision="fp32c", lam=s.lam, phi=s.phi)
     with pytest.raises(dbs.DbsError) as ei:

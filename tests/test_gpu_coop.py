@@ -46,7 +46,7 @@ def test_coop_path_follows_oracle(S, mob):
     assert np.abs(x - ref).max() <= 1e-4 * s.ell
 
 
-@pytest.mark.parametrize("S", [64, 256, 512, 1024, 2048])   # 1, 2, 4, 8, 16 dumbbells per CTA
+@pytest.mark.parametrize("S", [64, 256, 512, 1024, 2048, 2300, 4096])   # 1 .. 32 dumbbells per CTA
 def test_coop_path_matches_grid_path(S):
     s = inputs.paper_scale(S, seed=5)
     nsteps = 300
@@ -142,7 +142,7 @@ def test_coop_tag_wraparound(tag):
 
 
 def test_coop_refuses_what_it_cannot_hold():
-    s = inputs.make_suspension(2049, seed=2, density=0.002)
+    s = inputs.make_suspension(4097, seed=2, density=0.002)
     with _handle(s) as h:
         with pytest.raises(dbs.DbsError) as ei:
             h.set_path("coop")
