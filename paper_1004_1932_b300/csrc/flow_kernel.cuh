@@ -27,14 +27,15 @@
 // touches another CTA's shared memory, so a CTA may leave early.
 //
 // Precision (FP32C).  Pair sums in FP32 with two-sum folding, as in
-// eval_kernel.  Positions (relative to the suspension's centre), the Heun
-// update and the stroke-average sums are FP64.  An FP64 instruction holds its
-// sub-partition for 64 cycles on this part, so the epilogue spreads that work
-// over three warps, one per axis, each on its own sub-partition.  The rest
-// length L and d^2 = |x_b - x_a|^2 (from the FP64 difference) are formed as
-// unevaluated FP32 pairs hi + lo (double-single: Dekker's two-sum and the FMA
-// two-product), so the small stretch d - L = (d^2 - L^2)/(d + L) keeps FP32
-// relative accuracy; the force and the velocity are FP32, as in the records.
+// eval_kernel.  Positions (relative to the suspension's centre), their Heun
+// update and the stroke-average sums are FP64; an FP64 instruction holds its SM
+// sub-partition for 64 cycles on this part, so that work runs after the records
+// are published, spread over three warps (one per axis).  The critical path
+// takes the Heun step on a double-single copy of the positions (refreshed from
+// the FP64 state at every launch); the rest length L and d^2 = |x_b - x_a|^2
+// are double-single pairs hi + lo (Dekker's two-sum and the FMA two-product),
+// so the small stretch d - L = (d^2 - L^2)/(d + L) keeps FP32 relative
+// accuracy; the force and the velocity are FP32, as in the records.
 #pragma once
 #include "dbs_common.cuh"
 #include "eval_kernel.cuh"
@@ -251,7 +252,7 @@ __device__ __forceinline__ void ts_merge(float &s, float &c, float s2, float c2)
 // The three normals of one sphere at step n into z[0], z[stride], z[2 stride]
 // (out of line: the per-evaluation code stays short).
 __device__ __noinline__ void draw_sphere_normals(unsigned long long seed, int64_t n, int64_t sphere,
-                                                   float *z, int stride)
+                                                 float *z, int stride)
 {
     float w[3];
     sphere_normals(seed, n, sphere, w);
