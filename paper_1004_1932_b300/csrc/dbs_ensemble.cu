@@ -25,6 +25,10 @@
 
 using namespace dbs;
 
+#ifndef DBS_ENS_HEAVY_FIRST
+#define DBS_ENS_HEAVY_FIRST 1
+#endif
+
 namespace {
 
 constexpr int K_BLOCK = 1024;     // Heun steps per resident launch (< clock ring / 2)
@@ -157,6 +161,12 @@ static int build_classes(dbs_ensemble *e)
     }
     for (auto &kv : e->classes) {
         Class &c = kv.second;
+        if (DBS_ENS_HEAVY_FIRST) {
+            // heaviest members (pair work ~ S^2) first: their clusters get the lowest
+            // block indices and are dispatched first
+            std::stable_sort(c.members.begin(), c.members.end(),
+                             [&](int a, int b) { return e->m[a]->S > e->m[b]->S; });
+        }
         ECK(e, cudaMalloc(&c.csys, sizeof(int) * c.members.size()));
         ECK(e, cudaMemcpy(c.csys, c.members.data(), sizeof(int) * c.members.size(), cudaMemcpyHostToDevice));
         // the greatest priority: where an ensemble shares the device with large
@@ -221,7 +231,20 @@ static ResSys make_sys(const dbs_suspension *h, int G)
 static int enqueue_launches(dbs_ensemble *e)
 {
     ECK(e, cudaEventRecord(e->fork, e->stream));
-    for (auto &kv : e->classes) {
+    // classes in decreasing order of pair work (sum of S^2), so that the heaviest,
+    // which set the batch's time, are dispatched first
+    std::vector<std::pair<const ClassKey, Class> *> order;
+    for (auto &kv : e->classes) order.push_back(&kv);
+    auto work = [&](const Class &c) {
+        double w = 0;
+        for (int i : c.members) w += (double)e->m[i]->S * (double)e->m[i]->S;
+        return w;
+    };
+    if (DBS_ENS_HEAVY_FIRST)
+        std::stable_sort(order.begin(), order.end(),
+                         [&](auto *a, auto *b) { return work(a->second) > work(b->second); });
+    for (auto *kvp : order) {
+        auto &kv = *kvp;
         Class &c = kv.second;
         ECK(e, cudaStreamWaitEvent(c.stream, e->fork, 0));
         cudaLaunchConfig_t cfg{};
