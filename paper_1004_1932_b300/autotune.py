@@ -1,5 +1,6 @@
-"""Autotuner for the pair-sum launch: picks the j-split (chunks) of a suspension
-by timing candidate splits on the device and caches the winner.
+"""Autotuners: the j-split (chunks) of the grid path's pair-sum launch, the
+stepping path of a suspension (with the cooperative path's split), and the
+cluster sizes of an ensemble, each chosen by timing candidates on the device.
 
 The kernel's work units are (i-block of dumbbells) x (j-chunk); how many
 chunks fill the 148 SMs best depends on S, precision, mobility and occupancy
@@ -89,8 +90,9 @@ def tune(h: "dbs.Suspension", *, device_name: str = "cuda", precision: str = "fp
 
 def choose_path(h: "dbs.Suspension", steps: int = 1024) -> dict:
     """Time ``steps`` Heun steps on the grid, cluster and cooperative paths (where the
-    suspension fits it) and keep the faster.  The suspension's state is restored
-    to where it started, so the choice does not change the trajectory."""
+    suspension fits it), the cooperative one at its built-in split and at 4, 8 and 16
+    dumbbells per CTA, and keep the fastest.  The suspension's state is restored to
+    where it started, so the choice does not change the trajectory."""
     import time
     x0, n0 = h.get_state()
     timings = {}
