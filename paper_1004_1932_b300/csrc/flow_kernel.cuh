@@ -29,8 +29,10 @@
 // Precision (FP32C).  Pair sums in FP32 with two-sum folding, as in
 // eval_kernel.  Positions (relative to the suspension's centre), their Heun
 // update and the stroke-average sums are FP64; an FP64 instruction holds its SM
-// sub-partition for 64 cycles on this part, so that work runs after the records
-// are published, spread over three warps (one per axis).  The critical path
+// sub-partition for 64 cycles on this part, so that work is kept off the
+// critical path: the corrector leaves its inputs in registers of the three axis
+// warps, and the next poll runs it while its first round of loads is in flight
+// (it costs no time there: those warps wait for records anyway).  The critical path
 // takes the Heun step on a double-single copy of the positions (refreshed from
 // the FP64 state at every launch); the rest length L and d^2 = |x_b - x_a|^2
 // are double-single pairs hi + lo (Dekker's two-sum and the FMA two-product),
@@ -146,17 +148,20 @@ __device__ __forceinline__ ds ds_neg(ds a) { return {-a.h, -a.l}; }
 // loads are kept in flight, the second issued `stagger` cycles after the first,
 // so every word is read twice per memory round trip: a word that becomes
 // visible just after one round passed it is seen by the other about half a
-// round trip later.  False on timeout or abort (see wait_tagged).
-template <int NB, int NT>
+// round trip later.  `gap()` runs between the two rounds, while the first is in
+// flight (it may take longer than `stagger`).  False on timeout or abort (see
+// wait_tagged).
+template <int NB, int NT, class Gap>
 __device__ __forceinline__ bool poll_staggered(const ulonglong2 *base, float *dst, unsigned pending,
                                                unsigned tag, int *flags, unsigned long long timeout_ns,
-                                               int stagger)
+                                               int stagger, Gap &&gap)
 {
     ulonglong2 va[NB], vb[NB];
 #pragma unroll
     for (int j = 0; j < NB; ++j)
         if ((pending >> j) & 1u) va[j] = ld_tagged(base + j * NT);
     const long long c0 = clock64();
+    gap();
     while (clock64() - c0 < stagger) {
     }
     unsigned long long t0 = 0;
@@ -327,6 +332,42 @@ __global__ void __launch_bounds__(NT, 1) flow_kernel(const EvalArgs A, const Flo
     const int s_me = st0 + t_me;
     const bool act = t_me < nown;
 
+    // The FP64 Heun update x_{n+1} = x_n + dt/2 (v0 + v1) (+ noise) of the state
+    // and the stroke average of the geometric centre (trapezoid rule) stay off the
+    // critical path: a corrector evaluation leaves their inputs in registers (hn =
+    // its step n), and the next poll runs them while its first round of loads is in
+    // flight (the end of the launch runs the last one).
+    float hsa = 0.f, hsb = 0.f, hza = 0.f, hzb = 0.f;   // v0 + v1 and the normals along a
+    int64_t hn = -1;                                    // -1: nothing pending
+    auto flush_fp64 = [&]() {
+        if (hn < 0) return;
+        const int a = warp, d = lane;
+        double xa = fma(0.5 * A.dt, (double)hsa, own.x[a][d]);
+        double xb = fma(0.5 * A.dt, (double)hsb, own.x[a + 3][d]);
+        if (NOISE) {
+            xa = fma(A.noise_sigma, (double)hza, xa);
+            xb = fma(A.noise_sigma, (double)hzb, xb);
+        }
+        own.x[a][d] = xa;
+        own.x[a + 3][d] = xb;
+        if (!(finite1(xa) && finite1(xb))) atomicOr(A.flags, FLAG_NONFINITE);
+        const int64_t k_local = hn + 1 - A.avg_n0;
+        if (A.avg_m > 0 && k_local > 0) {
+            const double Rt = 0.5 * (xa + xb) + (a == 0 ? A.cx : (a == 1 ? A.cy : A.cz));
+            double acc = own.R[a][d];
+            if ((k_local % A.avg_m) == 0) {
+                acc += 0.5 * Rt;
+                const int64_t kidx = k_local / A.avg_m - 1;
+                if (kidx < A.avg_maxk) A.Rbar[kidx * 3 * A.S + 3 * (int64_t)(st0 + d) + a] = acc / (double)A.avg_m;
+                acc = 0.5 * Rt;
+            } else {
+                acc += Rt;
+            }
+            own.R[a][d] = acc;
+        }
+        hn = -1;
+    };
+
     bool dead = false;
     for (int ev = 0; ev < 2 * P.K && !dead; ++ev) {
         const unsigned tag = P.base + (unsigned)ev;
@@ -359,8 +400,9 @@ __global__ void __launch_bounds__(NT, 1) flow_kernel(const EvalArgs A, const Flo
                 if (idx < nwords && (idx < own_w0 || idx >= own_w1)) pend |= 1u << j;
             }
             ok = poll_staggered<POLL, NT>(R + b0 + tid, (float *)tile + 2 * (b0 + tid), pend, tag,
-                                          A.flags, P.timeout_ns, DBS_FLOW_STAGGER);
+                                          A.flags, P.timeout_ns, DBS_FLOW_STAGGER, flush_fp64);
         }
+        flush_fp64();   // done in the first gap: ends the live range of its inputs
         dead = __syncthreads_or(!ok);
         if (dead) break;
 
@@ -425,7 +467,6 @@ __global__ void __launch_bounds__(NT, 1) flow_kernel(const EvalArgs A, const Flo
         const int a = warp, d = lane;
         const bool eax = warp < 3 && d < nown;
         float pa = 0.f, pb = 0.f, eh = 0.f;
-        float va1 = 0.f, vb1 = 0.f;  // corrector velocities along a (the FP64 update uses them)
         if (eax) {
             // the target's pair sums along a: its warps' pairs folded in warp order
             float2 ua = red[d * WPT][a], ub = red[d * WPT][a + 3];
@@ -440,20 +481,25 @@ __global__ void __launch_bounds__(NT, 1) flow_kernel(const EvalArgs A, const Flo
             // records and the spring need FP32 accuracy; the FP64 state takes the
             // same Heun update once the records are out)
             ds na = {own.xs[a][d].x, own.xs[a][d].y}, nb = {own.xs[a + 3][d].x, own.xs[a + 3][d].y};
+            // the normals are read before the barrier below: the next predictor
+            // draws the next step's into the same place after it
+            const float za = NOISE ? own.z[a][d] : 0.f, zb = NOISE ? own.z[a + 3][d] : 0.f;
             if (!corr) {
                 own.v0[a][d] = va;
                 own.v0[a + 3][d] = vb;
                 na = ds_add(na, ds_mul_f(dt_ds, va));                             // x~ = x_n + dt v0
                 nb = ds_add(nb, ds_mul_f(dt_ds, vb));
             } else {
-                va1 = va;
-                vb1 = vb;
-                na = ds_add(na, ds_mul_f(hdt_ds, own.v0[a][d] + va));            // x_n + dt/2 (v0 + v1)
-                nb = ds_add(nb, ds_mul_f(hdt_ds, own.v0[a + 3][d] + vb));
+                hsa = own.v0[a][d] + va;
+                hsb = own.v0[a + 3][d] + vb;
+                hza = za;
+                hzb = zb;
+                na = ds_add(na, ds_mul_f(hdt_ds, hsa));                           // x_n + dt/2 (v0 + v1)
+                nb = ds_add(nb, ds_mul_f(hdt_ds, hsb));
             }
             if (NOISE) {
-                na = ds_add(na, ds_mul_f(sig_ds, own.z[a][d]));
-                nb = ds_add(nb, ds_mul_f(sig_ds, own.z[a + 3][d]));
+                na = ds_add(na, ds_mul_f(sig_ds, za));
+                nb = ds_add(nb, ds_mul_f(sig_ds, zb));
             }
             const ds e = ds_add(nb, ds_neg(na));
             const ds e2 = ds_mul(e, e);
@@ -499,43 +545,14 @@ __global__ void __launch_bounds__(NT, 1) flow_kernel(const EvalArgs A, const Flo
                 pk[a] = wp;
                 pk[3 + a] = wg;
             }
-            // off the critical path, once the records are out: the FP64 Heun update
-            // x_{n+1} = x_n + dt/2 (v0 + v1) (+ noise) of the state and the stroke
-            // average of the geometric centre along a (trapezoid rule)
-            double xa = 0.0, xb = 0.0;
-            if (corr) {
-                xa = fma(0.5 * A.dt, (double)(own.v0[a][d] + va1), own.x[a][d]);
-                xb = fma(0.5 * A.dt, (double)(own.v0[a + 3][d] + vb1), own.x[a + 3][d]);
-                if (NOISE) {
-                    xa = fma(A.noise_sigma, (double)own.z[a][d], xa);
-                    xb = fma(A.noise_sigma, (double)own.z[a + 3][d], xb);
-                }
-                own.x[a][d] = xa;
-                own.x[a + 3][d] = xb;
-                if (!(finite1(xa) && finite1(xb))) atomicOr(A.flags, FLAG_NONFINITE);
-            }
-            if (corr && A.avg_m > 0) {
-                const int64_t k_local = n + 1 - A.avg_n0;
-                if (k_local > 0) {
-                    const double Rt = 0.5 * (xa + xb) + (a == 0 ? A.cx : (a == 1 ? A.cy : A.cz));
-                    double acc = own.R[a][d];
-                    if ((k_local % A.avg_m) == 0) {
-                        acc += 0.5 * Rt;
-                        const int64_t kidx = k_local / A.avg_m - 1;
-                        if (kidx < A.avg_maxk) A.Rbar[kidx * 3 * A.S + 3 * (int64_t)(st0 + d) + a] = acc / (double)A.avg_m;
-                        acc = 0.5 * Rt;
-                    } else {
-                        acc += Rt;
-                    }
-                    own.R[a][d] = acc;
-                }
-            }
+            if (corr) hn = n;   // the FP64 update of step n runs in the next poll
         }
         // no barrier here: the next poll writes only records this CTA does not own,
         // and the next sweep starts after the poll's barrier
     }
 
     // ---- write the owned state back ----------------------------------------------
+    flush_fp64();
     __syncthreads();
     if (warp == 0 && lane < nown) {
         const int d = lane, s = st0 + d;
