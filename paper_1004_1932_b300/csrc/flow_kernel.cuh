@@ -431,30 +431,62 @@ __global__ void __launch_bounds__(NT, 1) flow_kernel(const EvalArgs A, const Flo
         }
 
         // 3. fold the slices of each target: FP32 two-sum across the LW lanes of a
-        // warp (butterfly: every lane ends with the same pair), then across the
-        // WPT warps of a target in warp order
-        float sv[6], cv[6];
+        // warp, then across the WPT warps of a target in warp order.  The lanes
+        // fold by transposition: the six components sit in eight slots, and each
+        // of the first three levels halves the slots a lane carries (the lane
+        // whose level bit is clear keeps the lower half and merges its partner's
+        // copy of it into its own, the other lane the upper half), so a level
+        // moves half as many words as the one before; the remaining levels are a
+        // plain butterfly on the one slot left.  14 shuffles per thread at LW = 32
+        // instead of 60 for a butterfly on all six.
+        static_assert(LW >= 8, "the transposing fold needs 8 lanes per target");
+        float fs[8], fc[8];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            sv[k] = qa[k].x + qa[k].y;
-            sv[3 + k] = qb[k].x + qb[k].y;
-            cv[k] = 0.f;
-            cv[3 + k] = 0.f;
+            fs[k] = qa[k].x + qa[k].y;
+            fs[3 + k] = qb[k].x + qb[k].y;
         }
+        fs[6] = 0.f;
+        fs[7] = 0.f;
+        int ci = 0;   // first slot (component) this lane still carries
+        {   // 8 -> 4 slots; the slice sums carry no compensation yet
+            const bool hi = (lane & (LW / 2)) != 0;
 #pragma unroll
-        for (int off = LW / 2; off >= 1; off >>= 1) {
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                const float s2 = __shfl_xor_sync(0xffffffffu, sv[k], off);
-                const float cc2 = __shfl_xor_sync(0xffffffffu, cv[k], off);
-                ts_merge(sv[k], cv[k], s2, cc2);
+            for (int k = 0; k < 4; ++k) {
+                const float send = hi ? fs[k] : fs[k + 4];
+                const float keep = hi ? fs[k + 4] : fs[k];
+                const float r = __shfl_xor_sync(0xffffffffu, send, LW / 2);
+                fs[k] = keep;
+                fc[k] = 0.f;
+                ts_merge(fs[k], fc[k], r, 0.f);
             }
+            ci += hi ? 4 : 0;
         }
-        // one pair per (target, warp): the epilogue folds the WPT warps of a target
-        if (WPT == 1 ? sl == 0 : lane == 0) {
 #pragma unroll
-            for (int k = 0; k < 6; ++k) red[WPT == 1 ? t_me : warp][k] = make_float2(sv[k], cv[k]);
+        for (int h = 2; h >= 1; h >>= 1) {   // 4 -> 2 -> 1 slots
+            const int off = LW / (8 / h);
+            const bool hi = (lane & off) != 0;
+#pragma unroll
+            for (int k = 0; k < h; ++k) {
+                const float ss = hi ? fs[k] : fs[k + h], sc = hi ? fc[k] : fc[k + h];
+                const float ks = hi ? fs[k + h] : fs[k], kc = hi ? fc[k + h] : fc[k];
+                const float rs = __shfl_xor_sync(0xffffffffu, ss, off);
+                const float rc = __shfl_xor_sync(0xffffffffu, sc, off);
+                fs[k] = ks;
+                fc[k] = kc;
+                ts_merge(fs[k], fc[k], rs, rc);
+            }
+            ci += hi ? h : 0;
         }
+#pragma unroll
+        for (int off = LW / 16; off >= 1; off >>= 1) {
+            const float rs = __shfl_xor_sync(0xffffffffu, fs[0], off);
+            const float rc = __shfl_xor_sync(0xffffffffu, fc[0], off);
+            ts_merge(fs[0], fc[0], rs, rc);
+        }
+        // one pair per (target, warp, component): the epilogue folds the WPT warps
+        // of a target
+        if ((lane & (LW / 8 - 1)) == 0 && ci < 6) red[WPT == 1 ? t_me : warp][ci] = make_float2(fs[0], fc[0]);
         __syncthreads();
 
         // 4. epilogue.  Warps 0-2 take axis a = warp of the owned dumbbells (lane d):
