@@ -40,7 +40,7 @@ SA_STEPS_PER_PERIOD = 10
 FLOPS_PER_PAIR = {"oseen": 27, "rpy": 34}   # algorithmic FP32 flops (FMA = 2), rsqrt not counted
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture of
 # the same launch (profiles/flow_kernel_rpy_s512_n1024.md): 1024 Heun steps, S = 512, RPY
-NCU_TRAFFIC = {("coop", 512, "rpy"): 222208 + 34048}
+NCU_TRAFFIC = {("coop", 512, "rpy"): 424704 + 33792}
 METRIC = "sphere-pair interactions/s"
 
 
