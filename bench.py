@@ -60,6 +60,8 @@ def _args():
                    help="stepping path of the microscopic model (auto: the autotuner times all three)")
     p.add_argument("--cpu-sample-steps", type=int, default=400,
                    help="Heun steps of the oracle timed for the CPU baseline")
+    p.add_argument("--no-cpu-sweep", action="store_true",
+                   help="skip the oracle's timings on the other workloads (cpu_baseline.sweep)")
     return p.parse_args()
 
 
@@ -161,6 +163,60 @@ def _cpu_baseline(S, mobility, nsteps):
             "kind": "oracle",
             "sample": f"{nsteps} Heun steps of the same S={S} suspension (FP64 C oracle, OpenMP over "
                       f"targets), {el:.2f} s"}
+
+
+def _cpu_sweep(mobility):
+    """The oracle on the other workloads, each on a bounded sample (about 10 s in all):
+    the paper-scale suspension on one thread, the small FP64 Oseen suspension per Heun
+    step, one velocity evaluation at N = 4096 and 16384 (N = 65536 scaled from 16384 by
+    N^2, the pair loop being exactly N(N-1) terms), and the 256-system ensemble from 10
+    Heun steps of every 8th member, scaled by its pair count."""
+    import oracle
+    from paper_1004_1932_b300 import inputs
+    cores = os.cpu_count()
+    mob = oracle.RPY if mobility == "rpy" else oracle.OSEEN
+
+    def heun_rate(s, nsteps, threads, m=mob):
+        oracle.set_threads(threads)
+        oracle.heun(s.x0, 0, 1, dt=s.dt, mobility=m, **s.phys())
+        t0 = time.perf_counter()
+        oracle.heun(s.x0, 0, nsteps, dt=s.dt, mobility=m, **s.phys())
+        return (time.perf_counter() - t0) / nsteps
+
+    out = {"cores_all": cores}
+    s = inputs.paper_scale(512, seed=0, mobility=mobility)
+    el = heun_rate(s, 10, 1)
+    out["paper_scale_s512_one_thread"] = {"pairs_per_s": 2 * 1024 * 1023 / el, "ms_per_heun_step": 1e3 * el,
+                                          "sample": "10 Heun steps"}
+    s1 = inputs.small_fp64_oseen(0)
+    out["small_s16_oseen_fp64"] = {
+        "us_per_heun_step_one_thread": 1e6 * heun_rate(s1, 1000, 1, oracle.OSEEN),
+        "us_per_heun_step_all_cores": 1e6 * heun_rate(s1, 1000, cores, oracle.OSEEN),
+        "sample": "1000 Heun steps"}
+    oracle.set_threads(cores)
+    ev = []
+    for S in (2048, 8192):
+        sl = inputs.paper_scale(S, seed=0, mobility=mobility)
+        t0 = time.perf_counter()
+        oracle.velocities(sl.x0, 0.0, mobility=mob, **sl.phys())
+        el = time.perf_counter() - t0
+        N = 2 * S
+        ev.append({"N": N, "s_all_cores": el, "pairs_per_s": N * (N - 1) / el})
+    N = 65536
+    ev.append({"N": N, "s_all_cores": ev[-1]["s_all_cores"] * (N * (N - 1)) / (16384 * 16383),
+               "scaled": "from N = 16384 by N(N-1)"})
+    out["velocity_evaluation"] = ev
+    systems = inputs.ensemble(256)
+    pairs_all = sum(2 * (2 * m.S) * (2 * m.S - 1) for m in systems)
+    sample = systems[::8]
+    pairs_sample = sum(2 * (2 * m.S) * (2 * m.S - 1) for m in sample)
+    t0 = time.perf_counter()
+    for m in sample:
+        oracle.heun(m.x0, 0, 10, dt=m.dt, mobility=mob, **m.phys())
+    el = (time.perf_counter() - t0) / 10 * pairs_all / pairs_sample
+    out["ensemble_256"] = {"s_per_step_all_cores": el, "system_steps_per_s": 256 / el,
+                           "sample": "10 Heun steps of members 0, 8, ..., 248, scaled by pair count"}
+    return out
 
 
 def ensemble_measure(dbs, inputs, torch, stream, steps=1000, count=256):
@@ -530,6 +586,8 @@ def run_ours(args):
     if rank != 0:
         return
     cpu = _cpu_baseline(S, args.mobility, args.cpu_sample_steps) if ws == 1 else None
+    if cpu is not None and not args.no_cpu_sweep:
+        cpu["sweep"] = _cpu_sweep(args.mobility)
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
