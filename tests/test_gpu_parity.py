@@ -214,10 +214,11 @@ def test_stroke_averaged_rates_and_steps(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp32c", "fp64"])
-@pytest.mark.parametrize("S", [2, 33, 129, 300, 1000, 2500])
+@pytest.mark.parametrize("S", [2, 33, 129, 300, 1000, 2500, 5000])
 def test_stroke_averaged_rates_sizes(S, prec):
     # every split of the averaged-model kernel (1 .. 32 targets per CTA), ragged
-    # last CTAs and tiles, against the oracle's rates
+    # last CTAs and tiles, against the oracle's rates; S = 5000 has more CTAs
+    # than SMs (the plain-launch branch, state loaded in the epilogue)
     s = inputs.paper_scale(S, seed=21 + S)
     kw = dict(a=s.a, ell=s.ell, omega=s.omega)
     Rd_ref, Nd_ref = oracle.sa_rates(s.R0, s.N0, s.phi, s.lam, **kw)
