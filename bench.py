@@ -522,9 +522,11 @@ def run_ours(args):
     sa.close()
 
     # ---- the same kernel on large single systems: FP32C vs all-FP64 ----------------
-    # (S = 2048, 8192, 32768; one pair-sum launch of the grid path, CUDA events)
+    # (S = 2048, 8192, 32768; one pair-sum launch of the grid path, CUDA events),
+    # and 100 Heun steps of each size on its autotuned stepping path (FP32C)
     large = None
     if not args.no_large:
+        from paper_1004_1932_b300 import autotune
         fp64_peak = props.multi_processor_count * 2 * 2 * mhz_max * 1e6 / 1e12   # 2 DFMA/clk/SM
         sweep = []
         for Sl in (2048, 8192, 32768):
@@ -541,6 +543,20 @@ def run_ours(args):
                              "achieved_tflops": ach_l,
                              "frac_of_fp32_peak": ach_l / peak,
                              **({"frac_of_fp64_peak": ach_l / fp64_peak} if prec == "fp64" else {})}
+            hl = dbs.Suspension.from_inputs(sl, precision="fp32c", stream=stream, device=local)
+            choice = autotune.choose_path(hl, steps=100)
+            hl.step(8)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            hl.step(100)
+            ev1.record(stream)
+            ev1.synchronize()
+            hl.close()
+            el = ev0.elapsed_time(ev1) / 1e3 / 100
+            ach_s = 2 * Nl * (Nl - 1) * FLOPS_PER_PAIR[args.mobility] / el / 1e12
+            row["fp32c_stepping"] = {"path": choice["path"], "heun_steps": 100, "us_per_heun_step": el * 1e6,
+                                     "pairs_per_s": 2 * Nl * (Nl - 1) / el, "achieved_tflops": ach_s,
+                                     "frac_of_fp32_peak": ach_s / peak}
             sweep.append(row)
         top = sweep[-1]["fp32c"]
         large = {"workload": "single suspension S=32768 (N=65536), density 0.002, same kernel",
@@ -548,7 +564,9 @@ def run_ours(args):
                  "unit": "TFLOP/s", "frac": top["frac_of_fp32_peak"], "pairs_per_s": top["pairs_per_s"],
                  "size_sweep": sweep,
                  "fp64_peak_tflops": fp64_peak,
-                 "note": "one pair-sum launch (grid path); FP64 peak = SMs x 2 DFMA/clk x 2 x max clock"}
+                 "note": "one pair-sum launch (grid path); FP64 peak = SMs x 2 DFMA/clk x 2 x max clock; "
+                         "fp32c_stepping: 100 Heun steps (two evaluations each, fused epilogues) on the "
+                         "autotuned path, CUDA events"}
 
     # ---- end to end through the C-ABI with host buffers -----------------------
     e2e = None
