@@ -38,6 +38,10 @@ sys.path.insert(0, ROOT)
 STEPS_PER_PERIOD = 1000
 SA_STEPS_PER_PERIOD = 10
 FLOPS_PER_PAIR = {"oseen": 27, "rpy": 34}   # algorithmic FP32 flops (FMA = 2), rsqrt not counted
+# the stroke-averaged pair term (Eqs. (9b), (9c)) as the kernel evaluates it: the
+# difference vector, its norm, three projections, the phase factor and the three
+# polynomials, the J and K updates; FMA = 2, rsqrt not counted
+SA_FLOPS_PER_PAIR = 98
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture of
 # the same launch (profiles/flow_kernel_rpy_s512_n1024.md): 1024 Heun steps, S = 512, RPY
 NCU_TRAFFIC = {("coop", 512, "rpy"): 424704 + 33792}
@@ -569,6 +573,28 @@ def run_ours(args):
                          "autotuned path, CUDA events"}
 
     # ---- end to end through the C-ABI with host buffers -----------------------
+    # ---- the stroke-averaged kernel on its own (CUDA events on its stream) --------
+    sa_kernel = None
+    if not args.no_large:
+        sa_kernel = {"kernel": "sa_eval_kernel (stroke-averaged pair sums + FP64 Heun epilogue, "
+                               "2 launches per averaged step)",
+                     "flops_per_pair": SA_FLOPS_PER_PAIR, "peak": peak, "unit": "TFLOP/s", "sizes": []}
+        for Ss, reps in ((S, 200), (8192, 20)):
+            ss = inputs.paper_scale(Ss, seed=rank, mobility=args.mobility)
+            sst = torch.cuda.Stream(device=dev)
+            with dbs.StrokeAveraged(ss.R0, ss.N0, ss.phi, ss.lam, a=ss.a, ell=ss.ell, omega=ss.omega,
+                                    dt=0.1, precision="fp32c", stream=sst) as sk:
+                sk.step(4)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(sst)
+                sk.step(reps)
+                e1.record(sst)
+                e1.synchronize()
+            el = e0.elapsed_time(e1) / 1e3 / reps
+            ach = 2 * Ss * (Ss - 1) * SA_FLOPS_PER_PAIR / el / 1e12
+            sa_kernel["sizes"].append({"S": Ss, "us_per_step": el * 1e6, "achieved": ach,
+                                       "frac": ach / peak})
+
     e2e = None
     if not args.no_e2e:
         x_host = torch.from_numpy(s.x0.copy()).pin_memory()
@@ -630,6 +656,7 @@ def run_ours(args):
         "large_system_kernel": large,
         "ensemble": ensemble,
         "serving": serving,
+        "sa_kernel": sa_kernel,
     }
     print(json.dumps(line), flush=True)
 

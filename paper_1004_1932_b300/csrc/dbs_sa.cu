@@ -124,6 +124,72 @@ __device__ __forceinline__ void sa_pair(bool self, T Rx, T Ry, T Rz, T lam_s, T 
     K[2] += ck * hz;
 }
 
+// FP32: the same pair term for two source records at once with paired f32x2
+// instructions (FFMA2/FMUL2: two IEEE single-precision lanes per instruction),
+// half the issue slots of two scalar calls; lane .x is record q0, .y record q1.
+// The target's fields come duplicated in both lanes.  self0 / self1 mask the
+// target's own record (w = 0 makes its term exactly zero).
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
+
+__device__ __forceinline__ void sa_pair2(bool self0, bool self1, float2 Rx, float2 Ry, float2 Rz, float2 lam_s,
+                                         float2 Nx, float2 Ny, float2 Nz, float2 sn_s, float2 cs_s,
+                                         const SaRecF32 &q0, const SaRecF32 &q1, float2 J[3], float2 K[3])
+{
+    const float2 m1 = f2s(-1.f);
+    const float2 Dx = __ffma2_rn(f2(q0.R.x, q1.R.x), m1, Rx);
+    const float2 Dy = __ffma2_rn(f2(q0.R.y, q1.R.y), m1, Ry);
+    const float2 Dz = __ffma2_rn(f2(q0.R.z, q1.R.z), m1, Rz);
+    float2 D2 = __fmul2_rn(Dx, Dx);
+    D2 = __ffma2_rn(Dy, Dy, D2);
+    D2 = __ffma2_rn(Dz, Dz, D2);
+    const float2 w = f2(self0 ? 0.f : rsqrtf(D2.x), self1 ? 0.f : rsqrtf(D2.y));
+    const float2 hx = __fmul2_rn(Dx, w), hy = __fmul2_rn(Dy, w), hz = __fmul2_rn(Dz, w);
+    const float2 qNx = f2(q0.N.x, q1.N.x), qNy = f2(q0.N.y, q1.N.y), qNz = f2(q0.N.z, q1.N.z);
+    float2 s = __fmul2_rn(hx, Nx);
+    s = __ffma2_rn(hy, Ny, s);
+    s = __ffma2_rn(hz, Nz, s);
+    float2 r = __fmul2_rn(hx, qNx);
+    r = __ffma2_rn(hy, qNy, r);
+    r = __ffma2_rn(hz, qNz, r);
+    float2 qq = __fmul2_rn(Nx, qNx);
+    qq = __ffma2_rn(Ny, qNy, qq);
+    qq = __ffma2_rn(Nz, qNz, qq);
+    // sin(phi^s - phi^r) = sin phi^s cos phi^r - cos phi^s sin phi^r
+    const float2 sd = __ffma2_rn(sn_s, f2(q0.sc.y, q1.sc.y), __fmul2_rn(__fmul2_rn(cs_s, m1), f2(q0.sc.x, q1.sc.x)));
+    const float2 amp = __fmul2_rn(__fmul2_rn(lam_s, f2(q0.R.w, q1.R.w)), sd);
+    const float2 w2 = __fmul2_rn(w, w);
+    const float2 w4 = __fmul2_rn(w2, w2);
+    const float2 s2 = __fmul2_rn(s, s), r2 = __fmul2_rn(r, r);
+    const float2 qr = __fmul2_rn(qq, r), sr2 = __fmul2_rn(s, r2), qq2 = __fmul2_rn(qq, qq);
+    const float2 qsr = __fmul2_rn(qr, s), s3 = __fmul2_rn(s2, s);
+    // pN = 2s + 4 q r - 10 s r^2
+    float2 pN = __ffma2_rn(f2s(4.f), qr, __fmul2_rn(f2s(2.f), s));
+    pN = __ffma2_rn(f2s(-10.f), sr2, pN);
+    // pD = 1 + 2 q^2 - 5 s^2 - 5 r^2 - 20 q s r + 35 s^2 r^2
+    float2 pD = __ffma2_rn(f2s(2.f), qq2, f2s(1.f));
+    pD = __ffma2_rn(f2s(-5.f), s2, pD);
+    pD = __ffma2_rn(f2s(-5.f), r2, pD);
+    pD = __ffma2_rn(f2s(-20.f), qsr, pD);
+    pD = __ffma2_rn(f2s(35.f), __fmul2_rn(s2, r2), pD);
+    // pK = 3s + 6 r q + 6 s q^2 - 7 s^3 - 21 s r^2 - 42 q s^2 r + 63 s^3 r^2
+    float2 pK = __fmul2_rn(f2s(3.f), s);
+    pK = __ffma2_rn(f2s(6.f), qr, pK);
+    pK = __ffma2_rn(f2s(6.f), __fmul2_rn(s, qq2), pK);
+    pK = __ffma2_rn(f2s(-7.f), s3, pK);
+    pK = __ffma2_rn(f2s(-21.f), sr2, pK);
+    pK = __ffma2_rn(f2s(-42.f), __fmul2_rn(qsr, s), pK);
+    pK = __ffma2_rn(f2s(63.f), __fmul2_rn(s3, r2), pK);
+    const float2 cj = __fmul2_rn(amp, w4);          // times CJ in the epilogue
+    const float2 ck = __fmul2_rn(__fmul2_rn(cj, w), pK);  // times CK in the epilogue
+    J[0] = __ffma2_rn(cj, __ffma2_rn(hx, pD, __fmul2_rn(Nx, pN)), J[0]);
+    J[1] = __ffma2_rn(cj, __ffma2_rn(hy, pD, __fmul2_rn(Ny, pN)), J[1]);
+    J[2] = __ffma2_rn(cj, __ffma2_rn(hz, pD, __fmul2_rn(Nz, pN)), J[2]);
+    K[0] = __ffma2_rn(ck, hx, K[0]);
+    K[1] = __ffma2_rn(ck, hy, K[1]);
+    K[2] = __ffma2_rn(ck, hz, K[2]);
+}
+
 // (s, c) += (s2, c2): FP32 with Knuth's two-sum on the sums, FP64 plain sums.
 template <typename T>
 __device__ __forceinline__ void sa_merge(T &s, T &c, T s2, T c2)
@@ -289,9 +355,27 @@ __global__ void __launch_bounds__(SA_NT) sa_eval_kernel(SaArgs A)
         for (int k = tid; k < len; k += SA_NT) tile[k] = in[t0 + k];
         __syncthreads();
         T J[3] = {0, 0, 0}, K[3] = {0, 0, 0};
-        if (act)
-            for (int k = sl; k < len; k += NSL)
+        if (act) {
+            int k = sl;
+            // two records per paired call (FP32; with TL <= 2 a thread holds at most
+            // two records of a tile, and the paired code would only cost registers)
+            if constexpr (sizeof(T) == 4 && TL >= 4) {
+                float2 J2[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+                float2 K2[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+                for (; k + NSL < len; k += 2 * NSL)
+                    sa_pair2(t0 + k == st, t0 + k + NSL == st, f2s(Rx), f2s(Ry), f2s(Rz), f2s(lam), f2s(Nx),
+                             f2s(Ny), f2s(Nz), f2s(sn), f2s(cs), tile[k], tile[k + NSL], J2, K2);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    sa_merge(fs[c], fc[c], J2[c].x, T(0));
+                    sa_merge(fs[c], fc[c], J2[c].y, T(0));
+                    sa_merge(fs[3 + c], fc[3 + c], K2[c].x, T(0));
+                    sa_merge(fs[3 + c], fc[3 + c], K2[c].y, T(0));
+                }
+            }
+            for (; k < len; k += NSL)
                 sa_pair<T, Rec>(t0 + k == st, Rx, Ry, Rz, lam, Nx, Ny, Nz, sn, cs, tile[k], J, K);
+        }
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             sa_merge(fs[k], fc[k], J[k], T(0));
@@ -585,15 +669,19 @@ static void sa_launch_t(const dbs_sa *h, const SaArgs &A)
 
 // Targets per CTA: the smallest power of two that keeps the grid within about
 // 128 CTAs (one wave on the SMs), at most 32.
+#ifndef DBS_SA_TL_MAX
+#define DBS_SA_TL_MAX 16
+#endif
 template <typename T>
 static void sa_launch_p(const dbs_sa *h, const SaArgs &A)
 {
     const int64_t S = h->p.S;
-    if (S <= 128) sa_launch_t<T, 1>(h, A);
-    else if (S <= 256) sa_launch_t<T, 2>(h, A);
-    else if (S <= 512) sa_launch_t<T, 4>(h, A);
-    else if (S <= 1024) sa_launch_t<T, 8>(h, A);
-    else if (S <= 2048) sa_launch_t<T, 16>(h, A);
+    constexpr int TM = DBS_SA_TL_MAX;
+    if (S <= 128 || TM == 1) sa_launch_t<T, 1>(h, A);
+    else if (S <= 256 || TM == 2) sa_launch_t<T, 2>(h, A);
+    else if (S <= 512 || TM == 4) sa_launch_t<T, 4>(h, A);
+    else if (S <= 1024 || TM == 8) sa_launch_t<T, 8>(h, A);
+    else if (S <= 2048 || TM == 16) sa_launch_t<T, 16>(h, A);
     else sa_launch_t<T, 32>(h, A);
 }
 

@@ -3,6 +3,7 @@
     python -m paper_1004_1932_b300.run --S 512 --mobility rpy --steps 20 [--precision fp32c]
     python -m paper_1004_1932_b300.run --S 512 --path coop --steps 2048
     python -m paper_1004_1932_b300.run --S 512 --path coop --breakdown 5
+    python -m paper_1004_1932_b300.run --S 8192 --sa --steps 20
 
 Creates the paper-scale workload (density 0.002, lambda 0.2, seeded).  On the
 grid path it advances ``--steps`` Heun steps one launch at a time
@@ -11,7 +12,8 @@ with the algorithmic FP32 rate; on the cluster and cooperative paths it prints
 the wall time per Heun step.  ``--breakdown P`` runs P stroke periods of the
 benchmark's hot path (1000 Heun steps, 10 stroke-averaged steps, the
 pair-distance comparison) and prints the CUDA-event time of each part on the
-stream.
+stream.  ``--sa`` advances the stroke-averaged model alone (dt = T/10) and
+prints the CUDA-event time of one of its Heun steps.
 """
 import argparse
 import json
@@ -34,9 +36,13 @@ def main(argv=None):
     ap.add_argument("--shape", type=int, default=0,
                     help="shape-driven dynamics with this many constraint iterations (0 = spring)")
     ap.add_argument("--cluster", type=int, default=0, help="cluster size of the cluster path (0 = auto)")
+    ap.add_argument("--sa", action="store_true", help="the stroke-averaged model alone")
     a = ap.parse_args(argv)
     s = inputs.paper_scale(a.S, seed=a.seed, mobility=a.mobility)
     N = 2 * a.S
+    if a.sa:
+        print(json.dumps(stroke_averaged(s, a)))
+        return
     if a.breakdown:
         print(json.dumps(breakdown(s, a)))
         return
@@ -73,6 +79,23 @@ def main(argv=None):
             el = time.perf_counter() - t0
             print(json.dumps({"S": a.S, "N": N, "mobility": a.mobility, "path": a.path, "kT": a.kT,
                               "cluster": h.get_path()[1], "ms_per_step": 1e3 * el / a.steps}))
+
+
+def stroke_averaged(s, a):
+    """CUDA-event time of one Heun step of the stroke-averaged model (dt = T/10)."""
+    import math
+    import torch
+    stream = torch.cuda.Stream()
+    with dbs.StrokeAveraged(s.R0, s.N0, s.phi, s.lam, a=s.a, ell=s.ell, omega=s.omega,
+                            dt=2 * math.pi / s.omega / 10, precision=a.precision, stream=stream) as h:
+        h.step(4)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.step(a.steps)
+        e1.record(stream)
+        e1.synchronize()
+    return {"S": a.S, "model": "stroke-averaged", "precision": a.precision, "steps": a.steps,
+            "us_per_step": e0.elapsed_time(e1) * 1e3 / a.steps}
 
 
 def breakdown(s, a):
