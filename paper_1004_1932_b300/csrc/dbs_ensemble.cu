@@ -261,13 +261,14 @@ static int enqueue_launches(dbs_ensemble *e)
         cfg.numAttrs = 1;
         const ResSys *ds = e->d_sys;
         const int *cs = c.csys;
+        const int nc = (int)c.members.size(), Gc = kv.first.G;   // the shape the kernel checks
         cudaError_t err;
         if (kv.first.mob == DBS_OSEEN)
-            err = kv.first.nt == NT_BIG ? cudaLaunchKernelEx(&cfg, resident_kernel<0, NT_BIG>, ds, cs)
-                                        : cudaLaunchKernelEx(&cfg, resident_kernel<0, NT_SMALL>, ds, cs);
+            err = kv.first.nt == NT_BIG ? cudaLaunchKernelEx(&cfg, resident_kernel<0, NT_BIG>, ds, cs, nc, Gc)
+                                        : cudaLaunchKernelEx(&cfg, resident_kernel<0, NT_SMALL>, ds, cs, nc, Gc);
         else
-            err = kv.first.nt == NT_BIG ? cudaLaunchKernelEx(&cfg, resident_kernel<1, NT_BIG>, ds, cs)
-                                        : cudaLaunchKernelEx(&cfg, resident_kernel<1, NT_SMALL>, ds, cs);
+            err = kv.first.nt == NT_BIG ? cudaLaunchKernelEx(&cfg, resident_kernel<1, NT_BIG>, ds, cs, nc, Gc)
+                                        : cudaLaunchKernelEx(&cfg, resident_kernel<1, NT_SMALL>, ds, cs, nc, Gc);
         if (err != cudaSuccess)
             return efail(e, DBS_E_CUDA, "resident launch (G=%d, %zu members): %s", kv.first.G,
                          c.members.size(), cudaGetErrorString(err));

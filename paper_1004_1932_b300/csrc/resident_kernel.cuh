@@ -105,15 +105,22 @@ __device__ __forceinline__ void res_sweep(const DbF32 *rec, int db, int de, int 
 }
 
 // P.K Heun steps of the cluster's suspension (members of one launch may take
-// different step counts).  Grid = sum over members of G_m CTAs in clusters of G
-// (all members of a launch share G); csys[cluster] is the member index.  NT
-// threads per CTA.
+// different step counts).  Grid = nclust clusters of Gl CTAs (all members of a
+// launch share the cluster size); csys[cluster] is the member index.  NT
+// threads per CTA.  A launch in any other shape (a tool that drops the cluster
+// dimension, say) would index csys past its end: every CTA checks the shape
+// first, and on a mismatch all of them (the test is grid-uniform) raise
+// FLAG_LAUNCH on the first member and return before any cluster barrier.
 template <int MOB, int NT>
 __global__ void __launch_bounds__(NT, 1)
-resident_kernel(const ResSys *__restrict__ systems, const int *__restrict__ csys)
+resident_kernel(const ResSys *__restrict__ systems, const int *__restrict__ csys, int nclust, int Gl)
 {
     cg::cluster_group cluster = cg::this_cluster();
     const int G = (int)cluster.num_blocks();
+    if (G != Gl || gridDim.x != (unsigned)(Gl * nclust) || blockDim.x != (unsigned)NT) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(systems[csys[0]].flags, FLAG_LAUNCH);
+        return;
+    }
     const int r = (int)cluster.block_rank();
     const int cid = blockIdx.x / G;
     const ResSys &P = systems[csys[cid]];
