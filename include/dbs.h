@@ -504,6 +504,16 @@ DBS_API int dbs_test_wait_timeout(int32_t timeout_ms, int32_t *status);
  */
 DBS_API int dbs_test_set_flow_tag(dbs_suspension *h, uint32_t tag);
 
+/*
+ * Diagnostic of the cluster-resident kernel's launch-shape check: one Heun step
+ * of the ensemble whose kernels are told to expect twice their true cluster
+ * size.  Every CTA must refuse before touching member state and raise the
+ * launch flag; returns what dbs_ensemble_sync then returns (DBS_E_CUDA,
+ * "kernel launched in a grid or cluster shape it cannot run", expected).  The
+ * members are left in that error state (sticky): destroy them afterwards.
+ */
+DBS_API int dbs_test_ensemble_misshape(dbs_ensemble *e);
+
 /* Library version string. */
 DBS_API const char *dbs_version(void);
 

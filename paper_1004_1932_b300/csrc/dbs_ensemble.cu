@@ -73,6 +73,7 @@ int min_cluster(int64_t S, int nt)
 }  // namespace
 
 struct dbs_ensemble {
+    int test_g_scale = 1;          // diagnostic: the kernels expect G x this (1 = the true shape)
     std::vector<dbs_suspension *> m;
     std::vector<int> G;            // cluster size per member
     int device = 0;
@@ -261,7 +262,7 @@ static int enqueue_launches(dbs_ensemble *e)
         cfg.numAttrs = 1;
         const ResSys *ds = e->d_sys;
         const int *cs = c.csys;
-        const int nc = (int)c.members.size(), Gc = kv.first.G;   // the shape the kernel checks
+        const int nc = (int)c.members.size(), Gc = kv.first.G * e->test_g_scale;   // the shape the kernel checks
         cudaError_t err;
         if (kv.first.mob == DBS_OSEEN)
             err = kv.first.nt == NT_BIG ? cudaLaunchKernelEx(&cfg, resident_kernel<0, NT_BIG>, ds, cs, nc, Gc)
@@ -490,6 +491,24 @@ int dbs_ensemble_sync(dbs_ensemble *e)
         if (rc) return efail(e, rc, "member fault: %s", h->msg);
     }
     return DBS_OK;
+}
+
+int dbs_test_ensemble_misshape(dbs_ensemble *e)
+{
+    if (!e) return DBS_E_ARG;
+    if (e->status != DBS_OK) return e->status;
+    ECK(e, cudaSetDevice(e->device));
+    // one step recaptured with kernels told to expect twice their cluster size,
+    // then the true shape again for any later capture
+    if (e->launches) cudaGraphExecDestroy(e->launches);
+    e->launches = nullptr;
+    e->test_g_scale = 2;
+    const int rc = ensemble_step(e, 1);
+    e->test_g_scale = 1;
+    if (e->launches) cudaGraphExecDestroy(e->launches);
+    e->launches = nullptr;
+    if (rc) return rc;
+    return dbs_ensemble_sync(e);
 }
 
 int dbs_set_path(dbs_suspension *h, int32_t path, int32_t cluster_size)

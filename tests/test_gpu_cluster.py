@@ -10,6 +10,9 @@
   clock and the step counter exactly.
 * The benchmark's 256-system ensemble: sampled members (smallest, median,
   largest) follow the oracle over 20 steps, every member stays finite.
+* The resident kernel refuses a launch in a shape other than the one it was
+  built for (told to expect twice its cluster size) with DBS_E_CUDA, before
+  touching member state, and the device stays usable.
 """
 import numpy as np
 import pytest
@@ -146,6 +149,25 @@ def test_cluster_path_refusal_leaves_handle_usable():
     with pytest.raises(dbs.DbsError):
         h.set_path("coop")
     assert h.get_path()[0] == "grid"
+    h.step(2)
+    assert np.isfinite(h.positions()).all()
+    h.close()
+
+
+def test_resident_kernel_refuses_a_launch_shape_it_was_not_built_for():
+    # two launch classes (a small and a large member); both kernels are told to
+    # expect twice their cluster size and must refuse
+    members = [_handle(inputs.paper_scale(S, seed=S)) for S in (40, 300)]
+    ens = dbs.Ensemble(members)
+    lib = dbs.load()
+    rc = lib.dbs_test_ensemble_misshape(ens._h)
+    assert rc == dbs.E_CUDA
+    assert "shape" in lib.dbs_ensemble_last_error(ens._h).decode()
+    ens.close()
+    for m in members:
+        m.close()
+    # the device stays usable
+    h = _handle(inputs.paper_scale(40, seed=40))
     h.step(2)
     assert np.isfinite(h.positions()).all()
     h.close()
