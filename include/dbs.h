@@ -505,6 +505,16 @@ DBS_API int dbs_test_wait_timeout(int32_t timeout_ms, int32_t *status);
 DBS_API int dbs_test_set_flow_tag(dbs_suspension *h, uint32_t tag);
 
 /*
+ * Diagnostic of the cooperative kernel's launch-shape check: one Heun step on
+ * the cooperative path whose kernel is told it has one CTA more than it was
+ * launched with.  Every CTA must refuse before touching the state or the
+ * exchange buffers and raise the launch flag; returns what the flag check then
+ * returns (DBS_E_CUDA expected; the handle keeps that error).  DBS_E_STATE if
+ * the handle is not on the cooperative path.
+ */
+DBS_API int dbs_test_flow_misshape(dbs_suspension *h);
+
+/*
  * Diagnostic of the cluster-resident kernel's launch-shape check: one Heun step
  * of the ensemble whose kernels are told to expect twice their true cluster
  * size.  Every CTA must refuse before touching member state and raise the

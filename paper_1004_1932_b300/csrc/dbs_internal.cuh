@@ -22,6 +22,7 @@ struct dbs_suspension {
     int flow_T = 0, flow_G = 0;    // dumbbells per CTA, CTAs
     int flow_creq = 0;             // dbs_set_chunks request (dumbbells per CTA), 0 = built-in
     unsigned flow_base = 1;
+    int flow_test_dG = 0;          // diagnostic: the kernel is told G + this many CTAs (0 = the true grid)
     dbs_params p{};
     int device = 0;
     cudaStream_t stream = nullptr;

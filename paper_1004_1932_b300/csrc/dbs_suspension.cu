@@ -791,7 +791,7 @@ static int coop_step(dbs_suspension *h, int64_t n)
         P.rec = h->ll_rec;
         P.pack = (DbF32 *)h->packA;
         P.n0 = h->n_host;
-        P.G = h->flow_G;
+        P.G = h->flow_G + h->flow_test_dG;
         P.K = K;
         P.base = h->flow_base;
         P.timeout_ns = 1000000000ull;
@@ -929,6 +929,18 @@ int dbs_test_set_flow_tag(dbs_suspension *h, uint32_t tag)
     if (tag == 0) return DBS_E_ARG;
     h->flow_base = tag;
     return DBS_OK;
+}
+
+int dbs_test_flow_misshape(dbs_suspension *h)
+{
+    GUARD(h);
+    if (h->path != DBS_PATH_COOP) return DBS_E_STATE;
+    // one Heun step whose kernel is told it has one CTA more than it was launched with
+    h->flow_test_dG = 1;
+    const int rc = coop_step(h, 1);
+    h->flow_test_dG = 0;
+    if (rc) return rc;
+    return check_flags(h);
 }
 
 int dbs_test_wait_timeout(int32_t timeout_ms, int32_t *status)

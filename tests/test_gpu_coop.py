@@ -14,6 +14,9 @@
   and the device stays usable afterwards.
 * Sizes and precisions the path cannot hold are refused with DBS_E_ARG and
   leave the handle usable on the grid path.
+* The kernel refuses a launch in a shape other than the one it was told
+  (DBS_E_CUDA), before touching state or exchange buffers; the device and the
+  path stay usable.
 """
 import numpy as np
 import pytest
@@ -166,3 +169,22 @@ def test_bounded_wait_times_out_and_device_stays_usable():
         h.set_path("coop")
         h.step(20)
         assert np.abs(h.positions() - ref).max() <= 1e-4 * s.ell
+
+
+def test_cooperative_kernel_refuses_a_launch_shape_it_was_not_built_for():
+    # the kernel is told it has one CTA more than it was launched with: every CTA
+    # must refuse before touching state or exchange buffers, the host reports it
+    lib = dbs.load()
+    for S in (16, 512):
+        s = inputs.paper_scale(S, seed=3)
+        h = dbs.Suspension.from_inputs(s, precision="fp32c")
+        h.set_path("coop")
+        assert lib.dbs_test_flow_misshape(h._h) == dbs.E_CUDA
+        assert "shape" in lib.dbs_last_error(h._h).decode()
+        h.close()
+    # the device stays usable, and so does the cooperative path
+    s = inputs.paper_scale(512, seed=3)
+    with dbs.Suspension.from_inputs(s, precision="fp32c") as h:
+        h.set_path("coop")
+        h.step(4)
+        assert np.isfinite(h.positions()).all()
