@@ -27,7 +27,36 @@ using namespace dbs;
 
 namespace {
 
-__global__ void sd_set_step_kernel(int64_t *step, int64_t n) { *step = n; }
+// Programmatic dependent launch: the step's small kernels may be scheduled
+// while the previous kernel on the stream finishes; each waits for it (and its
+// memory) before reading anything, then lets the next one be scheduled.  Both
+// are no-ops for an ordinary launch.
+__device__ __forceinline__ void pdl_sync()
+{
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t sd_launch(void (*kern)(KArgs...), int blocks, int thr, cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(thr);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+__global__ void sd_set_step_kernel(int64_t *step, int64_t n)
+{
+    pdl_sync();
+    *step = n;
+}
 
 // Work arrays of one handle, carved from h->sd_buf (doubles).
 struct SdBuf {
@@ -73,6 +102,7 @@ __device__ __forceinline__ double2 rest_and_rate(const EvalArgs &A, int64_t s, i
 template <typename Real>
 __global__ void sd_begin_kernel(EvalArgs A, const double *P, int64_t k, SdBuf B, int rpy, void *pack)
 {
+    pdl_sync();
     using Rec = typename RecOf<Real>::type;
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= A.S) return;
@@ -106,6 +136,7 @@ __global__ void sd_begin_kernel(EvalArgs A, const double *P, int64_t k, SdBuf B,
 template <typename Real>
 __global__ void sd_iter_kernel(EvalArgs A, const double *P, SdBuf B, const double *u, void *pack)
 {
+    pdl_sync();
     using Rec = typename RecOf<Real>::type;
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= A.S) return;
@@ -136,6 +167,7 @@ __device__ __forceinline__ void unit3(double *v)
 // stroke average of the centre.
 __global__ void sd_heun_kernel(EvalArgs A, SdBuf B, const double *v, int phase, int64_t n)
 {
+    pdl_sync();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= A.S) return;
     const double *v1 = v + 6 * s, *v2 = v1 + 3, *nv = B.N + 3 * s;
@@ -214,16 +246,16 @@ int shape_eval(dbs_suspension *h, const double *P, int64_t k)
     const int thr = 128, blocks = (int)((h->S + thr - 1) / thr);
     EvalArgs A = base_args(h);
     const SdBuf B = sd_view(h);
-    if (f64) sd_begin_kernel<double><<<blocks, thr, 0, h->stream>>>(A, P, k, B, rpy, h->packT);
-    else sd_begin_kernel<float><<<blocks, thr, 0, h->stream>>>(A, P, k, B, rpy, h->packT);
+    if (f64) sd_launch(sd_begin_kernel<double>, blocks, thr, h->stream, A, P, k, B, rpy, h->packT);
+    else sd_launch(sd_begin_kernel<float>, blocks, thr, h->stream, A, P, k, B, rpy, h->packT);
     SCK(h, cudaGetLastError());
     EvalArgs Ap = A;
     Ap.pack_in = h->packT;
     for (int it = 1; it < h->sd_iters; ++it) {
         Ap.apply_self = 0;   // interaction only
         launch_apply(h, Ap);
-        if (f64) sd_iter_kernel<double><<<blocks, thr, 0, h->stream>>>(A, P, B, h->vout, h->packT);
-        else sd_iter_kernel<float><<<blocks, thr, 0, h->stream>>>(A, P, B, h->vout, h->packT);
+        if (f64) sd_launch(sd_iter_kernel<double>, blocks, thr, h->stream, A, P, B, (const double *)h->vout, h->packT);
+        else sd_launch(sd_iter_kernel<float>, blocks, thr, h->stream, A, P, B, (const double *)h->vout, h->packT);
         SCK(h, cudaGetLastError());
     }
     Ap.apply_self = 1;       // v = H F, Eq. (3)
@@ -264,14 +296,14 @@ int shape_step(dbs_suspension *h, int64_t n)
         if (rc) return rc;
         EvalArgs A = base_args(h);
         if ((rc = shape_eval(h, h->x, k))) return rc;
-        sd_heun_kernel<<<blocks, thr, 0, h->stream>>>(A, B, h->vout, 0, k);
+        sd_launch(sd_heun_kernel, blocks, thr, h->stream, A, B, (const double *)h->vout, 0, k);
         SCK(h, cudaGetLastError());
         if ((rc = shape_eval(h, B.xt, k + 1))) return rc;
-        sd_heun_kernel<<<blocks, thr, 0, h->stream>>>(A, B, h->vout, 1, k);
+        sd_launch(sd_heun_kernel, blocks, thr, h->stream, A, B, (const double *)h->vout, 1, k);
         SCK(h, cudaGetLastError());
         h->n_host = k + 1;
     }
-    sd_set_step_kernel<<<1, 1, 0, h->stream>>>(h->step, h->n_host);
+    sd_launch(sd_set_step_kernel, 1, 1, h->stream, h->step, h->n_host);
     SCK(h, cudaGetLastError());
     // leave packA / Fd describing the current state, for dbs_velocities and friends
     int rc = shape_eval(h, h->x, h->n_host);
