@@ -299,9 +299,9 @@ DBS_API const char *dbs_sa_last_error(const dbs_sa *h);
 /*
  * For S centres in four device arrays [S][3] (doubles), with
  *   dA^{sr} = |A1^s - A1^r| - |A0^s - A0^r|,  dB^{sr} likewise,
- * computes over all pairs s < r:
- *   out[0] = max |dA - dB|,  out[1] = sum (dA - dB)^2,  out[2] = sum dB^2,
- *   out[3] = number of pairs,
+ * computes over all P = S (S - 1) / 2 pairs s < r:
+ *   out[0] = max |dA - dB|,  out[1] = sqrt(sum (dA - dB)^2 / P)  (RMS error),
+ *   out[2] = sqrt(sum dB^2 / P)  (RMS of the reference change),  out[3] = P,
  * into out (host, 4 doubles).  Stream-ordered on `stream`, then synchronises.
  */
 DBS_API int dbs_pair_distance_error(int64_t S, const double *A0_dev, const double *A1_dev,
@@ -463,12 +463,15 @@ DBS_API const char *dbs_engine_last_error(const dbs_engine *e);
 #define DBS_NOALLOC_MAX_S 4096
 
 /*
- * v = H F (Eq. (3): self term plus the FP32 compensated pair sum) for S
+ * v = H F, the self term plus the FP32 compensated pair sum, for S
  * dumbbells whose positions x_dev [2S][3], forces F_dev [2S][3] and output
  * v_dev [2S][3] are caller-owned device buffers (doubles) on the current
- * device; mobility is DBS_OSEEN or DBS_RPY.  Work is enqueued on `stream`
- * (NULL = legacy default stream) and the call waits for it, returning
- * DBS_E_OVERLAP / DBS_E_NONFINITE for geometry faults.
+ * device; mobility is DBS_OSEEN or DBS_RPY.  Positions are packed relative to
+ * the first sphere before their FP32 rounding, so the result does not depend
+ * on where the suspension sits.  Work is enqueued on `stream` (NULL = legacy
+ * default stream); the call then waits for it and reads a status word back to
+ * the host before it returns, reporting DBS_E_OVERLAP / DBS_E_NONFINITE for
+ * geometry faults.
  *
  * The paper has no counterpart: this entry point exists for callers that may
  * not allocate device memory while they run -- code inside a framework that

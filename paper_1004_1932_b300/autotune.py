@@ -17,8 +17,11 @@ import os
 
 from . import dbs
 
+# the cache lives in the user's cache directory (never inside the package);
+# DBS_TUNE_CACHE names another file
 CACHE = os.environ.get("DBS_TUNE_CACHE",
-                       os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_chunks.json"))
+                       os.path.join(os.environ.get("XDG_CACHE_HOME", os.path.expanduser("~/.cache")),
+                                    "paper_1004_1932_b300", "tuned_chunks.json"))
 
 
 def _key(h: "dbs.Suspension", device_name: str, precision: str, mobility: str) -> str:
@@ -80,6 +83,7 @@ def tune(h: "dbs.Suspension", *, device_name: str = "cuda", precision: str = "fp
         cache = _load()
         cache[key] = entry
         try:
+            os.makedirs(os.path.dirname(CACHE) or ".", exist_ok=True)
             with open(CACHE + ".tmp", "w") as f:
                 json.dump(cache, f, indent=1, sort_keys=True)
             os.replace(CACHE + ".tmp", CACHE)

@@ -77,10 +77,16 @@ int setup_device(int dev)
 }
 
 // Pack positions x and the given forces F into dumbbell records (FP32 pair data).
+// Positions are taken relative to the first sphere, a point of the suspension,
+// before the FP32 rounding: the pair sum needs only differences, and the
+// records keep their relative precision wherever the suspension sits.
 __global__ void noalloc_pack_kernel(EvalArgs A, const double *F)
 {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= A.S) return;
+    A.cx = A.x[0];
+    A.cy = A.x[1];
+    A.cz = A.x[2];
     double xq[6], Fq[6];
     for (int k = 0; k < 6; ++k) {
         xq[k] = A.x[6 * s + k];

@@ -890,10 +890,11 @@ int dbs_pair_distance_error(int64_t S, const double *A0, const double *A1, const
     if (e == cudaSuccess) e = cudaMemcpyFromSymbolAsync(hb, g_pd_out, sizeof(hb), 0, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return DBS_E_CUDA;
+    const double pairs = (double)S * (double)(S - 1) / 2.0;
     out[0] = hb[0];
-    out[1] = hb[1];
-    out[2] = hb[2];
-    out[3] = (double)S * (double)(S - 1) / 2.0;
+    out[1] = std::sqrt(hb[1] / pairs);
+    out[2] = std::sqrt(hb[2] / pairs);
+    out[3] = pairs;
     return DBS_OK;
 }
 

@@ -25,7 +25,7 @@
 #include "dbs_common.cuh"
 #include "noise.cuh"
 
-// Tuning macros (defaults measured on B300 at N = 65536, see profiles/):
+// Tuning macros (defaults measured on B300 at N = 65536):
 //   DBS_RPY_W35           RPY coefficients as A = w + c2 w^3, B = (r.G)(w^3 + c3 w^5)
 //   DBS_UNROLL            unroll of the fast j-loop for CTAs of fewer than 256 threads
 //   DBS_UNROLL_LARGE      the same for CTAs of 256 threads or more (large systems)

@@ -357,15 +357,14 @@ class StrokeAveraged:
 
 
 def pair_distance_error(S, A0, A1, B0, B1, stream=None):
-    """max / sum-of-squares of |dA - dB| over pairs and sum dB^2 (device pointers or tensors)."""
+    """max and RMS of |dA - dB| over pairs, and RMS of dB (device pointers or tensors)."""
     out = np.empty(4)
     rc = load().dbs_pair_distance_error(
         _i64(int(S)), *(ctypes.c_void_p(_devptr(t)) for t in (A0, A1, B0, B1)), _p(out),
         None if stream is None else ctypes.c_void_p(_devptr_stream(stream)))
     if rc != OK:
         raise DbsError(rc, "dbs_pair_distance_error")
-    return {"max": out[0], "rms": float(np.sqrt(out[1] / out[3])),
-            "ref_rms": float(np.sqrt(out[2] / out[3])), "pairs": int(out[3])}
+    return {"max": float(out[0]), "rms": float(out[1]), "ref_rms": float(out[2]), "pairs": int(out[3])}
 
 
 class Ensemble:
