@@ -223,12 +223,17 @@ def _cpu_sweep(mobility):
     return out
 
 
-def ensemble_measure(dbs, inputs, torch, stream, steps=1000, count=256):
+def ensemble_measure(dbs, inputs, torch, stream, steps=1000, count=256, ws=1, rank=0, dev=None):
     """256 independent suspensions, S log-uniform in [8, 2048], lambda ~ U[0.1, 0.3],
-    seeds 0..255: batched on thread-block clusters vs one system per launch."""
-    systems = inputs.ensemble(count)
+    seeds 0..255: batched on thread-block clusters vs one system per launch.  Over
+    several ranks each rank runs its LPT share (pair work S^2 x steps) and the times
+    are the maxima over ranks (no collective on the data path)."""
+    from paper_1004_1932_b300 import partition
+    systems_all = inputs.ensemble(count)
+    assign = partition.lpt([partition.pair_work(m.S, steps) for m in systems_all], ws)
+    systems = [m for m, r in zip(systems_all, assign) if r == rank]
     hs = [dbs.Suspension.from_inputs(s, precision="fp32c", stream=stream) for s in systems]
-    pairs = sum(2 * (2 * s.S) * (2 * s.S - 1) for s in systems)
+    pairs = sum(2 * (2 * s.S) * (2 * s.S - 1) for s in systems_all)
     ens = dbs.Ensemble(hs, stream=stream)
     from paper_1004_1932_b300 import autotune
     tuned = autotune.tune_ensemble(ens, hs)
@@ -237,7 +242,7 @@ def ensemble_measure(dbs, inputs, torch, stream, steps=1000, count=256):
     t0 = time.perf_counter()
     ens.step(steps)
     ens.sync()
-    el_b = time.perf_counter() - t0
+    el_b = reduce_max(time.perf_counter() - t0, dev)
     G = ens.get_clusters()
     ens.close()
     seq_steps = max(32, steps // 5)
@@ -249,7 +254,7 @@ def ensemble_measure(dbs, inputs, torch, stream, steps=1000, count=256):
         h.step(seq_steps)
     for h in hs:
         h.sync()
-    el_s = time.perf_counter() - t0
+    el_s = reduce_max(time.perf_counter() - t0, dev)
     # the same, each system on its fastest single-system path (cooperative launch)
     for h in hs:
         h.set_path("coop")
@@ -260,7 +265,7 @@ def ensemble_measure(dbs, inputs, torch, stream, steps=1000, count=256):
         h.step(seq_steps)
     for h in hs:
         h.sync()
-    el_c = time.perf_counter() - t0
+    el_c = reduce_max(time.perf_counter() - t0, dev)
     for h in hs:
         h.close()
     b = count * steps / el_b
@@ -268,6 +273,7 @@ def ensemble_measure(dbs, inputs, torch, stream, steps=1000, count=256):
     sc = count * seq_steps / el_c
     return {"workload": f"{count} suspensions, S log-uniform in [8, 2048], lambda ~ U[0.1, 0.3], "
                         f"seeds 0..{count - 1}, RPY, FP32C",
+            "ranks": ws, "split": "LPT on S^2 x steps, no collective" if ws > 1 else None,
             "batched": {"steps": steps, "seconds": el_b, "system_steps_per_s": b,
                         "pairs_per_s": pairs * steps / el_b,
                         "clusters": {str(g): G.count(g) for g in sorted(set(G))},
@@ -283,18 +289,32 @@ def ensemble_measure(dbs, inputs, torch, stream, steps=1000, count=256):
             "speedup": b / sq, "speedup_vs_cooperative": b / sc}
 
 
+def _gather_lists(values, ws):
+    """Concatenate a per-rank list over all ranks (the metric only, not the data path)."""
+    if ws == 1:
+        return list(values)
+    import torch.distributed as dist
+    parts = [None] * ws
+    dist.all_gather_object(parts, list(values))
+    return [v for p in parts for v in p]
+
+
 def serving_measure(dbs, inputs, n_req=48, rate=200.0, steps_lo=1e3, steps_hi=1e4, block=256,
-                    budget=64 << 30):
+                    budget=64 << 30, ws=1, rank=0, dev=None):
     """Poisson trace (mean `rate` req/s), S uniform over {16, 64, 256, 1024, 4096},
     steps log-uniform in [steps_lo, steps_hi]: the engine (continuous batching under an
-    HBM budget) against serving the same requests one at a time in arrival order."""
-    trace = inputs.request_trace(n_req, rate, steps_lo=steps_lo, steps_hi=steps_hi)
+    HBM budget) against serving the same requests one at a time in arrival order.
+    Over several ranks, each request is routed on arrival to the rank with the least
+    pair work assigned so far; every rank runs its own engine on its share."""
+    from paper_1004_1932_b300 import partition
+    full = inputs.request_trace(n_req, rate, steps_lo=steps_lo, steps_hi=steps_hi)
+    route = partition.route_stream([partition.pair_work(S, n) for _, S, n, _ in full], ws)
+    trace = [t for t, r in zip(full, route) if r == rank]
     susp = {rid: inputs.make_suspension(S, seed=1000 + rid, density=0.002) for _, S, _, rid in trace}
     eng = dbs.Engine(hbm_budget_bytes=budget, block_steps=block)
     t0 = time.perf_counter()
     ids, sub_t, done = {}, {}, {}
     k = 0
-    total_steps = sum(n for _, _, n, _ in trace)
     while len(done) < len(trace):
         now = time.perf_counter() - t0
         while k < len(trace) and trace[k][0] <= now:
@@ -312,9 +332,11 @@ def serving_measure(dbs, inputs, n_req=48, rate=200.0, steps_lo=1e3, steps_hi=1e
                 done[rid] = (st, (sub - arr) + lat)
         if a == 0 and q == 0 and k < len(trace):
             time.sleep(max(0.0, trace[k][0] - (time.perf_counter() - t0)))
-    makespan = time.perf_counter() - t0
+    makespan = reduce_max(time.perf_counter() - t0, dev)
+    eng_host = eng.stats()
     eng.close()
-    lat = sorted(v[1] for v in done.values() if v[0] == dbs.REQ_DONE)
+    lat = sorted(_gather_lists([v[1] for v in done.values() if v[0] == dbs.REQ_DONE], ws))
+    total_steps = sum(n for _, _, n, _ in full)
     # one at a time in arrival order (grid path), measured run times, simulated queueing
     t_free, lat_seq, busy = 0.0, [], 0.0
     for arr, S, n, rid in trace:
@@ -328,7 +350,8 @@ def serving_measure(dbs, inputs, n_req=48, rate=200.0, steps_lo=1e3, steps_hi=1e
         t_free = start + run
         busy += run
         lat_seq.append(t_free - arr)
-    lat_seq.sort()
+    lat_seq = sorted(_gather_lists(lat_seq, ws))
+    t_free, busy = reduce_max(t_free, dev), reduce_max(busy, dev)
     # the same, each request on its fastest single-system path (cooperative for S <= 4096)
     t_free_c, lat_c, busy_c = 0.0, [], 0.0
     for arr, S, n, rid in trace:
@@ -344,19 +367,47 @@ def serving_measure(dbs, inputs, n_req=48, rate=200.0, steps_lo=1e3, steps_hi=1e
         t_free_c = start + run
         busy_c += run
         lat_c.append(t_free_c - arr)
-    lat_c.sort()
+    lat_c = sorted(_gather_lists(lat_c, ws))
+    t_free_c, busy_c = reduce_max(t_free_c, dev), reduce_max(busy_c, dev)
     q = lambda v, p: v[min(len(v) - 1, int(round(p * (len(v) - 1))))]
     return {"trace": f"{n_req} requests, Poisson {rate:g}/s (seed 0), S in {{16,64,256,1024,4096}}, "
                      f"steps log-uniform [{steps_lo:g}, {steps_hi:g}], HBM budget {budget >> 30} GB, "
                      f"block {block} steps",
+            "ranks": ws, "routing": "least assigned pair work, on arrival" if ws > 1 else None,
             "completed": len(lat),
             "engine": {"makespan_s": makespan, "system_steps_per_s": total_steps / makespan,
-                       "p50_latency_s": q(lat, 0.5), "p99_latency_s": q(lat, 0.99)},
+                       "p50_latency_s": q(lat, 0.5), "p99_latency_s": q(lat, 0.99),
+                       "host": eng_host},
             "one_at_a_time": {"path": "grid", "makespan_s": t_free, "system_steps_per_s": total_steps / busy,
                               "p50_latency_s": q(lat_seq, 0.5), "p99_latency_s": q(lat_seq, 0.99)},
             "one_at_a_time_fastest_path": {"path": "cooperative (S <= 4096), grid", "makespan_s": t_free_c,
                                            "system_steps_per_s": total_steps / busy_c,
                                            "p50_latency_s": q(lat_c, 0.5), "p99_latency_s": q(lat_c, 0.99)}}
+
+
+def sharded_measure(dbs, inputs, torch, stream, ws, rank, dev, S=32768, steps=10):
+    """One suspension of S dumbbells split by target rows over all ranks (NCCL
+    all-gather of the packed records after every evaluation): strong scaling."""
+    from paper_1004_1932_b300 import shard
+    s = inputs.paper_scale(S, seed=0)
+    sh = shard.Shard(s, ws, rank, precision="fp32c", stream=stream, device=dev.index)
+    ex = shard.GroupExchange(device_index=dev.index)
+    shard.step([sh], 2, ex)
+    torch.cuda.synchronize(dev)
+    torch.distributed.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    shard.step([sh], steps, ex)
+    e1.record(stream)
+    e1.synchronize()
+    el = reduce_max(e0.elapsed_time(e1) / 1e3, dev)
+    rows = (sh.row0, sh.row1)
+    sh.close()
+    N = 2 * S
+    return {"workload": f"one suspension S={S} (N={N}) density 0.002, RPY, FP32C, split by target rows "
+                        f"over {ws} ranks (all-gather of the packed records after every evaluation)",
+            "scaling": "strong", "heun_steps": steps, "ms_per_heun_step": 1e3 * el / steps,
+            "pairs_per_s": 2 * N * (N - 1) * steps / el, "rank0_rows": rows}
 
 
 def run_reference(args):
@@ -624,8 +675,51 @@ def run_ours(args):
         h.close()
         sa.close()
 
-    ensemble = None if args.no_ensemble else ensemble_measure(dbs, inputs, torch, stream)
-    serving = None if args.no_serving else serving_measure(dbs, inputs)
+    # ---- the stroke-averaged model at the nominal and at the measured amplitude ---
+    # (outside the timed region): the k0 = 1 springs lag the rest length, so the
+    # dumbbells stroke with a smaller amplitude lambda_eff than the nominal lambda
+    sa_cmp = {"timed_loop": last_err}
+    if not args.no_large:
+        from paper_1004_1932_b300 import experiments
+        periods = args.warmup + args.steps
+        eff = experiments.effective_amplitude(s, path=path_choice["path"])
+        lr_ratio, lr_lag = experiments.linear_response_ratio(s)
+        sa_cmp.update({
+            "periods": periods,
+            "nominal": experiments.sa_comparison(s, periods=periods, path=path_choice["path"]),
+            "lambda_eff": experiments.sa_comparison(s, periods=periods, lam=eff["lam_eff"],
+                                                    path=path_choice["path"]),
+            "lambda_eff_over_lambda": eff["ratio_mean"], "lag_deg": math.degrees(eff["lag_mean"]),
+            "linear_response": {"ratio": lr_ratio, "lag_deg": math.degrees(lr_lag)},
+            "note": "pair-distance error of the stroke-averaged model (Eqs. (9a)-(9e)) against the "
+                    "period-averaged centres, with the nominal stroke amplitudes and with each "
+                    "dumbbell's measured amplitude (first Fourier coefficient of its length over one "
+                    "period after a settling period)"})
+
+    # ---- the small FP64 suspension (S = 16, Oseen, all-FP64) on the GPU -----------
+    small = None
+    if not args.no_large:
+        s1 = inputs.small_fp64_oseen(0)
+        with dbs.Suspension.from_inputs(s1, precision="fp64", stream=stream, device=local) as h1:
+            h1.step(64)
+            h1.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h1.step(1000)
+            e1.record(stream)
+            e1.synchronize()
+            el1 = e0.elapsed_time(e1) / 1e3 / 1000
+        N1 = 2 * s1.S
+        small = {"workload": "S=16 (N=32), cube side 8, Oseen, all-FP64, dt=1e-3, 1000 Heun steps "
+                             "(grid path, CUDA graphs)",
+                 "us_per_heun_step": el1 * 1e6, "heun_steps_per_s": 1.0 / el1,
+                 "pairs_per_s": 2 * N1 * (N1 - 1) / el1,
+                 "bound": "launch latency (2 pair-sum launches per Heun step)"}
+
+    ensemble = None if args.no_ensemble else ensemble_measure(dbs, inputs, torch, stream, ws=ws,
+                                                              rank=rank, dev=dev)
+    sharded = sharded_measure(dbs, inputs, torch, stream, ws, rank, dev) if ws > 1 else None
+    serving = None if args.no_serving else serving_measure(dbs, inputs, ws=ws, rank=rank, dev=dev)
 
     if rank != 0:
         return
@@ -652,7 +746,9 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps + ring_fills,
         "clocks": clk,
-        "sa_comparison": last_err,
+        "sa_comparison": sa_cmp,
+        "small_system": small,
+        "sharded_large_system": sharded,
         "large_system_kernel": large,
         "ensemble": ensemble,
         "serving": serving,

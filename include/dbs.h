@@ -440,6 +440,18 @@ DBS_API int dbs_engine_tick(dbs_engine *e, int32_t *active, int32_t *pending);
  * receives the final positions and *latency_s (may be NULL) the time from
  * submission to completion on the host clock.
  */
+/*
+ * Host-side accounting of the engine since creation: ticks, their total host
+ * time, the part spent waiting for a block to complete, and how often (and for
+ * how long in total) the ensemble of cluster-path requests was rebuilt because
+ * its membership changed.  The paper has no counterpart (serving machinery).
+ */
+typedef struct {
+    int64_t ticks, ensemble_rebuilds;
+    double tick_s, rebuild_s, wait_s;
+} dbs_engine_stats_t;
+DBS_API int dbs_engine_stats(const dbs_engine *e, dbs_engine_stats_t *out);
+
 DBS_API int dbs_engine_poll(dbs_engine *e, int64_t id, int32_t *state, double *x_out,
                             double *latency_s);
 
@@ -450,6 +462,58 @@ DBS_API int dbs_engine_cancel(dbs_engine *e, int64_t id);
 DBS_API int dbs_engine_request_bytes(int64_t S, int32_t precision, size_t *bytes);
 
 DBS_API const char *dbs_engine_last_error(const dbs_engine *e);
+
+/* ======================================================================== */
+/* One suspension split by target rows over several processes              */
+/* ======================================================================== */
+
+/*
+ * The pair sum of Eq. (3b) splits by target rows: the velocity of a sphere
+ * needs every record, but only its own dumbbell's state.  Each of nranks
+ * processes (one GPU each) holds a full copy of the suspension and computes the
+ * Heun evaluations (Sec. IV) of one contiguous block of dumbbells; after every
+ * evaluation the ranks exchange the packed records of their blocks (an
+ * all-gather, done by the caller, e.g. with NCCL), so that each rank's record
+ * buffer again holds all S records before the next evaluation.  The j-order of
+ * every sum, the j-split and the i-blocks are those of the unsharded grid path,
+ * so each rank's rows are bit-identical to an unsharded run of the same
+ * handle configuration (same S, precision, mobility and dbs_set_chunks).
+ *
+ * dbs_shard_rows: the block [*row0, *row1) of dumbbells that rank `rank` of
+ * nranks owns, for i-blocks of rows_per_block dumbbells (the `bt` of
+ * dbs_get_launch): rank r takes i-blocks [r nb / nranks, (r + 1) nb / nranks)
+ * of the nb = ceil(S / rows_per_block) (block counts differ by at most one).
+ * Host only, no device needed.  DBS_E_ARG if nranks exceeds nb.
+ */
+DBS_API int dbs_shard_rows(int64_t S, int32_t rows_per_block, int32_t nranks, int32_t rank,
+                           int64_t *row0, int64_t *row1);
+
+/*
+ * Make h (grid path, spring dynamics) compute only rank `rank`'s row block in
+ * dbs_shard_eval; *row0, *row1 (may be NULL) receive it.  Call it after any
+ * dbs_set_chunks.  A sharded handle refuses dbs_step (DBS_E_STATE).
+ */
+DBS_API int dbs_shard_set(dbs_suspension *h, int32_t nranks, int32_t rank, int64_t *row0,
+                          int64_t *row1);
+
+/*
+ * One evaluation for the handle's row block, stream-ordered on its stream:
+ * phase 0 = predictor (reads record buffer A, the state x_n; writes the
+ * records of x~ for its rows into buffer B), phase 1 = corrector (reads B,
+ * writes the records of x_{n+1} into A and advances the step).  Before the
+ * next evaluation the caller must fill the other rows of the buffer just
+ * written with the other ranks' records (all-gather on the same stream, or
+ * after a device synchronisation).
+ */
+DBS_API int dbs_shard_eval(dbs_suspension *h, int32_t phase);
+
+/*
+ * Device pointers of the two record buffers A and B (S records each, owned by
+ * the handle) and the bytes of one record (48 for FP32C, 96 for FP64): record
+ * s of dumbbell s at byte offset s * record_bytes.
+ */
+DBS_API int dbs_shard_buffers(dbs_suspension *h, void **records_a, void **records_b,
+                              int64_t *record_bytes);
 
 /* ======================================================================== */
 /* Allocation-free mobility product                                         */
@@ -501,9 +565,11 @@ DBS_API int dbs_mobility_apply_noalloc(int64_t S, const double *x_dev, const dou
 DBS_API int dbs_test_wait_timeout(int32_t timeout_ms, int32_t *status);
 
 /*
- * Diagnostic: set the evaluation tag the cooperative path uses next (>= 1), so
- * that a test can run the tag wrap-around (the tagged buffers are cleared and
- * the tags restart at 1 before they could wrap).  DBS_E_ARG for tag 0.
+ * Diagnostic: set the evaluation counter of the cooperative path (rounded down
+ * to a multiple of 4; the exchange buffers are cleared), so that a test can run
+ * the counter through its wrap-around at 2^32: the records' parity bits depend
+ * only on the counter modulo 4, which the wrap keeps.  DBS_E_STATE if the
+ * handle is not on the cooperative path.
  */
 DBS_API int dbs_test_set_flow_tag(dbs_suspension *h, uint32_t tag);
 

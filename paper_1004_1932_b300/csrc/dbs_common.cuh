@@ -80,6 +80,7 @@ struct EvalArgs {
     float c3;             // -2 a^2     (RPY: -3 * c2)
     float overlap_r2;     // (2a)^2 in FP32 (RPY overlap threshold)
     int chunks;           // C, number of j-chunks per i-block
+    int ib0, nib;         // i-blocks (of BT dumbbells) this launch computes: [ib0, ib0 + nib)
     int apply_self;       // APPLY: 1 = add self term, 0 = interaction only
     double noise_sigma;   // additive noise per step, sqrt(2 kT dt / (6 pi mu a)); 0 = off
     unsigned long long noise_seed;  // key of the noise generator

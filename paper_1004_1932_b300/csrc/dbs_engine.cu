@@ -82,6 +82,9 @@ struct dbs_engine {
     std::vector<int64_t> ens_k;    // steps of the ensemble block in flight, per member
     bool ens_busy = false;
     cudaEvent_t ens_ev = nullptr;  // recorded after the block in flight
+    // host-side accounting (dbs_engine_stats)
+    int64_t ticks = 0, rebuilds = 0;
+    double tick_s = 0.0, rebuild_s = 0.0, wait_s = 0.0;
 };
 
 static int engfail(dbs_engine *e, int st, const char *fmt, ...)
@@ -218,6 +221,12 @@ int dbs_engine_tick(dbs_engine *e, int32_t *active, int32_t *pending)
 {
     if (!e) return DBS_E_ARG;
     if (cudaSetDevice(e->device) != cudaSuccess) return engfail(e, DBS_E_CUDA, "cudaSetDevice");
+    const double t_tick = now_s();
+    struct TickClock {   // adds this tick's host time to the engine's total on every return
+        dbs_engine *e;
+        double t0;
+        ~TickClock() { e->tick_s += now_s() - t0; ++e->ticks; }
+    } tick_clock{e, t_tick};
     // (1) admission, arrival order
     while (!e->queue.empty()) {
         Request &r = e->req[e->queue.front()];
@@ -289,6 +298,7 @@ int dbs_engine_tick(dbs_engine *e, int32_t *active, int32_t *pending)
         if (now_s() - t_wait > 600.0) return engfail(e, DBS_E_TIMEOUT, "no block completed in 600 s");
         std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
+    e->wait_s += now_s() - t_wait;
     // (3) retire: failed requests, and finished ones that nothing still runs
     std::vector<int64_t> still;
     for (int64_t id : e->active) {
@@ -313,6 +323,7 @@ int dbs_engine_tick(dbs_engine *e, int32_t *active, int32_t *pending)
             if (r.cluster && r.state == DBS_REQ_RUNNING && r.remaining > 0) cl.push_back(id);
         }
         if (cl != e->ens_ids) {
+            const double t_rb = now_s();
             drop_ensemble(e);
             if (!cl.empty()) {
                 std::vector<dbs_suspension *> hs;
@@ -321,6 +332,8 @@ int dbs_engine_tick(dbs_engine *e, int32_t *active, int32_t *pending)
                 if (rc != DBS_OK) return engfail(e, rc, "ensemble: %s", ens_error(nullptr));
                 e->ens_ids = cl;
             }
+            ++e->rebuilds;
+            e->rebuild_s += now_s() - t_rb;
         }
         if (e->ens) {
             e->ens_k.clear();
@@ -364,6 +377,17 @@ int dbs_engine_tick(dbs_engine *e, int32_t *active, int32_t *pending)
     }
     if (active) *active = (int32_t)e->active.size();
     if (pending) *pending = (int32_t)e->queue.size();
+    return DBS_OK;
+}
+
+int dbs_engine_stats(const dbs_engine *e, dbs_engine_stats_t *out)
+{
+    if (!e || !out) return DBS_E_ARG;
+    out->ticks = e->ticks;
+    out->ensemble_rebuilds = e->rebuilds;
+    out->tick_s = e->tick_s;
+    out->rebuild_s = e->rebuild_s;
+    out->wait_s = e->wait_s;
     return DBS_OK;
 }
 

@@ -48,6 +48,9 @@ struct dbs_suspension {
     double lam_max = 0;
     // launch configuration
     int grid = 1, chunks = 1, bt = 128, sms = 148;
+    // row sharding (dbs_shard_set): the i-blocks [shard_ib0, shard_ib0 + shard_nib)
+    // this handle computes, and their grid; shard_nib = 0: not sharded
+    int shard_ib0 = 0, shard_nib = 0, shard_grid = 0;
     // captured block of GRAPH_STEPS Heun steps
     cudaGraphExec_t graph = nullptr;
 };

@@ -152,6 +152,8 @@ extern "C" DBS_API int dbs_mobility_apply_noalloc(int64_t S, const double *x_dev
     A.c3 = (float)(-2.0 * a * a);
     A.overlap_r2 = (float)(4.0 * a * a);
     A.chunks = (int)C;
+    A.ib0 = 0;
+    A.nib = (int)iblocks;
     A.apply_self = 1;
 
     // the arrival tickets, fault flags and step word start at zero on every call

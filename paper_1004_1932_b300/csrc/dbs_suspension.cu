@@ -143,6 +143,8 @@ EvalArgs base_args(const dbs_suspension *h)
     A.c3 = (float)(-2.0 * h->p.a * h->p.a);
     A.overlap_r2 = (float)(4.0 * h->p.a * h->p.a);
     A.chunks = h->chunks;
+    A.ib0 = 0;
+    A.nib = (int)((h->S + h->bt - 1) / h->bt);
     A.apply_self = 1;
     A.noise_sigma = h->noise_sigma;
     A.noise_seed = h->noise_seed;
@@ -674,10 +676,7 @@ int dbs_set_external_force(dbs_suspension *h, const double *F)
 // ---------------------------------------------------------------------------
 // cooperative dataflow path (flow_kernel)
 // ---------------------------------------------------------------------------
-#ifndef DBS_FLOW_THREADS
-#define DBS_FLOW_THREADS 256
-#endif
-constexpr int FLOW_THREADS = DBS_FLOW_THREADS;   // threads per CTA of flow_kernel
+constexpr int FLOW_THREADS = FLOW_NT;   // threads per CTA of flow_kernel
 constexpr int FLOW_MAX_T = 32;        // dumbbells per CTA at most
 constexpr int64_t FLOW_MAX_S = 4096;  // all records of a suspension in one CTA's shared memory
 constexpr int FLOW_MAX_STEPS = 1024;  // Heun steps per launch
@@ -692,12 +691,12 @@ template <int MOB, bool NOISE>
 static const void *flow_pick(int T)
 {
     switch (T) {
-    case 1: return (const void *)flow_kernel<MOB, 1, NOISE, FLOW_THREADS>;
-    case 2: return (const void *)flow_kernel<MOB, 2, NOISE, FLOW_THREADS>;
-    case 4: return (const void *)flow_kernel<MOB, 4, NOISE, FLOW_THREADS>;
-    case 8: return (const void *)flow_kernel<MOB, 8, NOISE, FLOW_THREADS>;
-    case 16: return (const void *)flow_kernel<MOB, 16, NOISE, FLOW_THREADS>;
-    case 32: return (const void *)flow_kernel<MOB, 32, NOISE, FLOW_THREADS>;
+    case 1: return (const void *)flow_kernel<MOB, 1, NOISE>;
+    case 2: return (const void *)flow_kernel<MOB, 2, NOISE>;
+    case 4: return (const void *)flow_kernel<MOB, 4, NOISE>;
+    case 8: return (const void *)flow_kernel<MOB, 8, NOISE>;
+    case 16: return (const void *)flow_kernel<MOB, 16, NOISE>;
+    case 32: return (const void *)flow_kernel<MOB, 32, NOISE>;
     default: return nullptr;
     }
 }
@@ -764,28 +763,24 @@ int coop_setup(dbs_suspension *h)
     }
     CK(h, cudaStreamSynchronize(h->stream));
     drop_flow(h);
-    const size_t words = 2 * (size_t)G * T * 6;
+    const size_t words = 2 * (size_t)G * T * 3;
     CK(h, cudaMalloc(&h->ll_rec, words * sizeof(ulonglong2)));
+    // a cleared buffer carries parity bit 0 everywhere: the evaluation counter
+    // starts at a multiple of 4, whose first two evaluations expect bit 1
     CK(h, cudaMemsetAsync(h->ll_rec, 0, words * sizeof(ulonglong2), h->stream));
     h->flow_T = T;
     h->flow_G = G;
-    h->flow_base = 1;
+    h->flow_base = 0;
     return DBS_OK;
 }
 
 static int coop_step(dbs_suspension *h, int64_t n)
 {
-    const size_t words = 2 * (size_t)h->flow_G * h->flow_T * 6;
     int64_t left = n;
     while (left > 0) {
         const int K = (int)std::min<int64_t>(left, FLOW_MAX_STEPS);
         int rc = ensure_trig(h, h->n_host + K + 1);
         if (rc) return rc;
-        if (h->flow_base > 0xffffffffu - (unsigned)(2 * K + 2)) {
-            // tags are about to wrap: clear the buffers so that no old tag can match
-            CK(h, cudaMemsetAsync(h->ll_rec, 0, words * sizeof(ulonglong2), h->stream));
-            h->flow_base = 1;
-        }
         const EvalArgs A = base_args(h);
         FlowArgs P{};
         P.rec = h->ll_rec;
@@ -800,7 +795,10 @@ static int coop_step(dbs_suspension *h, int64_t n)
         void *args[] = {(void *)&A, (void *)&P};
         cudaError_t e = cudaLaunchKernelExC(&cfg, flow_fn(h, h->flow_T), args);
         if (e != cudaSuccess) return fail(h, DBS_E_CUDA, "cooperative launch: %s", cudaGetErrorString(e));
-        h->flow_base += (unsigned)(2 * K + 1);
+        // the evaluation counter runs on from launch to launch (2K evaluations per
+        // launch, so it stays even; modulo 2^32 it keeps its residue mod 4, which is
+        // all the parity bits depend on)
+        h->flow_base += (unsigned)(2 * K);
         h->n_host += K;
         left -= K;
     }
@@ -814,6 +812,7 @@ int dbs_step(dbs_suspension *h, int64_t n)
 {
     GUARD(h);
     if (n < 0) return DBS_E_ARG;
+    if (h->shard_nib > 0) return refuse(h, DBS_E_STATE, "a row-sharded handle steps with dbs_shard_eval");
     if (h->solo) return solo_step(h, n);
     if (h->dyn == DBS_DYN_SHAPE) return shape_step(h, n);
     if (h->path == DBS_PATH_COOP) return coop_step(h, n);
@@ -923,11 +922,73 @@ int dbs_get_launch(dbs_suspension *h, int32_t *bt, int32_t *chunks, int32_t *gri
     return DBS_OK;
 }
 
+// ---- one suspension split by target rows (several processes) ------------------
+int dbs_shard_rows(int64_t S, int32_t rows_per_block, int32_t nranks, int32_t rank, int64_t *row0,
+                   int64_t *row1)
+{
+    if (S < 1 || rows_per_block < 1 || nranks < 1 || rank < 0 || rank >= nranks || !row0 || !row1)
+        return DBS_E_ARG;
+    const int64_t nb = (S + rows_per_block - 1) / rows_per_block;   // i-blocks
+    if (nranks > nb) return DBS_E_ARG;                               // every rank needs a block
+    const int64_t b0 = nb * rank / nranks, b1 = nb * (rank + 1) / nranks;   // sizes differ by <= 1
+    *row0 = b0 * rows_per_block;
+    *row1 = std::min<int64_t>(S, b1 * rows_per_block);
+    return DBS_OK;
+}
+
+int dbs_shard_set(dbs_suspension *h, int32_t nranks, int32_t rank, int64_t *row0, int64_t *row1)
+{
+    GUARD(h);
+    if (h->path != DBS_PATH_GRID || h->dyn != DBS_DYN_SPRING || h->solo)
+        return refuse(h, DBS_E_STATE, "row sharding needs the grid path and spring dynamics");
+    int64_t r0 = 0, r1 = 0;
+    int rc = dbs_shard_rows(h->S, h->bt, nranks, rank, &r0, &r1);
+    if (rc) return refuse(h, rc, "no row block for this rank (more ranks than i-blocks?)");
+    h->shard_ib0 = (int)(r0 / h->bt);
+    h->shard_nib = (int)((r1 - r0 + h->bt - 1) / h->bt);
+    h->shard_grid = (int)std::min<int64_t>(h->grid, (int64_t)h->shard_nib * h->chunks);
+    if (row0) *row0 = r0;
+    if (row1) *row1 = r1;
+    return DBS_OK;
+}
+
+int dbs_shard_eval(dbs_suspension *h, int32_t phase)
+{
+    GUARD(h);
+    if (h->shard_nib < 1) return refuse(h, DBS_E_STATE, "dbs_shard_set first");
+    if (phase != 0 && phase != 1) return DBS_E_ARG;
+    int rc = ensure_trig(h, h->n_host + 1);
+    if (rc) return rc;
+    EvalArgs A = base_args(h);
+    A.ib0 = h->shard_ib0;
+    A.nib = h->shard_nib;
+    A.pack_in = phase == 0 ? h->packA : h->packB;    // predictor: x_n -> records of x~
+    A.pack_out = phase == 0 ? h->packB : h->packA;   // corrector: x~ -> records of x_{n+1}
+    const int ph = phase == 0 ? PHASE_PREDICT : PHASE_CORRECT;
+    if (is_f64(h)) launch_eval_r<double>(h->p.mobility, ph, A, h->shard_grid, h->bt, h->stream);
+    else launch_eval_r<float>(h->p.mobility, ph, A, h->shard_grid, h->bt, h->stream);
+    CK(h, cudaGetLastError());
+    if (phase == 1) h->n_host += 1;
+    return DBS_OK;
+}
+
+int dbs_shard_buffers(dbs_suspension *h, void **records_a, void **records_b, int64_t *record_bytes)
+{
+    GUARD(h);
+    if (records_a) *records_a = h->packA;
+    if (records_b) *records_b = h->packB;
+    if (record_bytes) *record_bytes = (int64_t)(is_f64(h) ? sizeof(DbF64) : sizeof(DbF32));
+    return DBS_OK;
+}
+
 int dbs_test_set_flow_tag(dbs_suspension *h, uint32_t tag)
 {
     GUARD(h);
-    if (tag == 0) return DBS_E_ARG;
-    h->flow_base = tag;
+    if (h->path != DBS_PATH_COOP || !h->ll_rec) return DBS_E_STATE;
+    // a cleared buffer and a counter at a multiple of 4, as after the path's set-up
+    const size_t words = 2 * (size_t)h->flow_G * h->flow_T * 3;
+    CK(h, cudaMemsetAsync(h->ll_rec, 0, words * sizeof(ulonglong2), h->stream));
+    h->flow_base = tag & ~3u;
     return DBS_OK;
 }
 

@@ -376,7 +376,7 @@ __device__ __forceinline__ void eval_units(const EvalArgs &A, const void *pack_i
     const int tid = threadIdx.x;
     const Rec *pin = (const Rec *)pack_in;
     const int S = (int)A.S, C = A.chunks;
-    const int iblocks = (S + BT - 1) / BT;
+    const int iblocks = A.nib;   // all ceil(S / BT) i-blocks, or one row block of a sharded system
     const int units = iblocks * C;
 
     for (int unit = blockIdx.x; unit < units; unit += gridDim.x) {
@@ -388,7 +388,7 @@ __device__ __forceinline__ void eval_units(const EvalArgs &A, const void *pack_i
         // other order costs the FP64 kernel 8 registers and one CTA per SM).
         constexpr bool kChunkMajor = DBS_UNIT_ORDER && BT >= 256;
         const int c = kChunkMajor ? unit / iblocks : unit % C;
-        const int ib_ = kChunkMajor ? unit - c * iblocks : unit / C;
+        const int ib_ = A.ib0 + (kChunkMajor ? unit - c * iblocks : unit / C);
         const int s = ib_ * BT + tid;
         const bool active = s < S;
         const int db = (int)(((int64_t)S * c) / C);

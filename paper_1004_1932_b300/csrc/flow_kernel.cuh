@@ -5,7 +5,7 @@
 // Work split.  CTA g owns the T consecutive dumbbells [gT, gT + T) and, for
 // each evaluation, sums the pair terms of Eq. (3b) for its own 2T target
 // spheres over ALL S records: thread tid takes target t = tid / P and the
-// records r = (tid mod P) + P k (P = NT / T slices per target), so the
+// records r = (tid mod P) + P k (P = 256 / T slices per target), so the
 // threads of a warp read different records (consecutive 48-byte records are
 // free of shared-memory bank conflicts for 16-byte loads).  The slice sums are
 // folded with FP32 two-sum, first across the lanes of a warp (shuffles), then
@@ -14,30 +14,29 @@
 // Heun step of Sec. IV, spring force of Eq. (4), stroke average) and
 // publishes their next records.
 //
-// Exchange.  Records travel through global memory as tagged 64-bit words
-// (FP32 value, 32-bit evaluation tag; a naturally aligned 64-bit access is
-// single-copy atomic), double-buffered by evaluation parity.  Each evaluation
-// every CTA polls the S - T records it does not own into shared memory.  A
-// slot is rewritten (evaluation e + 2) only after its owner has finished
-// evaluation e + 1, which needed every CTA's records of e + 1, which each CTA
-// publishes only after it copied all records of evaluation e into shared
-// memory: no reader can still be reading the old contents.  Every wait is
-// bounded (global timer and the shared abort flag); a CTA whose wait runs
-// out raises FLAG_TIMEOUT and stops, the others then give up too.  No CTA
-// touches another CTA's shared memory, so a CTA may leave early.
+// Exchange.  Records travel through global memory as three 16-byte words, one
+// per axis, each made of two single-copy-atomic 64-bit halves (a position and
+// its sphere's G, whose lowest bit carries the evaluation's parity bit),
+// double-buffered by evaluation parity.  A slot is rewritten (evaluation e + 2)
+// only after its owner has finished evaluation e + 1, which needed every CTA's
+// records of e + 1, which each CTA publishes only after it has copied all
+// records of evaluation e into shared memory: a slot read for e holds e or
+// e - 2, and the parity bit tells them apart.  Every wait is bounded (global
+// timer and the shared abort flag); a CTA whose wait runs out raises
+// FLAG_TIMEOUT and stops, the others then give up too.  No CTA touches another
+// CTA's shared memory, so a CTA may leave early.
 //
 // Precision (FP32C).  Pair sums in FP32 with two-sum folding, as in
 // eval_kernel.  Positions (relative to the suspension's centre), their Heun
 // update and the stroke-average sums are FP64; an FP64 instruction holds its SM
 // sub-partition for 64 cycles on this part, so that work is kept off the
 // critical path: the corrector leaves its inputs in registers of the three axis
-// warps, and the next poll runs it while its first round of loads is in flight
-// (it costs no time there: those warps wait for records anyway).  The critical path
-// takes the Heun step on a double-single copy of the positions (refreshed from
-// the FP64 state at every launch); the rest length L and d^2 = |x_b - x_a|^2
-// are double-single pairs hi + lo (Dekker's two-sum and the FMA two-product),
-// so the small stretch d - L = (d^2 - L^2)/(d + L) keeps FP32 relative
-// accuracy; the force and the velocity are FP32, as in the records.
+// warps, and the next poll runs it while its first round of loads is in flight.
+// The critical path takes the Heun step on a double-single copy of the
+// positions (refreshed from the FP64 state at every launch); the rest length L
+// and d^2 = |x_b - x_a|^2 are double-single pairs hi + lo (Dekker's two-sum and
+// the FMA two-product), so the small stretch d - L = (d^2 - L^2)/(d + L) keeps
+// FP32 relative accuracy; the force and the velocity are FP32, as in the records.
 #pragma once
 #include "dbs_common.cuh"
 #include "eval_kernel.cuh"
@@ -60,13 +59,6 @@ __device__ __forceinline__ ulonglong2 ld_tagged(const ulonglong2 *p)
     ulonglong2 v;
     asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p) : "memory");
     return v;
-}
-
-__device__ __forceinline__ void st_tagged(ulonglong2 *p, float a, float b, unsigned tag)
-{
-    const unsigned long long hi = (unsigned long long)tag << 32;
-    const unsigned long long x = hi | __float_as_uint(a), y = hi | __float_as_uint(b);
-    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(x), "l"(y) : "memory");
 }
 
 __device__ __forceinline__ bool tagged(const ulonglong2 &v, unsigned tag)
@@ -143,89 +135,63 @@ __device__ __forceinline__ double ds_to_double(ds a) { return (double)a.h + (dou
 
 __device__ __forceinline__ ds ds_neg(ds a) { return {-a.h, -a.l}; }
 
-// Poll the tagged words base[j NT] (bit j of `pending`) until each carries
-// `tag`, and store its two values to dst[2 j NT], dst[2 j NT + 1].  Two rounds of
-// loads are kept in flight, the second issued `stagger` cycles after the first,
-// so every word is read twice per memory round trip: a word that becomes
-// visible just after one round passed it is seen by the other about half a
-// round trip later.  `gap()` runs between the two rounds, while the first is in
-// flight (it may take longer than `stagger`).  False on timeout or abort (see
-// wait_tagged).
-template <int NB, int NT, class Gap>
-__device__ __forceinline__ bool poll_staggered(const ulonglong2 *base, float *dst, unsigned pending,
-                                               unsigned tag, int *flags, unsigned long long timeout_ns,
-                                               int stagger, Gap &&gap)
+// ---- compact tagged record words ------------------------------------------------
+// The record of dumbbell s travels as three 16-byte words, one per axis a:
+// {p_a(2s), G_a(2s), p_a(2s+1), G_a(2s+1)}.  Each 64-bit half (a position and its
+// sphere's G) is written and read as one single-copy-atomic access, and the lowest
+// significand bit of its G carries the evaluation's parity bit, so a reader that
+// sees the expected bit in a half has that evaluation's pair of values.  G is
+// rounded once to FP32 and its lowest bit cleared before use, on the writer's and
+// on every reader's side alike (a relative change below 2^-23).
+//
+// Buffers alternate by evaluation parity, so a slot read for evaluation e holds
+// evaluation e or e - 2: the parity bit of e is bit 1 of e, inverted, which
+// differs between the two (evaluations 0 and 1 of a zero-cleared buffer expect 1).
+__device__ __forceinline__ unsigned flow_bit(unsigned e) { return ((e >> 1) & 1u) ^ 1u; }
+
+__device__ __forceinline__ float g_clear(float g) { return __uint_as_float(__float_as_uint(g) & ~1u); }
+
+__device__ __forceinline__ void st_word(ulonglong2 *p, float pa, float ga, float pb, float gb, unsigned bit)
 {
-    ulonglong2 va[NB], vb[NB];
-#pragma unroll
-    for (int j = 0; j < NB; ++j)
-        if ((pending >> j) & 1u) va[j] = ld_tagged(base + j * NT);
-    const long long c0 = clock64();
-    gap();
-    while (clock64() - c0 < stagger) {
-    }
-    unsigned long long t0 = 0;
-    for (unsigned it = 0;; ++it) {
-        const unsigned pb = pending;
-#pragma unroll
-        for (int j = 0; j < NB; ++j)
-            if ((pb >> j) & 1u) vb[j] = ld_tagged(base + j * NT);
-#pragma unroll
-        for (int j = 0; j < NB; ++j)
-            if (((pending >> j) & 1u) && tagged(va[j], tag)) {
-                dst[2 * j * NT] = lo_float(va[j].x);
-                dst[2 * j * NT + 1] = lo_float(va[j].y);
-                pending &= ~(1u << j);
-            }
-        if (!pending) return true;
-        const unsigned pa = pending;
-#pragma unroll
-        for (int j = 0; j < NB; ++j)
-            if ((pa >> j) & 1u) va[j] = ld_tagged(base + j * NT);
-#pragma unroll
-        for (int j = 0; j < NB; ++j)   // pending is within pb: vb[j] was loaded
-            if (((pending >> j) & 1u) && tagged(vb[j], tag)) {
-                dst[2 * j * NT] = lo_float(vb[j].x);
-                dst[2 * j * NT + 1] = lo_float(vb[j].y);
-                pending &= ~(1u << j);
-            }
-        if (!pending) return true;
-        if (it == 0) t0 = flow_ns();
-        if ((it & 7u) == 7u) {
-            if (*(volatile int *)flags & FLAG_TIMEOUT) return false;
-            if (flow_ns() - t0 > timeout_ns) {
-                atomicOr(flags, FLAG_TIMEOUT);
-                return false;
-            }
-        }
-    }
+    const unsigned long long x = (unsigned long long)((__float_as_uint(ga) & ~1u) | bit) << 32 | __float_as_uint(pa);
+    const unsigned long long y = (unsigned long long)((__float_as_uint(gb) & ~1u) | bit) << 32 | __float_as_uint(pb);
+    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(x), "l"(y) : "memory");
 }
 
-__device__ __forceinline__ void put_record(DbF32 *t, const float r[12])
+__device__ __forceinline__ bool word_has(const ulonglong2 &v, unsigned bit)
 {
-    float4 *q = (float4 *)t;
-    q[0] = make_float4(r[0], r[1], r[2], r[3]);
-    q[1] = make_float4(r[4], r[5], r[6], r[7]);
-    q[2] = make_float4(r[8], r[9], r[10], r[11]);
+    return ((((unsigned)(v.x >> 32) ^ bit) | ((unsigned)(v.y >> 32) ^ bit)) & 1u) == 0u;
 }
 
-__device__ __forceinline__ void publish_record(ulonglong2 *dst, const float r[12], unsigned tag)
+// Store word a of a record into its shared-memory copy (the DbF32 layout, whose
+// pairs (sphere 2s, sphere 2s+1) feed the paired f32x2 instructions directly):
+// positions along a into pair a, G along a (parity bit cleared) into pair 3 + a.
+__device__ __forceinline__ void put_word(DbF32 *rec, int a, const ulonglong2 &v)
 {
-#pragma unroll
-    for (int w = 0; w < 6; ++w) st_tagged(dst + w, r[2 * w], r[2 * w + 1], tag);
+    float2 *q = (float2 *)rec;
+    q[a] = make_float2(__uint_as_float((unsigned)v.x), __uint_as_float((unsigned)v.y));
+    q[3 + a] = make_float2(__uint_as_float((unsigned)(v.x >> 32) & ~1u),
+                           __uint_as_float((unsigned)(v.y >> 32) & ~1u));
+}
+
+__device__ __forceinline__ void put_axis(DbF32 *rec, int a, float pa, float ga, float pb, float gb)
+{
+    float2 *q = (float2 *)rec;
+    q[a] = make_float2(pa, pb);
+    q[3 + a] = make_float2(ga, gb);
 }
 
 __device__ __forceinline__ bool finite_f(float v) { return ((__float_as_uint(v) >> 23) & 0xffu) != 0xffu; }
 
 constexpr int FLOW_NT = 256;      // threads per CTA (8 warps)
-constexpr int FLOW_POLL = 12;     // tagged words polled per thread per round (two rounds in flight)
+constexpr int FLOW_NW = FLOW_NT / 32;
 
 struct FlowArgs {
-    ulonglong2 *rec;   // tagged records [2][Spad][6]: word w holds record floats 2w, 2w+1
+    ulonglong2 *rec;   // tagged records [2][Spad][3]: word a = axis a of the dumbbell
     DbF32 *pack;       // plain records of the final state (the grid path's input)
     int64_t n0;        // step number at launch
     int G, K;          // CTAs (owners of T dumbbells each), Heun steps
-    unsigned base;     // tag of evaluation 0
+    unsigned base;     // evaluation counter at evaluation 0 of the launch (even)
     unsigned long long timeout_ns;
 };
 
@@ -266,14 +232,121 @@ __device__ __noinline__ void draw_sphere_normals(unsigned long long seed, int64_
     z[2 * stride] = w[2];
 }
 
-// NOISE: additive Brownian noise on (a separate instantiation).
-template <int MOB, int T, bool NOISE, int NT = FLOW_NT>
-__global__ void __launch_bounds__(NT, 1) flow_kernel(const EvalArgs A, const FlowArgs P)
+// Fold the (sum, compensation) pairs of 8 slots (the six components of one target
+// dumbbell and two empty ones) across the LS consecutive lanes that hold partial
+// sums of the same target, by transposition: while a lane carries more than one
+// slot, each level halves them (the lane whose level bit is clear keeps the lower
+// half and merges its partner's copy of it, the other lane the upper half); the
+// levels left are a butterfly on the one slot.  On return the lane carries the
+// M = max(1, 8 / LS) slots [base, base + M) in fs[0 .. M), fc[0 .. M).
+template <int LS>
+__device__ __forceinline__ int lane_fold(float (&fs)[8], float (&fc)[8], int lane)
 {
-    constexpr int POLL = NT >= 512 ? FLOW_POLL / 2 : FLOW_POLL;   // words per thread in flight
+    int base = 0;
+#pragma unroll
+    for (int off = LS / 2, m = 8; off >= 1; off >>= 1) {
+        if (m > 1) {
+            const int h = m / 2;
+            const bool hi = (lane & off) != 0;
+#pragma unroll
+            for (int k = 0; k < h; ++k) {
+                const float ss = hi ? fs[k] : fs[k + h], sc = hi ? fc[k] : fc[k + h];
+                const float ks = hi ? fs[k + h] : fs[k], kc = hi ? fc[k + h] : fc[k];
+                const float rs = __shfl_xor_sync(0xffffffffu, ss, off);
+                const float rc = __shfl_xor_sync(0xffffffffu, sc, off);
+                fs[k] = ks;
+                fc[k] = kc;
+                ts_merge(fs[k], fc[k], rs, rc);
+            }
+            base += hi ? h : 0;
+            m = h;
+        } else {
+            const float rs = __shfl_xor_sync(0xffffffffu, fs[0], off);
+            const float rc = __shfl_xor_sync(0xffffffffu, fc[0], off);
+            ts_merge(fs[0], fc[0], rs, rc);
+        }
+    }
+    return base;
+}
+
+// Poll the compact words base[j NT] (bit j of `pending`) of word index w0 + j NT
+// until each carries the parity bit `bit`, and store its values into the tile
+// (record idx / 3, axis idx mod 3).  Two rounds of loads are kept in flight, va
+// and vb, the second issued `stagger` cycles after the first, so every word is
+// read twice per memory round trip: a word that becomes visible just after one
+// round passed it is seen by the other about half a round trip later.  `gap()`
+// runs between the two rounds, while the first is in flight.  On return one
+// round may still be in flight; the caller owns va and vb, so it decides whether
+// their registers stay reserved until that round has landed.  False on timeout
+// or abort.
+template <int NB, int NT, class Gap>
+__device__ __forceinline__ bool poll_words(const ulonglong2 *base, DbF32 *tile, int w0, unsigned pending,
+                                           unsigned bit, int *flags, unsigned long long timeout_ns,
+                                           int stagger, Gap &&gap, ulonglong2 (&va)[NB],
+                                           ulonglong2 (&vb)[NB])
+{
+    auto store = [&](int j, const ulonglong2 &v) {
+        const int idx = w0 + j * NT;
+        put_word(tile + idx / 3, idx - 3 * (idx / 3), v);
+    };
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        if ((pending >> j) & 1u) va[j] = ld_tagged(base + j * NT);
+    const long long c0 = clock64();
+    gap();
+    while (clock64() - c0 < stagger) {
+    }
+    unsigned long long t0 = 0;
+    for (unsigned it = 0;; ++it) {
+        const unsigned pb = pending;
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+            if ((pb >> j) & 1u) vb[j] = ld_tagged(base + j * NT);
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+            if (((pending >> j) & 1u) && word_has(va[j], bit)) {
+                store(j, va[j]);
+                pending &= ~(1u << j);
+            }
+        if (!pending) return true;
+        const unsigned pa = pending;
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+            if ((pa >> j) & 1u) va[j] = ld_tagged(base + j * NT);
+#pragma unroll
+        for (int j = 0; j < NB; ++j)   // pending is within pb: vb[j] was loaded
+            if (((pending >> j) & 1u) && word_has(vb[j], bit)) {
+                store(j, vb[j]);
+                pending &= ~(1u << j);
+            }
+        if (!pending) return true;
+        if (it == 0) t0 = flow_ns();
+        if ((it & 7u) == 7u) {
+            if (*(volatile int *)flags & FLAG_TIMEOUT) return false;
+            if (flow_ns() - t0 > timeout_ns) {
+                atomicOr(flags, FLAG_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+// NOISE: additive Brownian noise on (a separate instantiation).
+template <int MOB, int T, bool NOISE>
+__global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, const FlowArgs P)
+{
+    constexpr int NT = FLOW_NT;
     constexpr int PS = NT / T;                 // slices (threads) per target dumbbell
     constexpr int LW = PS < 32 ? PS : 32;      // lanes of one target within a warp
     constexpr int WPT = PS > 32 ? PS / 32 : 1; // warps per target
+    // words per thread and round: up to 6 words (S <= 512 in one round) the poll's
+    // registers stay reserved across the evaluation, so that the round still in
+    // flight when the last word arrives is never waited for; above that (larger
+    // systems, whose sweep dominates) 12 words per round and the registers are
+    // released after the poll
+    constexpr bool KEEP = T <= 4;
+    constexpr int POLL = KEEP ? 6 : 12;
+    static_assert(LW >= 8, "the transposing fold needs 8 lanes per target");
     extern __shared__ float4 flow_smem[];     // all S records (Spad x DbF32)
     __shared__ FlowOwner<T> own;
     __shared__ float2 red[WPT == 1 ? T : NT / 32][6];   // folded sums per (target, warp)
@@ -299,7 +372,6 @@ __global__ void __launch_bounds__(NT, 1) flow_kernel(const EvalArgs A, const Flo
     if (warp == 0 && lane < nown) {
         const int d = lane, s = st0 + d;
         const int64_t o = 6 * (int64_t)s;
-        float r[12];
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             own.x[k][d] = A.x[o + k] - cen[k % 3];
@@ -318,19 +390,22 @@ __global__ void __launch_bounds__(NT, 1) flow_kernel(const EvalArgs A, const Flo
 #pragma unroll
             for (int k = 0; k < 3; ++k) own.R[k][d] = A.Racc[3 * (int64_t)s + k];
         }
-        r[0] = (float)own.x[0][d]; r[1] = (float)own.x[3][d]; r[2] = (float)own.x[1][d];
-        r[3] = (float)own.x[4][d]; r[4] = (float)own.x[2][d]; r[5] = (float)own.x[5][d];
-        r[6] = own.F[0][d] * k8; r[7] = own.F[3][d] * k8; r[8] = own.F[1][d] * k8;
-        r[9] = own.F[4][d] * k8; r[10] = own.F[2][d] * k8; r[11] = own.F[5][d] * k8;
-        put_record(tile + s, r);
-        publish_record(P.rec + (size_t)s * 6, r, P.base);
+        const unsigned bit = flow_bit(P.base);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float pa = (float)own.x[a][d], pb = (float)own.x[a + 3][d];
+            const float ga = g_clear(own.F[a][d] * k8), gb = g_clear(own.F[a + 3][d] * k8);
+            put_axis(tile + s, a, pa, ga, pb, gb);
+            st_word(P.rec + (size_t)s * 3 + a, pa, ga, pb, gb, bit);
+        }
     }
     const float2 c2 = make_float2(A.c2, A.c2), c3 = make_float2(A.c3, A.c3);
-    const int nwords = 6 * S;
-    const int own_w0 = 6 * st0, own_w1 = 6 * (st0 + nown);   // words not polled (own records)
+    const int nwords = 3 * S;
+    const int own_w0 = 3 * st0, own_w1 = 3 * (st0 + nown);   // words not polled (own records)
     const int t_me = tid / PS, sl = tid - t_me * PS;         // sweep: target and slice
     const int s_me = st0 + t_me;
     const bool act = t_me < nown;
+    ulonglong2 kva[KEEP ? POLL : 1], kvb[KEEP ? POLL : 1];   // the kept poll registers
 
     // The FP64 Heun update x_{n+1} = x_n + dt/2 (v0 + v1) (+ noise) of the state
     // and the stroke average of the geometric centre (trapezoid rule) stay off the
@@ -370,11 +445,11 @@ __global__ void __launch_bounds__(NT, 1) flow_kernel(const EvalArgs A, const Flo
 
     bool dead = false;
     for (int ev = 0; ev < 2 * P.K && !dead; ++ev) {
-        const unsigned tag = P.base + (unsigned)ev;
+        const unsigned bit = flow_bit(P.base + (unsigned)ev);
         const int par = ev & 1;
         const bool corr = (ev & 1) != 0;
         const int64_t n = P.n0 + (ev >> 1);
-        const ulonglong2 *R = P.rec + (size_t)par * Spad * 6;
+        const ulonglong2 *R = P.rec + (size_t)par * Spad * 3;
         float4 trig = make_float4(0.f, 0.f, 1.f, 0.f);
         if (warp == 3) trig = A.trig_df[(n + 1) & A.trig_mask];   // rest length (epilogue warp 3)
 
@@ -399,8 +474,14 @@ __global__ void __launch_bounds__(NT, 1) flow_kernel(const EvalArgs A, const Flo
                 const int idx = b0 + j * NT + tid;
                 if (idx < nwords && (idx < own_w0 || idx >= own_w1)) pend |= 1u << j;
             }
-            ok = poll_staggered<POLL, NT>(R + b0 + tid, (float *)tile + 2 * (b0 + tid), pend, tag,
-                                          A.flags, P.timeout_ns, DBS_FLOW_STAGGER, flush_fp64);
+            if constexpr (KEEP) {
+                ok = poll_words<POLL, NT>(R + b0 + tid, tile, b0 + tid, pend, bit, A.flags, P.timeout_ns,
+                                          DBS_FLOW_STAGGER, flush_fp64, kva, kvb);
+            } else {
+                ulonglong2 va[POLL], vb[POLL];
+                ok = poll_words<POLL, NT>(R + b0 + tid, tile, b0 + tid, pend, bit, A.flags, P.timeout_ns,
+                                          DBS_FLOW_STAGGER, flush_fp64, va, vb);
+            }
         }
         flush_fp64();   // done in the first gap: ends the live range of its inputs
         dead = __syncthreads_or(!ok);
@@ -431,62 +512,24 @@ __global__ void __launch_bounds__(NT, 1) flow_kernel(const EvalArgs A, const Flo
         }
 
         // 3. fold the slices of each target: FP32 two-sum across the LW lanes of a
-        // warp, then across the WPT warps of a target in warp order.  The lanes
-        // fold by transposition: the six components sit in eight slots, and each
-        // of the first three levels halves the slots a lane carries (the lane
-        // whose level bit is clear keeps the lower half and merges its partner's
-        // copy of it into its own, the other lane the upper half), so a level
-        // moves half as many words as the one before; the remaining levels are a
-        // plain butterfly on the one slot left.  14 shuffles per thread at LW = 32
-        // instead of 60 for a butterfly on all six.
-        static_assert(LW >= 8, "the transposing fold needs 8 lanes per target");
-        float fs[8], fc[8];
+        // warp by transposition (lane_fold: the six components sit in eight slots,
+        // each of the first three levels halves the slots a lane carries, the rest
+        // is a butterfly on the one slot left: 14 shuffle pairs at LW = 32 instead
+        // of 30 for a butterfly on all six), then across the WPT warps of a target
+        // in warp order in the epilogue
+        {
+            float fs[8], fc[8];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            fs[k] = qa[k].x + qa[k].y;
-            fs[3 + k] = qb[k].x + qb[k].y;
-        }
-        fs[6] = 0.f;
-        fs[7] = 0.f;
-        int ci = 0;   // first slot (component) this lane still carries
-        {   // 8 -> 4 slots; the slice sums carry no compensation yet
-            const bool hi = (lane & (LW / 2)) != 0;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float send = hi ? fs[k] : fs[k + 4];
-                const float keep = hi ? fs[k + 4] : fs[k];
-                const float r = __shfl_xor_sync(0xffffffffu, send, LW / 2);
-                fs[k] = keep;
-                fc[k] = 0.f;
-                ts_merge(fs[k], fc[k], r, 0.f);
+            for (int k = 0; k < 3; ++k) {
+                fs[k] = qa[k].x + qa[k].y;
+                fs[3 + k] = qb[k].x + qb[k].y;
             }
-            ci += hi ? 4 : 0;
-        }
+            fs[6] = fs[7] = 0.f;
 #pragma unroll
-        for (int h = 2; h >= 1; h >>= 1) {   // 4 -> 2 -> 1 slots
-            const int off = LW / (8 / h);
-            const bool hi = (lane & off) != 0;
-#pragma unroll
-            for (int k = 0; k < h; ++k) {
-                const float ss = hi ? fs[k] : fs[k + h], sc = hi ? fc[k] : fc[k + h];
-                const float ks = hi ? fs[k + h] : fs[k], kc = hi ? fc[k + h] : fc[k];
-                const float rs = __shfl_xor_sync(0xffffffffu, ss, off);
-                const float rc = __shfl_xor_sync(0xffffffffu, sc, off);
-                fs[k] = ks;
-                fc[k] = kc;
-                ts_merge(fs[k], fc[k], rs, rc);
-            }
-            ci += hi ? h : 0;
+            for (int k = 0; k < 8; ++k) fc[k] = 0.f;
+            const int sb = lane_fold<LW>(fs, fc, lane);
+            if ((lane & (LW / 8 - 1)) == 0 && sb < 6) red[WPT == 1 ? t_me : warp][sb] = make_float2(fs[0], fc[0]);
         }
-#pragma unroll
-        for (int off = LW / 16; off >= 1; off >>= 1) {
-            const float rs = __shfl_xor_sync(0xffffffffu, fs[0], off);
-            const float rc = __shfl_xor_sync(0xffffffffu, fc[0], off);
-            ts_merge(fs[0], fc[0], rs, rc);
-        }
-        // one pair per (target, warp, component): the epilogue folds the WPT warps
-        // of a target
-        if ((lane & (LW / 8 - 1)) == 0 && ci < 6) red[WPT == 1 ? t_me : warp][ci] = make_float2(fs[0], fc[0]);
         __syncthreads();
 
         // 4. epilogue.  Warps 0-2 take axis a = warp of the owned dumbbells (lane d):
@@ -563,24 +606,21 @@ __global__ void __launch_bounds__(NT, 1) flow_kernel(const EvalArgs A, const Flo
             const float Fa = fmaf(f, eh, own.fext[a][d]), Fb = fmaf(-f, eh, own.fext[a + 3][d]);
             own.F[a][d] = Fa;
             own.F[a + 3][d] = Fb;
-            const float2 wp = make_float2(pa, pb), wg = make_float2(Fa * k8, Fb * k8);
+            const float ga = g_clear(Fa * k8), gb = g_clear(Fb * k8);
             const int s = st0 + d;
-            float2 *tr = (float2 *)(tile + s);
-            tr[a] = wp;            // record word a: positions along a
-            tr[3 + a] = wg;        // record word 3 + a: G along a
+            put_axis(tile + s, a, pa, ga, pb, gb);   // record word a of the next evaluation
             if (ev + 1 < 2 * P.K) {
-                ulonglong2 *dst = P.rec + ((size_t)(par ^ 1) * Spad + s) * 6;
-                st_tagged(dst + a, wp.x, wp.y, tag + 1);
-                st_tagged(dst + 3 + a, wg.x, wg.y, tag + 1);
+                st_word(P.rec + ((size_t)(par ^ 1) * Spad + s) * 3 + a, pa, ga, pb, gb,
+                        flow_bit(P.base + (unsigned)ev + 1u));
             } else {
                 float2 *pk = (float2 *)(P.pack + s);   // the final state's records, for the grid path
-                pk[a] = wp;
-                pk[3 + a] = wg;
+                pk[a] = make_float2(pa, pb);
+                pk[3 + a] = make_float2(ga, gb);
             }
             if (corr) hn = n;   // the FP64 update of step n runs in the next poll
         }
         // no barrier here: the next poll writes only records this CTA does not own,
-        // and the next sweep starts after the poll's barrier
+        // and the next sweep reads the own records after the poll's barrier
     }
 
     // ---- write the owned state back ----------------------------------------------

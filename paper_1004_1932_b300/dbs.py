@@ -234,6 +234,24 @@ class Suspension:
         """j-split of the pair sum (0 = built-in choice); used by the autotuner."""
         self._check(load().dbs_set_chunks(self._h, ctypes.c_int32(int(chunks))))
 
+    # -- row sharding (dbs_shard_*): one suspension split over several ranks --
+    def shard_set(self, nranks: int, rank: int):
+        """Compute only rank ``rank``'s row block in shard_eval; returns (row0, row1)."""
+        r0, r1 = ctypes.c_int64(), ctypes.c_int64()
+        self._check(load().dbs_shard_set(self._h, ctypes.c_int32(int(nranks)), ctypes.c_int32(int(rank)),
+                                         ctypes.byref(r0), ctypes.byref(r1)))
+        return r0.value, r1.value
+
+    def shard_eval(self, phase: int):
+        """One evaluation of the row block: 0 = predictor, 1 = corrector."""
+        self._check(load().dbs_shard_eval(self._h, ctypes.c_int32(int(phase))))
+
+    def shard_buffers(self):
+        """(device pointer of record buffer A, of B, bytes per record)."""
+        a, b, rb = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int64()
+        self._check(load().dbs_shard_buffers(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(rb)))
+        return a.value, b.value, rb.value
+
     def get_launch(self):
         bt, c, g = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         self._check(load().dbs_get_launch(self._h, ctypes.byref(bt), ctypes.byref(c), ctypes.byref(g)))
@@ -476,6 +494,16 @@ class Engine:
         self._check(load().dbs_engine_tick(self._h, ctypes.byref(a), ctypes.byref(q)))
         return a.value, q.value
 
+    def stats(self) -> dict:
+        """Host-side accounting (``dbs_engine_stats``)."""
+        class _St(ctypes.Structure):
+            _fields_ = [("ticks", ctypes.c_int64), ("ensemble_rebuilds", ctypes.c_int64),
+                        ("tick_s", ctypes.c_double), ("rebuild_s", ctypes.c_double),
+                        ("wait_s", ctypes.c_double)]
+        st = _St()
+        self._check(load().dbs_engine_stats(self._h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in _St._fields_}
+
     def poll(self, rid: int):
         st = ctypes.c_int32()
         x = np.empty((2 * self._S[rid], 3))
@@ -544,7 +572,7 @@ def check_wait_timeout(timeout_ms: int = 100) -> int:
 class DeviceView:
     """Zero-copy view of library-owned device memory for torch (``torch.as_tensor``)."""
 
-    def __init__(self, ptr: int, shape, device_index: int = 0):
-        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f8",
+    def __init__(self, ptr: int, shape, device_index: int = 0, typestr: str = "<f8"):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
                                          "data": (int(ptr), False), "version": 3, "strides": None}
         self.device_index = device_index

@@ -10,9 +10,27 @@ lattice_msd_sa   the same quantity from the stroke-averaged model of
                  Eqs. (9a)-(9e) started from the same initial condition.
 colloids_rate    Sec. IV speed-up workload: N colloids under a constant force
                  (Oseen); GPU Heun steps per second.
+effective_amplitude
+                 the stroke amplitude the dumbbells actually perform: the
+                 lengths d_s(t) of the microscopic model over one period
+                 (after a settling period) projected on sin and cos of
+                 (omega t + phi_s).  The spring model is shape-driven (Sec. II)
+                 only when the spring relaxes much faster than one stroke; at
+                 k0 = 1, a = 0.05 it lags, so its amplitude is smaller than the
+                 rest length's.
+sa_comparison    the pair-distance error of the stroke-averaged model of
+                 Eqs. (9a)-(9e) against the period-averaged centres of the
+                 microscopic model, at given stroke amplitudes.
+serving_trace    a Poisson stream of simulation requests through the serving
+                 engine (admission by a device-memory budget, continuous
+                 batching): makespan, request latencies, and the engine's host
+                 accounting (ticks, ensemble rebuilds); the same requests one
+                 at a time in arrival order, from measured per-step times.
 
     python -m paper_1004_1932_b300.experiments lattice --x 5 --W 100 --spacing 10 [--phases random]
     python -m paper_1004_1932_b300.experiments colloids --N 2000 --steps 2000
+    python -m paper_1004_1932_b300.experiments serving [--requests 200 --steps-hi 1e5 --rate 200]
+    python -m paper_1004_1932_b300.experiments serving --full
 """
 from __future__ import annotations
 
@@ -84,6 +102,173 @@ def lattice_msd_sa(x=5, spacing_over_ell=10.0, W=100, phases="checkerboard", see
             "msd_over_ell2": msd / s0.ell ** 2}
 
 
+def effective_amplitude(s, samples=50, settle_periods=1, precision="fp32c", path="coop"):
+    """Measured stroke amplitude of the microscopic model (every step on the GPU).
+
+    After ``settle_periods`` periods, the dumbbell lengths d_s(t_k) are read at
+    ``samples`` equally spaced times of the next period; their first Fourier
+    coefficients against sin(omega t + phi_s) and cos(omega t + phi_s) give
+    d_s ~ mean_s + lam_eff_s sin(omega t + phi_s - lag_s).  Returns the
+    per-dumbbell lam_eff_s and lag_s and their means."""
+    T = 2 * math.pi / s.omega
+    m = int(round(T / s.dt))
+    if m % samples:
+        raise ValueError("samples must divide the steps of one period")
+    stride = m // samples
+    d = np.empty((samples, s.S))
+    tk = np.empty(samples)
+    with dbs.Suspension.from_inputs(s, precision=precision) as h:
+        if precision == "fp32c" and path:
+            h.set_path(path)
+        h.step(m * settle_periods)
+        for k in range(samples):
+            x = h.positions()
+            tk[k] = h.get_time()[1]
+            d[k] = np.linalg.norm(x[1::2] - x[0::2], axis=1)
+            h.step(stride)
+    ph = s.omega * tk[:, None] + s.phi[None, :]
+    dev = d - d.mean(axis=0)
+    A = 2.0 / samples * np.sum(dev * np.sin(ph), axis=0)
+    B = 2.0 / samples * np.sum(dev * np.cos(ph), axis=0)
+    lam_eff = np.hypot(A, B)
+    lag = np.arctan2(-B, A)
+    return {"lam_eff": lam_eff, "lag": lag, "lam_eff_mean": float(lam_eff.mean()),
+            "ratio_mean": float(np.mean(lam_eff / s.lam)), "lag_mean": float(lag.mean())}
+
+
+def linear_response_ratio(s):
+    """Amplitude ratio and lag of an isolated dumbbell's length in the linearised
+    spring model: d' = -kappa (d - L(t)) with kappa = 2 k0 (1/(6 pi mu a) - h(ell)),
+    h the pair mobility along the axis (Oseen 1/(4 pi mu r), RPY minus
+    a^2/(6 pi mu r^3), Eq. (3b)); ratio = 1/sqrt(1 + (omega/kappa)^2)."""
+    r = s.ell
+    h = 1.0 / (4 * math.pi * s.mu * r)
+    if s.mobility == "rpy":
+        h -= s.a ** 2 / (6 * math.pi * s.mu * r ** 3)
+    kappa = 2 * s.k0 * (1.0 / (6 * math.pi * s.mu * s.a) - h)
+    w = s.omega / kappa
+    return 1.0 / math.sqrt(1.0 + w * w), math.atan(w)
+
+
+def sa_comparison(s, periods=4, lam=None, sa_steps=10, precision="fp32c", path="coop"):
+    """Pair-distance error of the stroke-averaged model against the microscopic
+    one: period-averaged centres of periods 1 and ``periods - 1`` (the first
+    period is discarded) against the averaged model at the middle of those
+    periods, both started from the same initial condition.  ``lam``: the
+    averaged model's stroke amplitudes (default: the nominal ones)."""
+    import torch
+    T = 2 * math.pi / s.omega
+    m = int(round(T / s.dt))
+    lam = s.lam if lam is None else np.broadcast_to(np.asarray(lam, float), s.lam.shape).copy()
+    with dbs.Suspension.from_inputs(s, precision=precision) as h, \
+            dbs.StrokeAveraged(s.R0, s.N0, s.phi, lam, a=s.a, ell=s.ell, omega=s.omega,
+                               dt=T / sa_steps, precision=precision) as sa:
+        if precision == "fp32c" and path:
+            h.set_path(path)
+        h.enable_period_average(m, max_periods=periods)
+        h.step(m * periods)
+        sa.step(sa_steps + sa_steps // 2)                     # middle of period 1
+        ref = torch.empty((s.S, 3), dtype=torch.float64, device="cuda")
+        sa.copy_centres(ref)
+        sa.step(sa_steps * (periods - 2))                     # middle of period periods - 1
+        torch.cuda.synchronize()
+        return dbs.pair_distance_error(s.S, h.period_average_device(1),
+                                       h.period_average_device(periods - 1), ref.data_ptr(),
+                                       sa.centres_device())
+
+
+def _quantile(v, p):
+    v = sorted(v)
+    return v[min(len(v) - 1, int(round(p * (len(v) - 1))))] if v else None
+
+
+def serving_trace(n_req=200, rate=200.0, steps_lo=1e3, steps_hi=1e5, budget=64 << 30, block=256,
+                  sizes=(16, 64, 256, 1024, 4096), seed=0, per_step_s=None):
+    """The serving engine on a Poisson trace (every step on the GPU).  Latency =
+    completion on the host clock minus the request's arrival time.  The one-at-a-
+    time comparison serves the same requests in arrival order, each for steps x
+    its size's measured time per Heun step on its fastest single-system path
+    (``per_step_s``: {S: seconds}; measured here if not given)."""
+    trace = inputs.request_trace(n_req, rate, sizes=sizes, steps_lo=steps_lo, steps_hi=steps_hi,
+                                 seed=seed)
+    if per_step_s is None:
+        per_step_s = step_times(sizes)
+    susp = {rid: inputs.make_suspension(S, seed=1000 + rid, density=0.002) for _, S, _, rid in trace}
+    eng = dbs.Engine(hbm_budget_bytes=budget, block_steps=block)
+    t0 = time.perf_counter()
+    ids, arr_of, done = {}, {}, {}
+    k = 0
+    while len(done) < len(trace):
+        now = time.perf_counter() - t0
+        while k < len(trace) and trace[k][0] <= now:
+            arr, S, n, rid = trace[k]
+            ids[rid] = eng.submit_inputs(susp[rid], n)
+            arr_of[rid] = (arr, time.perf_counter() - t0)
+            k += 1
+        a, q = eng.tick()
+        for rid, eid in ids.items():
+            if rid in done:
+                continue
+            st, _, lat = eng.poll(eid)
+            if st in (dbs.REQ_DONE, dbs.REQ_FAILED, dbs.REQ_CANCELLED):
+                arr, sub = arr_of[rid]
+                done[rid] = (st, (sub - arr) + lat)
+        if a == 0 and q == 0 and k < len(trace):
+            time.sleep(max(0.0, trace[k][0] - (time.perf_counter() - t0)))
+    makespan = time.perf_counter() - t0
+    stats = eng.stats()
+    eng.close()
+    lat = [v[1] for v in done.values() if v[0] == dbs.REQ_DONE]
+    steps_total = sum(n for _, _, n, _ in trace)
+    t_free, lat_seq = 0.0, []
+    for arr, S, n, _ in trace:
+        t_free = max(arr, t_free) + n * per_step_s[S]
+        lat_seq.append(t_free - arr)
+    return {"requests": n_req, "rate_per_s": rate, "steps": [steps_lo, steps_hi],
+            "budget_bytes": budget, "block_steps": block, "completed": len(lat),
+            "engine": {"makespan_s": makespan, "system_steps_per_s": steps_total / makespan,
+                       "requests_per_s": len(lat) / makespan,
+                       "p50_latency_s": _quantile(lat, 0.5), "p99_latency_s": _quantile(lat, 0.99)},
+            "engine_host": stats,
+            "one_at_a_time_modelled": {"makespan_s": t_free, "system_steps_per_s": steps_total / t_free,
+                                       "p50_latency_s": _quantile(lat_seq, 0.5),
+                                       "p99_latency_s": _quantile(lat_seq, 0.99),
+                                       "per_step_s": {str(k_): v for k_, v in per_step_s.items()}}}
+
+
+def step_times(sizes=(16, 64, 256, 1024, 4096), steps=400):
+    """Seconds per Heun step of one suspension of each size on its fastest
+    single-system path (the cooperative path up to 4096 dumbbells)."""
+    out = {}
+    for S in sizes:
+        s = inputs.make_suspension(S, seed=5, density=0.002)
+        with dbs.Suspension.from_inputs(s, precision="fp32c") as h:
+            if S <= 4096:
+                h.set_path("coop")
+            h.step(32)
+            h.sync()
+            t0 = time.perf_counter()
+            h.step(steps)
+            h.sync()
+            out[S] = (time.perf_counter() - t0) / steps
+    return out
+
+
+def serving_full():
+    """The serving configuration: a 200-request Poisson trace (200 requests/s,
+    steps log-uniform in [1e3, 1e5], 64 GB budget); the same request mix at half
+    the engine's measured capacity (100 requests); and a small budget (room for
+    three of the largest requests) that makes admission queue."""
+    per_step = step_times()
+    full = serving_trace(200, 200.0, 1e3, 1e5, per_step_s=per_step)
+    cap = full["engine"]["requests_per_s"]
+    half = serving_trace(100, 0.5 * cap, 1e3, 1e5, seed=1, per_step_s=per_step)
+    small = serving_trace(48, 200.0, 1e3, 1e4, budget=3 * dbs.request_bytes(4096), seed=2,
+                          per_step_s=per_step)
+    return {"offered_200_per_s": full, "half_capacity": {"rate_per_s": 0.5 * cap, **half},
+            "small_budget": small}
+
+
 def colloids_rate(N=2000, steps=2000, mobility="oseen", precision="fp32c"):
     s, F = inputs.colloids(N, mobility=mobility)
     with dbs.Suspension.from_inputs(s, precision=precision) as h:
@@ -111,7 +296,16 @@ def main(argv=None):
     co = sub.add_parser("colloids")
     co.add_argument("--N", type=int, default=2000)
     co.add_argument("--steps", type=int, default=2000)
+    sv = sub.add_parser("serving")
+    sv.add_argument("--full", action="store_true", help="the three runs of serving_full()")
+    sv.add_argument("--requests", type=int, default=48)
+    sv.add_argument("--rate", type=float, default=200.0)
+    sv.add_argument("--steps-hi", type=float, default=1e4)
     a = ap.parse_args(argv)
+    if a.cmd == "serving":
+        r = serving_full() if a.full else serving_trace(a.requests, a.rate, 1e3, a.steps_hi)
+        print(json.dumps(r), flush=True)
+        return
     if a.cmd == "lattice":
         for sp in a.spacing:
             r = lattice_msd(a.x, sp, a.W, a.phases, dt_over_T=a.dt_over_T)
