@@ -42,9 +42,13 @@ FLOPS_PER_PAIR = {"oseen": 27, "rpy": 34}   # algorithmic FP32 flops (FMA = 2), 
 # difference vector, its norm, three projections, the phase factor and the three
 # polynomials, the J and K updates; FMA = 2, rsqrt not counted
 SA_FLOPS_PER_PAIR = 98
-# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture of
-# the same launch (profiles/flow_kernel_rpy_s512_n1024.md): 1024 Heun steps, S = 512, RPY
-NCU_TRAFFIC = {("coop", 512, "rpy"): 424704 + 33792}
+# DRAM bytes (read + write) per launch of the dominant kernel, copied from one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the same launch:
+# the cooperative kernel, 1024 Heun steps, S = 512, RPY.  None until the kernel
+# as it stands has been captured; the line says where the number comes from.
+NCU_TRAFFIC = {}
+TRAFFIC_SOURCE = ("copied from one ncu capture of the same launch (the benchmark cannot run "
+                  "ncu itself); null when no capture of the kernel as it stands exists")
 METRIC = "sphere-pair interactions/s"
 
 
@@ -391,7 +395,7 @@ def sharded_measure(dbs, inputs, torch, stream, ws, rank, dev, S=32768, steps=10
     from paper_1004_1932_b300 import shard
     s = inputs.paper_scale(S, seed=0)
     sh = shard.Shard(s, ws, rank, precision="fp32c", stream=stream, device=dev.index)
-    ex = shard.GroupExchange(device_index=dev.index)
+    ex = shard.GroupExchange()
     shard.step([sh], 2, ex)
     torch.cuda.synchronize(dev)
     torch.distributed.barrier()
@@ -739,6 +743,7 @@ def run_ours(args):
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "traffic": NCU_TRAFFIC.get((path_choice["path"], S, args.mobility)),
+                     "traffic_source": TRAFFIC_SOURCE,
                      "launch_ms": mean_ms, "flops_per_launch": flops_launch,
                      "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
                                    f"{mhz_max:.0f} MHz (max SM clock)"},

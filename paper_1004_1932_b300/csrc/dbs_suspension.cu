@@ -357,10 +357,14 @@ static void choose_launch(dbs_suspension *h)
         return (e == cudaSuccess && occ > 0) ? occ : 1;
     };
     const int64_t iblocks = (h->S + bt - 1) / bt;
-    // chunks of at least 16 (small systems) / 32 dumbbell records; small systems
-    // also keep C x BT within the shared-memory staging of the partials
+    // chunks of at least 16 (small systems) / 32 dumbbell records; small FP32C
+    // systems also keep C x BT within the shared-memory staging of the partials.
+    // Small FP64 systems go down to one record per chunk: an FP64 instruction
+    // holds its SM sub-partition for 64 cycles on this part, so a tiny system's
+    // sums must be spread over many SMs (S = 16: one CTA took ~50 us per
+    // evaluation, measured)
     const int64_t max_chunks = std::max<int64_t>(
-        1, small ? std::min<int64_t>(h->S / 16, STAGE_MAX / bt) : h->S / 32);
+        1, small ? (f64 ? h->S : std::min<int64_t>(h->S / 16, STAGE_MAX / bt)) : h->S / 32);
     // Single pass when it leaves at least 4 chunks: every CTA takes at most one
     // unit, and the fixup of each i-block reads few partials.  Otherwise (large
     // systems) many equal units over the persistent grid, C minimising

@@ -13,7 +13,7 @@ colloids_rate    Sec. IV speed-up workload: N colloids under a constant force
 effective_amplitude
                  the stroke amplitude the dumbbells actually perform: the
                  lengths d_s(t) of the microscopic model over one period
-                 (after a settling period) projected on sin and cos of
+                 (after settling periods) projected on sin and cos of
                  (omega t + phi_s).  The spring model is shape-driven (Sec. II)
                  only when the spring relaxes much faster than one stroke; at
                  k0 = 1, a = 0.05 it lags, so its amplitude is smaller than the
@@ -102,10 +102,12 @@ def lattice_msd_sa(x=5, spacing_over_ell=10.0, W=100, phases="checkerboard", see
             "msd_over_ell2": msd / s0.ell ** 2}
 
 
-def effective_amplitude(s, samples=50, settle_periods=1, precision="fp32c", path="coop"):
+def effective_amplitude(s, samples=50, settle_periods=4, precision="fp32c", path="coop"):
     """Measured stroke amplitude of the microscopic model (every step on the GPU).
 
-    After ``settle_periods`` periods, the dumbbell lengths d_s(t_k) are read at
+    After ``settle_periods`` periods (the lengths relax from the initial condition
+    with a time of about half a period at k0 = 1, a = 0.05: four periods leave
+    e^-8 of the transient), the dumbbell lengths d_s(t_k) are read at
     ``samples`` equally spaced times of the next period; their first Fourier
     coefficients against sin(omega t + phi_s) and cos(omega t + phi_s) give
     d_s ~ mean_s + lam_eff_s sin(omega t + phi_s - lag_s).  Returns the
@@ -172,9 +174,12 @@ def sa_comparison(s, periods=4, lam=None, sa_steps=10, precision="fp32c", path="
         sa.copy_centres(ref)
         sa.step(sa_steps * (periods - 2))                     # middle of period periods - 1
         torch.cuda.synchronize()
-        return dbs.pair_distance_error(s.S, h.period_average_device(1),
-                                       h.period_average_device(periods - 1), ref.data_ptr(),
-                                       sa.centres_device())
+        A0, A1 = h.period_average_device(1), h.period_average_device(periods - 1)
+        out = dbs.pair_distance_error(s.S, A0, A1, ref.data_ptr(), sa.centres_device())
+        # the same call with the models swapped gives the RMS of the microscopic model's change
+        full = dbs.pair_distance_error(s.S, ref.data_ptr(), sa.centres_device(), A0, A1)
+        return {"max": out["max"], "rms": out["rms"], "sa_rms": out["ref_rms"],
+                "full_rms": full["ref_rms"], "pairs": out["pairs"]}
 
 
 def _quantile(v, p):

@@ -55,6 +55,7 @@ class Shard:
         if stream is None or int(stream.cuda_stream) == 0:
             stream = torch.cuda.Stream(device=dev)
         self.stream = stream
+        self.device_index = dev.index
         self.h = dbs.Suspension.from_inputs(susp, precision=precision, stream=stream, device=dev.index)
         self.S = susp.S
         self.rank, self.nranks = rank, nranks
@@ -99,13 +100,10 @@ class LocalExchange:
     """All shards of one split held by this process on one device: copy every
     shard's block into every other shard's buffer (on the shards' stream)."""
 
-    def __init__(self, device_index: int = 0):
-        self.dev = device_index
-
     def __call__(self, ptrs, shards):
         rb = shards[0].record_bytes
         total = shards[0].S * rb
-        bufs = [_device_bytes(p, total, self.dev) for p in ptrs]
+        bufs = [_device_bytes(p, total, s.device_index) for p, s in zip(ptrs, shards)]
         for src, s in zip(bufs, shards):
             lo, hi = s.row0 * rb, s.row1 * rb
             for dst in bufs:
@@ -143,17 +141,15 @@ class GroupExchange:
     Other backends: the buffer goes through host memory (the shard's stream is
     synchronised first)."""
 
-    def __init__(self, group=None, device_index: int = 0):
+    def __init__(self, group=None):
         import torch.distributed as dist
         self.group = group
-        self.dev = device_index
         self.nccl = dist.get_backend(group) == "nccl"
 
     def __call__(self, ptrs, shards):
-        import torch
         (ptr,), (s,) = ptrs, shards
         rb = s.record_bytes
-        dev_buf = _device_bytes(ptr, s.S * rb, self.dev)
+        dev_buf = _device_bytes(ptr, s.S * rb, s.device_index)
         if self.nccl:
             gather_blocks(dev_buf, s.blocks, s.rank, rb, self.group)
             return

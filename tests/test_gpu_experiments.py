@@ -82,7 +82,7 @@ def test_effective_amplitude_follows_linear_response():
 def test_effective_amplitude_matches_oracle_trajectory():
     # the same measurement on an oracle trajectory of a small dense suspension
     s = inputs.make_suspension(16, seed=2, side=8.0)
-    r = experiments.effective_amplitude(s, samples=50, path="coop")
+    r = experiments.effective_amplitude(s, samples=50, settle_periods=1, path="coop")
     m = int(round(2 * math.pi / s.omega / s.dt))
     stride = m // 50
     x = oracle.heun(s.x0, 0, m, dt=s.dt, mobility=oracle.RPY, **s.phys())

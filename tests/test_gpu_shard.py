@@ -41,7 +41,7 @@ def test_local_shards_are_bit_identical_to_unsharded(S, precision, mob, nranks):
     shards = [shard.Shard(s, nranks, r, precision=precision, stream=stream) for r in range(nranks)]
     try:
         assert [(sh.row0, sh.row1) for sh in shards] == shards[0].blocks
-        shard.step(shards, steps, shard.LocalExchange(0))
+        shard.step(shards, steps, shard.LocalExchange())
         stream.synchronize()
         for sh in shards:
             assert sh.h.get_time()[0] == steps
