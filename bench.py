@@ -44,9 +44,9 @@ FLOPS_PER_PAIR = {"oseen": 27, "rpy": 34}   # algorithmic FP32 flops (FMA = 2), 
 SA_FLOPS_PER_PAIR = 98
 # DRAM bytes (read + write) per launch of the dominant kernel, copied from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the same launch:
-# the cooperative kernel, 1024 Heun steps, S = 512, RPY.  None until the kernel
-# as it stands has been captured; the line says where the number comes from.
-NCU_TRAFFIC = {}
+# the cooperative kernel, 1024 Heun steps, S = 512, RPY (null for any other path
+# or size); the line says where the number comes from.
+NCU_TRAFFIC = {("coop", 512, "rpy"): 179968 + 11520}
 TRAFFIC_SOURCE = ("copied from one ncu capture of the same launch (the benchmark cannot run "
                   "ncu itself); null when no capture of the kernel as it stands exists")
 METRIC = "sphere-pair interactions/s"
