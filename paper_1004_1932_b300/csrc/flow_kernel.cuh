@@ -208,7 +208,7 @@ struct FlowOwner {
     float fext[6][T];
     float z[6][T];                    // additive-noise normals of the current step
     float2 ee[3][T];                  // (x_b - x_a)^2 per axis (double-single)
-    float2 L[T], L2[T];               // rest length at t_{n+1} and its square
+    float2 L[2][T], L2[2][T];         // rest length at t_{n+1} and its square, by evaluation parity
 };
 
 // (s, c) += (s2, c2) with Knuth's two-sum on the sums (exact error, any order).
@@ -238,8 +238,9 @@ __device__ __noinline__ void draw_sphere_normals(unsigned long long seed, int64_
 // slot, each level halves them (the lane whose level bit is clear keeps the lower
 // half and merges its partner's copy of it, the other lane the upper half); the
 // levels left are a butterfly on the one slot.  On return the lane carries the
-// M = max(1, 8 / LS) slots [base, base + M) in fs[0 .. M), fc[0 .. M).
-template <int LS>
+// M = max(1, 8 / LS) slots [base, base + M) in fs[0 .. M), fc[0 .. M).  ZERO_C:
+// the compensations start at zero, so the first level moves the sums only.
+template <int LS, bool ZERO_C = false>
 __device__ __forceinline__ int lane_fold(float (&fs)[8], float (&fc)[8], int lane)
 {
     int base = 0;
@@ -248,14 +249,15 @@ __device__ __forceinline__ int lane_fold(float (&fs)[8], float (&fc)[8], int lan
         if (m > 1) {
             const int h = m / 2;
             const bool hi = (lane & off) != 0;
+            const bool first = ZERO_C && m == 8;
 #pragma unroll
             for (int k = 0; k < h; ++k) {
                 const float ss = hi ? fs[k] : fs[k + h], sc = hi ? fc[k] : fc[k + h];
                 const float ks = hi ? fs[k + h] : fs[k], kc = hi ? fc[k + h] : fc[k];
                 const float rs = __shfl_xor_sync(0xffffffffu, ss, off);
-                const float rc = __shfl_xor_sync(0xffffffffu, sc, off);
+                const float rc = first ? 0.f : __shfl_xor_sync(0xffffffffu, sc, off);
                 fs[k] = ks;
-                fc[k] = kc;
+                fc[k] = first ? 0.f : kc;
                 ts_merge(fs[k], fc[k], rs, rc);
             }
             base += hi ? h : 0;
@@ -399,6 +401,7 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
             st_word(P.rec + (size_t)s * 3 + a, pa, ga, pb, gb, bit);
         }
     }
+    __syncthreads();   // the owned state is read by warp 3 (rest length) in the first poll
     const float2 c2 = make_float2(A.c2, A.c2), c3 = make_float2(A.c3, A.c3);
     const int nwords = 3 * S;
     const int own_w0 = 3 * st0, own_w1 = 3 * (st0 + nown);   // words not polled (own records)
@@ -451,7 +454,25 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
         const int64_t n = P.n0 + (ev >> 1);
         const ulonglong2 *R = P.rec + (size_t)par * Spad * 3;
         float4 trig = make_float4(0.f, 0.f, 1.f, 0.f);
-        if (warp == 3) trig = A.trig_df[(n + 1) & A.trig_mask];   // rest length (epilogue warp 3)
+        if (warp == 3) trig = A.trig_df[(n + 1) & A.trig_mask];   // rest length (warp 3, in the poll)
+        // Eq. (4) rest length L(t_{n+1}) and its square, double-single, formed by
+        // warp 3 while the records are on their way (it needs no sum); buffered by
+        // evaluation parity, so the previous evaluation's spring may still read
+        // the other copy
+        auto rest_length_ds = [&]() {
+            if (warp != 3 || lane >= nown) return;
+            const int d = lane;
+            const ds sarg = ds_add(ds_mul({trig.x, trig.y}, {own.cph[d], own.cpl[d]}),
+                                   ds_mul({trig.z, trig.w}, {own.sph[d], own.spl[d]}));
+            const ds L = ds_add(ell, ds_mul({own.lamh[d], own.laml[d]}, sarg));
+            const ds L2 = ds_mul(L, L);
+            own.L[par][d] = make_float2(L.h, L.l);
+            own.L2[par][d] = make_float2(L2.h, L2.l);
+        };
+        auto gap = [&]() {
+            flush_fp64();
+            rest_length_ds();
+        };
 
         // the normals of step n, drawn once (predictor) by the last 2T threads while
         // the other CTAs' records are on their way
@@ -476,11 +497,11 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
             }
             if constexpr (KEEP) {
                 ok = poll_words<POLL, NT>(R + b0 + tid, tile, b0 + tid, pend, bit, A.flags, P.timeout_ns,
-                                          DBS_FLOW_STAGGER, flush_fp64, kva, kvb);
+                                          DBS_FLOW_STAGGER, gap, kva, kvb);
             } else {
                 ulonglong2 va[POLL], vb[POLL];
                 ok = poll_words<POLL, NT>(R + b0 + tid, tile, b0 + tid, pend, bit, A.flags, P.timeout_ns,
-                                          DBS_FLOW_STAGGER, flush_fp64, va, vb);
+                                          DBS_FLOW_STAGGER, gap, va, vb);
             }
         }
         flush_fp64();   // done in the first gap: ends the live range of its inputs
@@ -527,7 +548,7 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
             fs[6] = fs[7] = 0.f;
 #pragma unroll
             for (int k = 0; k < 8; ++k) fc[k] = 0.f;
-            const int sb = lane_fold<LW>(fs, fc, lane);
+            const int sb = lane_fold<LW, true>(fs, fc, lane);
             if ((lane & (LW / 8 - 1)) == 0 && sb < 6) red[WPT == 1 ? t_me : warp][sb] = make_float2(fs[0], fc[0]);
         }
         __syncthreads();
@@ -535,10 +556,11 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
         // 4. epilogue.  Warps 0-2 take axis a = warp of the owned dumbbells (lane d):
         // self term of Eq. (3a), Heun update of both spheres (Sec. IV) on the
         // double-single copy of the positions, the axis component of
-        // e = x_b - x_a; warp 3 the rest length L(t_{n+1}) of Eq. (4).  Then each
-        // axis warp forms the spring magnitude (the same value in the three
-        // warps, which saves a barrier), its force component, writes and
-        // publishes its record words, and only then updates the FP64 state.
+        // e = x_b - x_a (the rest length L(t_{n+1}) of Eq. (4) was formed during
+        // the poll).  Then each axis warp forms the spring magnitude (the same
+        // value in the three warps, which saves a barrier), its force component,
+        // writes and publishes its record words, and only then updates the FP64
+        // state.
         const int a = warp, d = lane;
         const bool eax = warp < 3 && d < nown;
         float pa = 0.f, pb = 0.f, eh = 0.f;
@@ -587,22 +609,15 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
                 own.xs[a + 3][d] = make_float2(nb.h, nb.l);
             }
             if (!(finite_f(pa) && finite_f(pb))) atomicOr(A.flags, FLAG_NONFINITE);
-        } else if (warp == 3 && d < nown) {
-            const ds sarg = ds_add(ds_mul({trig.x, trig.y}, {own.cph[d], own.cpl[d]}),
-                                   ds_mul({trig.z, trig.w}, {own.sph[d], own.spl[d]}));
-            const ds L = ds_add(ell, ds_mul({own.lamh[d], own.laml[d]}, sarg));
-            const ds L2 = ds_mul(L, L);
-            own.L[d] = make_float2(L.h, L.l);
-            own.L2[d] = make_float2(L2.h, L2.l);
         }
         __syncthreads();
         if (eax) {
             // Eq. (4): F_a = k0 (d - L) e/d with d - L = (d^2 - L^2)/(d + L)
             const ds dd = ds_add(ds_add({own.ee[0][d].x, own.ee[0][d].y}, {own.ee[1][d].x, own.ee[1][d].y}),
                                  {own.ee[2][d].x, own.ee[2][d].y});
-            const ds st2 = ds_add(dd, ds_neg({own.L2[d].x, own.L2[d].y}));
+            const ds st2 = ds_add(dd, ds_neg({own.L2[par][d].x, own.L2[par][d].y}));
             const float rd = rsqrtf(dd.h);
-            const float f = k0f * __fdividef((st2.h + st2.l) * rd, dd.h * rd + own.L[d].x);
+            const float f = k0f * __fdividef((st2.h + st2.l) * rd, dd.h * rd + own.L[par][d].x);
             const float Fa = fmaf(f, eh, own.fext[a][d]), Fb = fmaf(-f, eh, own.fext[a + 3][d]);
             own.F[a][d] = Fa;
             own.F[a + 3][d] = Fb;

@@ -96,3 +96,17 @@ def test_effective_amplitude_matches_oracle_trajectory():
     dev = d - d.mean(axis=0)
     lam_ref = np.hypot(2 / 50 * np.sum(dev * np.sin(ph), axis=0), 2 / 50 * np.sum(dev * np.cos(ph), axis=0))
     assert np.abs(r["lam_eff"] - lam_ref).max() <= 1e-6
+
+
+def test_averaged_model_at_the_measured_amplitude_tracks_the_full_model():
+    # the stroke-averaged model with the nominal amplitude overpredicts the soft
+    # springs' motion ~10x; with each dumbbell's measured amplitude its
+    # pair-distance error drops well below the microscopic model's own change
+    s = inputs.paper_scale(128, seed=4)
+    eff = experiments.effective_amplitude(s)
+    nominal = experiments.sa_comparison(s, periods=8)
+    measured = experiments.sa_comparison(s, periods=8, lam=eff["lam_eff"])
+    assert nominal["full_rms"] == pytest.approx(measured["full_rms"], rel=1e-12)
+    assert nominal["sa_rms"] > 5 * nominal["full_rms"]
+    assert measured["rms"] < 0.25 * nominal["rms"]
+    assert measured["rms"] < 0.6 * measured["full_rms"]
