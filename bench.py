@@ -704,21 +704,27 @@ def run_ours(args):
     small = None
     if not args.no_large:
         s1 = inputs.small_fp64_oseen(0)
-        with dbs.Suspension.from_inputs(s1, precision="fp64", stream=stream, device=local) as h1:
-            h1.step(64)
-            h1.sync()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            h1.step(1000)
-            e1.record(stream)
-            e1.synchronize()
-            el1 = e0.elapsed_time(e1) / 1e3 / 1000
         N1 = 2 * s1.S
+        per_path = {}
+        for p1 in ("grid", "coop"):
+            with dbs.Suspension.from_inputs(s1, precision="fp64", stream=stream, device=local) as h1:
+                h1.set_path(p1)
+                h1.step(64)
+                h1.sync()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h1.step(1000)
+                e1.record(stream)
+                e1.synchronize()
+                per_path[p1] = e0.elapsed_time(e1) / 1e3 / 1000
+        el1 = per_path["coop"]
         small = {"workload": "S=16 (N=32), cube side 8, Oseen, all-FP64, dt=1e-3, 1000 Heun steps "
-                             "(grid path, CUDA graphs)",
+                             "(cooperative FP64 path: one launch, 16 CTAs of one dumbbell)",
                  "us_per_heun_step": el1 * 1e6, "heun_steps_per_s": 1.0 / el1,
                  "pairs_per_s": 2 * N1 * (N1 - 1) / el1,
-                 "bound": "launch latency (2 pair-sum launches per Heun step)"}
+                 "us_per_heun_step_by_path": {k: v * 1e6 for k, v in per_path.items()},
+                 "bound": "FP64 latency (each FP64 instruction holds its SM sub-partition 64 cycles) "
+                          "and the record exchange; the grid path: 2 pair-sum launches per Heun step"}
 
     ensemble = None if args.no_ensemble else ensemble_measure(dbs, inputs, torch, stream, ws=ws,
                                                               rank=rank, dev=dev)

@@ -42,7 +42,8 @@
  * spring force and the self term are double precision on the grid and
  * cluster paths; the cooperative path forms them in single precision from a
  * double-single d^2 - L^2 (the stretch d - L keeps single-precision relative
- * accuracy).  FP64 does everything in double precision.
+ * accuracy).  FP64 does everything in double precision (on the cooperative
+ * path the pair sum reads positions and G with their lowest bit cleared).
  */
 #ifndef DBS_H
 #define DBS_H
@@ -128,7 +129,8 @@ DBS_API int dbs_set_external_force(dbs_suspension *h, const double *F);
  * counter (n mod 2^32, n / 2^32, sphere index, 0) with `seed` as the key,
  * then Box-Muller: z0, z1 = sqrt(-2 ln u0) (cos, sin)(2 pi u1),
  * z2 = sqrt(-2 ln u2) cos(2 pi u3), u = (r + 1/2) 2^-32.  kT = 0 turns it
- * off (the default).  kT must be finite and >= 0, else DBS_E_ARG.  All paths.
+ * off (the default).  kT must be finite and >= 0, else DBS_E_ARG.  All paths
+ * but the FP64 cooperative one (kT > 0 there: DBS_E_STATE).
  */
 DBS_API int dbs_set_noise(dbs_suspension *h, double kT, uint64_t seed);
 
@@ -337,12 +339,19 @@ DBS_API int dbs_pair_distance_error(int64_t S, const double *A0_dev, const doubl
  *                    memory, point to point, with no grid-wide barrier.  Every
  *                    wait is bounded (about one second): a launch whose
  *                    exchange cannot complete ends with DBS_E_TIMEOUT instead
- *                    of hanging.  FP32C, S <= 4096 (every CTA holds all
- *                    records in shared memory).  dbs_set_chunks(c) on this
- *                    path (1 <= c <= 16) asks for T = the largest power of two
- *                    not above c, raised until ceil(S / T) CTAs fit the SMs
- *                    (T <= 32); 0 restores the built-in choice (the smallest T
- *                    that fits; 16 for S <= 16).
+ *                    of hanging.  FP32C: S <= 4096 (every CTA holds all
+ *                    records in shared memory), T <= 32.  FP64 (every value
+ *                    double precision; a record's doubles carry the exchange's
+ *                    parity bit in their lowest significand bit, cleared on
+ *                    use, so the pair sum sees positions and G within one unit
+ *                    in the last place of the state's): T <= 4, so S <= 4 x the
+ *                    SM count (592 on B300), and no additive noise (DBS_E_ARG
+ *                    here, DBS_E_STATE from dbs_set_noise on this path).
+ *                    dbs_set_chunks(c) on this path (1 <= c <= 16) asks for T =
+ *                    the largest power of two not above min(c, the T limit),
+ *                    raised until ceil(S / T) CTAs fit the SMs; 0 restores the
+ *                    built-in choice (the smallest T that fits; FP32C: 16 for
+ *                    S <= 16).
  */
 #define DBS_PATH_COOP 2
 DBS_API int dbs_set_path(dbs_suspension *h, int32_t path, int32_t cluster_size);

@@ -15,6 +15,7 @@
 #include "dbs_common.cuh"
 #include "eval_kernel.cuh"
 #include "flow_kernel.cuh"
+#include "flow64_kernel.cuh"
 #include "dbs_internal.cuh"
 
 using namespace dbs;
@@ -644,6 +645,8 @@ int dbs_set_noise(dbs_suspension *h, double kT, uint64_t seed)
     GUARD(h);
     if (!(kT >= 0.0) || !std::isfinite(kT)) return DBS_E_ARG;
     if (h->dyn == DBS_DYN_SHAPE && kT > 0.0) return refuse(h, DBS_E_STATE, "no noise with shape-driven dynamics");
+    if (h->path == DBS_PATH_COOP && is_f64(h) && kT > 0.0)
+        return refuse(h, DBS_E_STATE, "cooperative FP64 path: no additive noise (use the grid path)");
     CK(h, cudaStreamSynchronize(h->stream));
     drop_graph(h);
     h->noise_sigma = std::sqrt(2.0 * kT * h->p.dt / (6.0 * PI * h->p.mu * h->p.a));
@@ -680,10 +683,18 @@ int dbs_set_external_force(dbs_suspension *h, const double *F)
 // ---------------------------------------------------------------------------
 // cooperative dataflow path (flow_kernel)
 // ---------------------------------------------------------------------------
-constexpr int FLOW_THREADS = FLOW_NT;   // threads per CTA of flow_kernel
-constexpr int FLOW_MAX_T = 32;        // dumbbells per CTA at most
+constexpr int FLOW_MAX_T = 32;        // dumbbells per CTA at most (FP32C)
+constexpr int FLOW64_MAX_T = 4;       // dumbbells per CTA at most (FP64)
 constexpr int64_t FLOW_MAX_S = 4096;  // all records of a suspension in one CTA's shared memory
 constexpr int FLOW_MAX_STEPS = 1024;  // Heun steps per launch
+
+// FP32C: flow_kernel, 256 threads, 3 record words per dumbbell; FP64:
+// flow64_kernel, 128 threads, 6 record words per dumbbell
+static int flow_threads(const dbs_suspension *h) { return is_f64(h) ? FLOW64_NT : FLOW_NT; }
+static size_t flow_words(const dbs_suspension *h)
+{
+    return 2 * (size_t)h->flow_G * h->flow_T * (is_f64(h) ? 6 : 3);
+}
 
 static void drop_flow(dbs_suspension *h)
 {
@@ -705,22 +716,37 @@ static const void *flow_pick(int T)
     }
 }
 
+template <int MOB>
+static const void *flow64_pick(int T)
+{
+    switch (T) {
+    case 1: return (const void *)flow64_kernel<MOB, 1>;
+    case 2: return (const void *)flow64_kernel<MOB, 2>;
+    case 4: return (const void *)flow64_kernel<MOB, 4>;
+    default: return nullptr;
+    }
+}
+
 static const void *flow_fn(const dbs_suspension *h, int T)
 {
+    if (is_f64(h)) return h->p.mobility == DBS_OSEEN ? flow64_pick<0>(T) : flow64_pick<1>(T);
     const bool noise = h->noise_sigma > 0.0;
     if (h->p.mobility == DBS_OSEEN) return noise ? flow_pick<0, true>(T) : flow_pick<0, false>(T);
     return noise ? flow_pick<1, true>(T) : flow_pick<1, false>(T);
 }
 
-// dynamic shared memory of flow_kernel: every record of the suspension
-static size_t flow_smem(int G, int T) { return (size_t)G * T * sizeof(DbF32); }
+// dynamic shared memory of the cooperative kernel: every record of the suspension
+static size_t flow_smem(const dbs_suspension *h, int G, int T)
+{
+    return (size_t)G * T * (is_f64(h) ? sizeof(DbF64) : sizeof(DbF32));
+}
 
 static cudaLaunchConfig_t flow_config(const dbs_suspension *h, int G, int T, cudaLaunchAttribute *attr)
 {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(G);
-    cfg.blockDim = dim3(FLOW_THREADS);
-    cfg.dynamicSmemBytes = flow_smem(G, T);
+    cfg.blockDim = dim3(flow_threads(h));
+    cfg.dynamicSmemBytes = flow_smem(h, G, T);
     cfg.stream = h->stream;
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
@@ -730,26 +756,30 @@ static cudaLaunchConfig_t flow_config(const dbs_suspension *h, int G, int T, cud
 }
 
 // Split: T dumbbells per CTA, the smallest power of two (at least the largest
-// one not above a dbs_set_chunks request; 16 for S <= 16, so that one CTA holds
-// a tiny system) for which all ceil(S / T) CTAs fit the SMs, one CTA each.
+// one not above a dbs_set_chunks request; FP32C: 16 for S <= 16, so that one CTA
+// holds a tiny system; FP64 spreads even a tiny system over the SMs, whose FP64
+// pipes are the bound) for which all ceil(S / T) CTAs fit the SMs, one CTA each.
 int coop_setup(dbs_suspension *h)
 {
-    if (h->p.precision != DBS_FP32C || h->S > FLOW_MAX_S)
-        return refuse(h, DBS_E_ARG, "cooperative path needs FP32C and S <= 4096");
+    const bool f64 = is_f64(h);
+    if (h->S > FLOW_MAX_S) return refuse(h, DBS_E_ARG, "cooperative path needs S <= 4096");
+    if (f64 && h->noise_sigma > 0.0)
+        return refuse(h, DBS_E_ARG, "cooperative FP64 path: no additive noise (use the grid path)");
+    const int max_t = f64 ? FLOW64_MAX_T : FLOW_MAX_T;
     int coop = 0, sms = 0, optin = 0;
     CK(h, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device));
     CK(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
     CK(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     if (!coop) return refuse(h, DBS_E_ARG, "device without cooperative launch");
-    // tiny systems: one CTA holds all dumbbells and no record leaves it
-    int T = h->S <= 16 ? 16 : 1;
+    // tiny FP32C systems: one CTA holds all dumbbells and no record leaves it
+    int T = (!f64 && h->S <= 16) ? 16 : 1;
     if (h->flow_creq > 0) {
         T = 1;
-        while (2 * T <= std::min(h->flow_creq, FLOW_MAX_T)) T *= 2;
+        while (2 * T <= std::min(h->flow_creq, max_t)) T *= 2;
     }
     int G = 0;
     for (;; T *= 2) {
-        if (T > FLOW_MAX_T) return refuse(h, DBS_E_ARG, "cooperative path: grid does not fit the device");
+        if (T > max_t) return refuse(h, DBS_E_ARG, "cooperative path: grid does not fit the device");
         G = (int)((h->S + T - 1) / T);
         if (G > sms) continue;
         const void *k = flow_fn(h, T);
@@ -758,22 +788,22 @@ int coop_setup(dbs_suspension *h)
         // would shrink it under a larger suspension set up earlier)
         cudaFuncAttributes fa{};
         CK(h, cudaFuncGetAttributes(&fa, k));
-        if (flow_smem(G, T) + fa.sharedSizeBytes > (size_t)optin) continue;
+        if (flow_smem(h, G, T) + fa.sharedSizeBytes > (size_t)optin) continue;
         CK(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    optin - (int)fa.sharedSizeBytes));
         int occ = 0;
-        CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, FLOW_THREADS, flow_smem(G, T)));
+        CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, flow_threads(h), flow_smem(h, G, T)));
         if ((int64_t)occ * sms >= G) break;
     }
     CK(h, cudaStreamSynchronize(h->stream));
     drop_flow(h);
-    const size_t words = 2 * (size_t)G * T * 3;
+    h->flow_T = T;
+    h->flow_G = G;
+    const size_t words = flow_words(h);
     CK(h, cudaMalloc(&h->ll_rec, words * sizeof(ulonglong2)));
     // a cleared buffer carries parity bit 0 everywhere: the evaluation counter
     // starts at a multiple of 4, whose first two evaluations expect bit 1
     CK(h, cudaMemsetAsync(h->ll_rec, 0, words * sizeof(ulonglong2), h->stream));
-    h->flow_T = T;
-    h->flow_G = G;
     h->flow_base = 0;
     return DBS_OK;
 }
@@ -794,9 +824,17 @@ static int coop_step(dbs_suspension *h, int64_t n)
         P.K = K;
         P.base = h->flow_base;
         P.timeout_ns = 1000000000ull;
+        Flow64Args P64{};
+        P64.rec = P.rec;
+        P64.pack = (DbF64 *)h->packA;
+        P64.n0 = P.n0;
+        P64.G = P.G;
+        P64.K = P.K;
+        P64.base = P.base;
+        P64.timeout_ns = P.timeout_ns;
         cudaLaunchAttribute attr[1];
         const cudaLaunchConfig_t cfg = flow_config(h, h->flow_G, h->flow_T, attr);
-        void *args[] = {(void *)&A, (void *)&P};
+        void *args[] = {(void *)&A, is_f64(h) ? (void *)&P64 : (void *)&P};
         cudaError_t e = cudaLaunchKernelExC(&cfg, flow_fn(h, h->flow_T), args);
         if (e != cudaSuccess) return fail(h, DBS_E_CUDA, "cooperative launch: %s", cudaGetErrorString(e));
         // the evaluation counter runs on from launch to launch (2K evaluations per
@@ -990,8 +1028,7 @@ int dbs_test_set_flow_tag(dbs_suspension *h, uint32_t tag)
     GUARD(h);
     if (h->path != DBS_PATH_COOP || !h->ll_rec) return DBS_E_STATE;
     // a cleared buffer and a counter at a multiple of 4, as after the path's set-up
-    const size_t words = 2 * (size_t)h->flow_G * h->flow_T * 3;
-    CK(h, cudaMemsetAsync(h->ll_rec, 0, words * sizeof(ulonglong2), h->stream));
+    CK(h, cudaMemsetAsync(h->ll_rec, 0, flow_words(h) * sizeof(ulonglong2), h->stream));
     h->flow_base = tag & ~3u;
     return DBS_OK;
 }

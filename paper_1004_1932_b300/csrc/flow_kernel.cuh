@@ -271,9 +271,9 @@ __device__ __forceinline__ int lane_fold(float (&fs)[8], float (&fc)[8], int lan
     return base;
 }
 
-// Poll the compact words base[j NT] (bit j of `pending`) of word index w0 + j NT
-// until each carries the parity bit `bit`, and store its values into the tile
-// (record idx / 3, axis idx mod 3).  Two rounds of loads are kept in flight, va
+// Poll the tagged words base[j NT] (bit j of `pending`) until has(word) holds for
+// each, and hand each to store(j, word) (which writes its values into the
+// shared-memory copy of the records).  Two rounds of loads are kept in flight, va
 // and vb, the second issued `stagger` cycles after the first, so every word is
 // read twice per memory round trip: a word that becomes visible just after one
 // round passed it is seen by the other about half a round trip later.  `gap()`
@@ -281,16 +281,12 @@ __device__ __forceinline__ int lane_fold(float (&fs)[8], float (&fc)[8], int lan
 // round may still be in flight; the caller owns va and vb, so it decides whether
 // their registers stay reserved until that round has landed.  False on timeout
 // or abort.
-template <int NB, int NT, class Gap>
-__device__ __forceinline__ bool poll_words(const ulonglong2 *base, DbF32 *tile, int w0, unsigned pending,
-                                           unsigned bit, int *flags, unsigned long long timeout_ns,
-                                           int stagger, Gap &&gap, ulonglong2 (&va)[NB],
+template <int NB, int NT, class Gap, class Has, class Store>
+__device__ __forceinline__ bool poll_words(const ulonglong2 *base, unsigned pending, int *flags,
+                                           unsigned long long timeout_ns, int stagger, Gap &&gap,
+                                           Has &&has, Store &&store, ulonglong2 (&va)[NB],
                                            ulonglong2 (&vb)[NB])
 {
-    auto store = [&](int j, const ulonglong2 &v) {
-        const int idx = w0 + j * NT;
-        put_word(tile + idx / 3, idx - 3 * (idx / 3), v);
-    };
 #pragma unroll
     for (int j = 0; j < NB; ++j)
         if ((pending >> j) & 1u) va[j] = ld_tagged(base + j * NT);
@@ -306,7 +302,7 @@ __device__ __forceinline__ bool poll_words(const ulonglong2 *base, DbF32 *tile, 
             if ((pb >> j) & 1u) vb[j] = ld_tagged(base + j * NT);
 #pragma unroll
         for (int j = 0; j < NB; ++j)
-            if (((pending >> j) & 1u) && word_has(va[j], bit)) {
+            if (((pending >> j) & 1u) && has(va[j])) {
                 store(j, va[j]);
                 pending &= ~(1u << j);
             }
@@ -317,7 +313,7 @@ __device__ __forceinline__ bool poll_words(const ulonglong2 *base, DbF32 *tile, 
             if ((pa >> j) & 1u) va[j] = ld_tagged(base + j * NT);
 #pragma unroll
         for (int j = 0; j < NB; ++j)   // pending is within pb: vb[j] was loaded
-            if (((pending >> j) & 1u) && word_has(vb[j], bit)) {
+            if (((pending >> j) & 1u) && has(vb[j])) {
                 store(j, vb[j]);
                 pending &= ~(1u << j);
             }
@@ -488,6 +484,7 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
         // 1. poll the S - T records this CTA does not own, POLL words per thread
         // in two staggered rounds of loads, into shared memory
         bool ok = true;
+        auto has = [&](const ulonglong2 &v) { return word_has(v, bit); };
         for (int b0 = 0; b0 < nwords && ok; b0 += POLL * NT) {
             unsigned pend = 0;
 #pragma unroll
@@ -495,13 +492,18 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
                 const int idx = b0 + j * NT + tid;
                 if (idx < nwords && (idx < own_w0 || idx >= own_w1)) pend |= 1u << j;
             }
+            // word idx: axis idx mod 3 of record idx / 3
+            auto store = [&](int j, const ulonglong2 &v) {
+                const int idx = b0 + tid + j * NT;
+                put_word(tile + idx / 3, idx - 3 * (idx / 3), v);
+            };
             if constexpr (KEEP) {
-                ok = poll_words<POLL, NT>(R + b0 + tid, tile, b0 + tid, pend, bit, A.flags, P.timeout_ns,
-                                          DBS_FLOW_STAGGER, gap, kva, kvb);
+                ok = poll_words<POLL, NT>(R + b0 + tid, pend, A.flags, P.timeout_ns, DBS_FLOW_STAGGER, gap,
+                                          has, store, kva, kvb);
             } else {
                 ulonglong2 va[POLL], vb[POLL];
-                ok = poll_words<POLL, NT>(R + b0 + tid, tile, b0 + tid, pend, bit, A.flags, P.timeout_ns,
-                                          DBS_FLOW_STAGGER, gap, va, vb);
+                ok = poll_words<POLL, NT>(R + b0 + tid, pend, A.flags, P.timeout_ns, DBS_FLOW_STAGGER, gap,
+                                          has, store, va, vb);
             }
         }
         flush_fp64();   // done in the first gap: ends the live range of its inputs
@@ -516,7 +518,12 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
             const float2 pax = make_float2(a4.x, a4.x), pay = make_float2(a4.z, a4.z);
             const float2 paz = make_float2(b4.x, b4.x), pbx = make_float2(a4.y, a4.y);
             const float2 pby = make_float2(a4.w, a4.w), pbz = make_float2(b4.y, b4.y);
-            float r2min = 3.0e38f;
+            // overlap minimum of r^2: one chain per target sphere at T = 2 (two
+            // short dependence chains interleave better with the pair arithmetic
+            // there: S = 256 4.03 -> 3.84 us per Heun step; at T = 4 they cost
+            // 0.5 %, at T = 1 and 8 they change nothing), one chain otherwise
+            float r2min = 3.0e38f, r2mb = 3.0e38f;
+            float &r2b = T == 2 ? r2mb : r2min;
 #pragma unroll kFlowUnroll
             for (int k = sl; k < S; k += PS) {
                 const float4 ra = tile[k].a, rb = tile[k].b, rc = tile[k].c;
@@ -527,8 +534,9 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
                 pair2<MOB, true>(pax, pay, paz, jx, jy, jz, gx, gy, gz, c2, c3, qa[0], qa[1], qa[2],
                                  r2min, self, false);
                 pair2<MOB, true>(pbx, pby, pbz, jx, jy, jz, gx, gy, gz, c2, c3, qb[0], qb[1], qb[2],
-                                 r2min, false, self);
+                                 r2b, false, self);
             }
+            r2min = fminf(r2min, r2mb);
             if (MOB == 1 && r2min < A.overlap_r2) atomicOr(A.flags, FLAG_OVERLAP);
         }
 
