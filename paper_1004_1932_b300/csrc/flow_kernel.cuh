@@ -4,10 +4,12 @@
 //
 // Work split.  CTA g owns the T consecutive dumbbells [gT, gT + T) and, for
 // each evaluation, sums the pair terms of Eq. (3b) for its own 2T target
-// spheres over ALL S records: thread tid takes target t = tid / P and the
-// records r = (tid mod P) + P k (P = 256 / T slices per target), so the
-// threads of a warp read different records (consecutive 48-byte records are
-// free of shared-memory bank conflicts for 16-byte loads).  The slice sums are
+// spheres over ALL S records: each target dumbbell has P = 256 / T slices, and
+// slice p takes the records r = p + P k.  With TPW targets interleaved per warp
+// (lane mod TPW; TPW = 2 for T = 2, 4 and 16), the TPW lanes that read one record
+// share its 16-byte shared-memory load: 32 / TPW different records per load,
+// half the shared-memory wavefronts of one target per warp (consecutive 48-byte
+// records are free of bank conflicts for 16-byte loads).  The slice sums are
 // folded with FP32 two-sum, first across the lanes of a warp (shuffles), then
 // across the warps of a target in warp order, so no partial sum leaves the
 // CTA: the CTA then runs the epilogue of its dumbbells (self term of Eq. (3a),
@@ -46,6 +48,19 @@
 #endif
 #ifndef DBS_FLOW_UNROLL
 #define DBS_FLOW_UNROLL 8
+#endif
+// targets interleaved per warp (1, 2 or 4) at T = 2, 4, 8 and 16 dumbbells per CTA
+#ifndef DBS_FLOW_TPW2
+#define DBS_FLOW_TPW2 2
+#endif
+#ifndef DBS_FLOW_TPW4
+#define DBS_FLOW_TPW4 2
+#endif
+#ifndef DBS_FLOW_TPW8
+#define DBS_FLOW_TPW8 1
+#endif
+#ifndef DBS_FLOW_TPW16
+#define DBS_FLOW_TPW16 2
 #endif
 
 namespace dbs {
@@ -240,12 +255,13 @@ __device__ __noinline__ void draw_sphere_normals(unsigned long long seed, int64_
 // levels left are a butterfly on the one slot.  On return the lane carries the
 // M = max(1, 8 / LS) slots [base, base + M) in fs[0 .. M), fc[0 .. M).  ZERO_C:
 // the compensations start at zero, so the first level moves the sums only.
-template <int LS, bool ZERO_C = false>
+// STRIDE: the target's lanes are STRIDE apart (lane bits log2(STRIDE) and up).
+template <int LS, bool ZERO_C = false, int STRIDE = 1>
 __device__ __forceinline__ int lane_fold(float (&fs)[8], float (&fc)[8], int lane)
 {
     int base = 0;
 #pragma unroll
-    for (int off = LS / 2, m = 8; off >= 1; off >>= 1) {
+    for (int off = (LS / 2) * STRIDE, m = 8; off >= STRIDE; off >>= 1) {
         if (m > 1) {
             const int h = m / 2;
             const bool hi = (lane & off) != 0;
@@ -335,8 +351,18 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
 {
     constexpr int NT = FLOW_NT;
     constexpr int PS = NT / T;                 // slices (threads) per target dumbbell
-    constexpr int LW = PS < 32 ? PS : 32;      // lanes of one target within a warp
-    constexpr int WPT = PS > 32 ? PS / 32 : 1; // warps per target
+    // TPW > 1: TPW targets interleaved in each warp (lane mod TPW), so that the
+    // lanes reading one record share its shared-memory load (a 16-byte load of 32
+    // different records takes 4 shared-memory wavefronts, of 16 records 2)
+    constexpr int TPW = T == 2    ? DBS_FLOW_TPW2
+                        : T == 4  ? DBS_FLOW_TPW4
+                        : T == 8  ? DBS_FLOW_TPW8
+                        : T == 16 ? DBS_FLOW_TPW16
+                                  : 1;
+    // lanes of one target within a warp, and warps per target
+    constexpr int LW = TPW == 1 ? (PS < 32 ? PS : 32) : 32 / TPW;
+    constexpr int WPT = TPW == 1 ? (PS > 32 ? PS / 32 : 1) : PS / LW;
+    static_assert(TPW == 1 || PS >= LW, "interleaved targets need LW slices per target");
     // words per thread and round: up to 6 words (S <= 512 in one round) the poll's
     // registers stay reserved across the evaluation, so that the round still in
     // flight when the last word arrives is never waited for; above that (larger
@@ -347,7 +373,7 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
     static_assert(LW >= 8, "the transposing fold needs 8 lanes per target");
     extern __shared__ float4 flow_smem[];     // all S records (Spad x DbF32)
     __shared__ FlowOwner<T> own;
-    __shared__ float2 red[WPT == 1 ? T : NT / 32][6];   // folded sums per (target, warp)
+    __shared__ float2 red[WPT == 1 ? T : T * WPT][6];   // folded sums per (target, warp of it)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = blockIdx.x;
@@ -401,7 +427,9 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
     const float2 c2 = make_float2(A.c2, A.c2), c3 = make_float2(A.c3, A.c3);
     const int nwords = 3 * S;
     const int own_w0 = 3 * st0, own_w1 = 3 * (st0 + nown);   // words not polled (own records)
-    const int t_me = tid / PS, sl = tid - t_me * PS;         // sweep: target and slice
+    // sweep: target and slice (TPW = 1: consecutive threads; else interleaved)
+    const int t_me = TPW == 1 ? tid / PS : (warp / WPT) * TPW + lane % TPW;
+    const int sl = TPW == 1 ? tid - t_me * PS : (warp % WPT) * (32 / TPW) + lane / TPW;
     const int s_me = st0 + t_me;
     const bool act = t_me < nown;
     ulonglong2 kva[KEEP ? POLL : 1], kvb[KEEP ? POLL : 1];   // the kept poll registers
@@ -556,8 +584,9 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
             fs[6] = fs[7] = 0.f;
 #pragma unroll
             for (int k = 0; k < 8; ++k) fc[k] = 0.f;
-            const int sb = lane_fold<LW, true>(fs, fc, lane);
-            if ((lane & (LW / 8 - 1)) == 0 && sb < 6) red[WPT == 1 ? t_me : warp][sb] = make_float2(fs[0], fc[0]);
+            const int sb = lane_fold<LW, true, TPW>(fs, fc, lane);
+            if (((lane / TPW) & (LW / 8 - 1)) == 0 && sb < 6)
+                red[WPT == 1 ? t_me : t_me * WPT + warp % WPT][sb] = make_float2(fs[0], fc[0]);
         }
         __syncthreads();
 
