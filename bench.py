@@ -489,6 +489,9 @@ def run_ours(args):
         h.set_path(path_choice["path"])
         sa = dbs.StrokeAveraged(s.R0, s.N0, s.phi, s.lam, a=s.a, ell=s.ell, omega=s.omega,
                                 dt=dt_sa, precision="fp32c", stream=sa_stream, device=local)
+        # overlapped with the microscopic model on the SMs it leaves free: one launch
+        # per evaluation (a cooperative launch needs all its CTAs resident at once)
+        sa.set_path("grid")
         h.enable_period_average(m, max_periods=total_periods)
         return h, sa
 
@@ -631,24 +634,34 @@ def run_ours(args):
     # ---- the stroke-averaged kernel on its own (CUDA events on its stream) --------
     sa_kernel = None
     if not args.no_large:
-        sa_kernel = {"kernel": "sa_eval_kernel (stroke-averaged pair sums + FP64 Heun epilogue, "
-                               "2 launches per averaged step)",
+        sa_kernel = {"kernel": "stroke-averaged pair sums with the Heun update: sa_flow_kernel "
+                               "(cooperative, one launch per 1024 averaged steps; FP32C, S <= 4096) "
+                               "or sa_eval_kernel (2 launches per averaged step)",
                      "flops_per_pair": SA_FLOPS_PER_PAIR, "peak": peak, "unit": "TFLOP/s", "sizes": []}
-        for Ss, reps in ((S, 200), (8192, 20)):
-            ss = inputs.paper_scale(Ss, seed=rank, mobility=args.mobility)
+
+        def sa_time(ss, reps, path):
             sst = torch.cuda.Stream(device=dev)
             with dbs.StrokeAveraged(ss.R0, ss.N0, ss.phi, ss.lam, a=ss.a, ell=ss.ell, omega=ss.omega,
                                     dt=0.1, precision="fp32c", stream=sst) as sk:
+                if path:
+                    sk.set_path(path)
+                used = sk.get_path()[0]
                 sk.step(4)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(sst)
                 sk.step(reps)
                 e1.record(sst)
                 e1.synchronize()
-            el = e0.elapsed_time(e1) / 1e3 / reps
+            return e0.elapsed_time(e1) / 1e3 / reps, used
+
+        for Ss, reps in ((S, 1000), (8192, 20)):
+            ss = inputs.paper_scale(Ss, seed=rank, mobility=args.mobility)
+            el, used = sa_time(ss, reps, None)
             ach = 2 * Ss * (Ss - 1) * SA_FLOPS_PER_PAIR / el / 1e12
-            sa_kernel["sizes"].append({"S": Ss, "us_per_step": el * 1e6, "achieved": ach,
-                                       "frac": ach / peak})
+            row = {"S": Ss, "path": used, "us_per_step": el * 1e6, "achieved": ach, "frac": ach / peak}
+            if used == "coop":
+                row["grid_path_us_per_step"] = sa_time(ss, 200, "grid")[0] * 1e6
+            sa_kernel["sizes"].append(row)
 
     e2e = None
     if not args.no_e2e:

@@ -283,8 +283,34 @@ DBS_API int dbs_sa_step(dbs_sa *h, int64_t n);
 /* Rates (dR/dt, dN/dt) at the current state into Rdot, Ndot [S][3] (host). */
 DBS_API int dbs_sa_rates(dbs_sa *h, double *Rdot, double *Ndot);
 
-/* Current state R, N [S][3] (host).  Synchronising. */
+/* Current state R, N [S][3] (host).  Synchronising; reports DBS_E_TIMEOUT /
+ * DBS_E_CUDA raised by the cooperative path (sticky). */
 DBS_API int dbs_sa_state(dbs_sa *h, double *R, double *N);
+
+/*
+ * Execution path of dbs_sa_step (Sec. III.B's Heun step either way):
+ *  DBS_PATH_GRID  one launch per evaluation of Eqs. (9a)-(9e) (any size and
+ *                 precision).
+ *  DBS_PATH_COOP  one cooperative launch of up to one CTA per SM advances up to
+ *                 1024 averaged steps; each CTA owns T dumbbells (T the
+ *                 smallest power of two <= 32 for which ceil(S / T) CTAs fit the
+ *                 SMs), holds every record in shared memory and sums its
+ *                 targets over all of them; CTAs exchange only (R, N), one
+ *                 64-bit word per dumbbell and axis with a parity bit in the
+ *                 lowest significand bit of N's component (cleared on use),
+ *                 point to point, with no grid-wide barrier.  The next record is
+ *                 formed in FP32 from double-single copies of the state, the FP64
+ *                 state update (N renormalised) off the critical path from the
+ *                 same pair sums.  Every wait is bounded (about one second): a
+ *                 launch whose exchange cannot complete ends with DBS_E_TIMEOUT
+ *                 (reported by dbs_sa_state / dbs_sa_rates).  FP32C and
+ *                 S <= 4096 only (DBS_E_ARG otherwise, the handle stays usable);
+ *                 the default wherever it applies.
+ * Results of the two paths differ only in the rounding of the pair sums.
+ */
+DBS_API int dbs_sa_set_path(dbs_sa *h, int32_t path);
+/* The path in use and, on DBS_PATH_COOP, the dumbbells per CTA (else 0). */
+DBS_API int dbs_sa_get_path(dbs_sa *h, int32_t *path, int32_t *targets_per_cta);
 
 /* Device pointer of the current centres R ([S][3] doubles). */
 DBS_API int dbs_sa_centres_device(dbs_sa *h, const double **R_dev);

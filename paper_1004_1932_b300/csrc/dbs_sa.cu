@@ -462,6 +462,378 @@ __global__ void sa_pack_kernel(SaArgs A)
     store_rec((Rec *)A.rec_out, s, R, N, A);
 }
 
+// ---- cooperative form of the averaged model (FP32C, S <= 4096) ---------------
+// One cooperative launch of G <= SMs CTAs advances K averaged Heun steps.  CTA
+// g owns the TL dumbbells [g TL, g TL + TL) and keeps every record of the
+// suspension in shared memory; amplitude and phase do not change, so they are
+// loaded once per launch, and per evaluation only (R, N) travel: one 64-bit
+// word per dumbbell and axis a, (R_a - c_a) in its low half and N_a in its high
+// half, whose lowest bit carries the evaluation's parity bit (bit 1 of the
+// evaluation counter, inverted), so a reader that sees the expected bit has
+// that evaluation's pair of values: no fence, flag or barrier.  Buffers
+// alternate by evaluation parity; a slot is rewritten (evaluation e + 2) only
+// after its owner has finished e + 1, which needed every CTA's words of e + 1,
+// which each CTA publishes only after it has copied all words of e into shared
+// memory.  Every wait is bounded (1 s of %globaltimer, and at once when another
+// CTA has raised SAF_TIMEOUT).
+//
+// Precision.  The pair sums are FP32 with two-sum compensation, as in
+// sa_eval_kernel, and so are the rates formed from them (their accuracy is the
+// pair terms' FP32 accuracy either way).  Within a launch the state (R - c and
+// N) is carried as double-single pairs hi + lo (48-bit significands; FP64
+// instructions, each of which holds its sub-partition's FP64 pipe 64 cycles on
+// this part, would set the pace of the step): the Heun step of Sec. III.B
+// advances them, and N is renormalised with an FP32 reciprocal square root and
+// one Newton step in double-single (|N| = 1 to about 1e-14).  The state is read
+// from and written back to the FP64 arrays once per launch, N renormalised in
+// FP64 there.  The critical path forms each next record from those pairs in
+// FP32 (the corrector's N normalised in FP32 for its record); the
+// double-single update runs in the next poll's gap.
+constexpr int SAF_TIMEOUT = 4, SAF_LAUNCH = 8;
+constexpr int SAC_CHUNK = 512;     // records per compensated partial sum (as sa_eval_kernel's tile)
+constexpr int SAC_POLL = 8;        // words per thread and round of a poll
+
+struct SaFlowArgs {
+    unsigned long long *words;     // [2][Spad][3]
+    int *flags;
+    int G, K;                      // CTAs, averaged Heun steps
+    unsigned base;                 // evaluation counter at evaluation 0 of the launch (even)
+    unsigned long long timeout_ns;
+};
+
+template <int TL>
+struct SaOwn {
+    float Rh[3][TL], Rl[3][TL];    // R - c as double-single
+    float Nh[3][TL], Nl[3][TL];    // N as double-single
+    float r0f[3][TL], n0f[3][TL];  // predictor rates (J, projected K)
+};
+
+__device__ __forceinline__ unsigned long long sac_ld(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void sac_st(unsigned long long *p, float R, float N, unsigned bit)
+{
+    const unsigned long long v =
+        (unsigned long long)((__float_as_uint(N) & ~1u) | bit) << 32 | __float_as_uint(R);
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long sac_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned sac_bit(unsigned e) { return ((e >> 1) & 1u) ^ 1u; }
+__device__ __forceinline__ float sac_nclear(float n) { return __uint_as_float(__float_as_uint(n) & ~1u); }
+// FP32 of (hi + (lo + d)) for a small increment d
+__device__ __forceinline__ float sac_add(float h, float l, float d) { return h + (l + d); }
+
+// double-single (hi, lo), |lo| <= ulp(hi) / 2: Knuth's two-sum and the FMA
+// two-product (Dekker)
+struct sads { float h, l; };
+__device__ __forceinline__ sads sads_fast(float a, float b)   // |a| >= |b|
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ sads sads_add(sads a, sads b)
+{
+    const float s = a.h + b.h;
+    const float bb = s - a.h;
+    const float e = (a.h - (s - bb)) + (b.h - bb) + a.l + b.l;
+    return sads_fast(s, e);
+}
+__device__ __forceinline__ sads sads_mul(sads a, sads b)
+{
+    const float p = a.h * b.h;
+    const float e = fmaf(a.h, b.h, -p) + fmaf(a.h, b.l, a.l * b.h);
+    return sads_fast(p, e);
+}
+__device__ __forceinline__ void sads_split(double x, float &h, float &l)
+{
+    h = (float)x;
+    l = (float)(x - (double)h);
+}
+
+template <int TL>
+__global__ void __launch_bounds__(SA_NT, 1) sa_flow_kernel(const SaArgs A, const SaFlowArgs P)
+{
+    constexpr int NSL = SA_NT / TL;
+    constexpr int LW = NSL < 32 ? NSL : 32;
+    constexpr int WPT = NSL > 32 ? NSL / 32 : 1;
+    extern __shared__ float4 sac_smem[];          // all records, SaRecF32
+    __shared__ SaOwn<TL> own;
+    __shared__ float red[WPT == 1 ? TL : SA_NT / 32][12];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = blockIdx.x;
+    const int S = (int)A.S;
+    const int Spad = P.G * TL;
+    const int st0 = g * TL, nown = min(TL, S - st0);
+    SaRecF32 *tile = (SaRecF32 *)sac_smem;
+    if (gridDim.x != (unsigned)P.G || blockDim.x != (unsigned)SA_NT) {
+        if (tid == 0) atomicOr(P.flags, SAF_LAUNCH);
+        return;
+    }
+    const float CJf = (float)A.CJ, CKf = (float)A.CK, dtf = (float)A.dt, hdtf = (float)(0.5 * A.dt);
+    const double cen_a = warp == 0 ? A.cx : (warp == 1 ? A.cy : A.cz);   // axis warps
+
+    // ---- static record fields of every dumbbell; the owned state; evaluation 0
+    for (int s = tid; s < S; s += SA_NT) {
+        tile[s].R.w = (float)A.lam[s];
+        tile[s].N.w = 0.f;
+        tile[s].sc = make_float4((float)A.sinp[s], (float)A.cosp[s], 0.f, 0.f);
+    }
+    if (warp < 3 && lane < nown) {
+        const int a = warp, d = lane, s = st0 + d;
+        const double R = A.R[3 * (int64_t)s + a] - cen_a, N = A.N[3 * (int64_t)s + a];
+        sads_split(R, own.Rh[a][d], own.Rl[a][d]);
+        sads_split(N, own.Nh[a][d], own.Nl[a][d]);
+        const float Rf = (float)R, Nf = sac_nclear((float)N);
+        ((float *)&tile[s].R)[a] = Rf;
+        ((float *)&tile[s].N)[a] = Nf;
+        sac_st(P.words + (size_t)s * 3 + a, Rf, Nf, sac_bit(P.base));
+    }
+    __syncthreads();
+
+    const int t = tid / NSL, sl = tid - t * NSL;
+    const int st = st0 + t;
+    const bool act = t < nown;
+    const int nwords = 3 * S, own_w0 = 3 * st0, own_w1 = 3 * (st0 + nown);
+    const bool ax = warp < 3 && lane < nown;      // epilogue lane: axis warp, dumbbell lane
+    // The corrector's increments dt/2 (rate0 + rate) of R along this warp's axis
+    // and of all three components of N; the next poll's gap adds them to the
+    // double-single state and renormalises N.  `pend` is the same in all lanes of
+    // an axis warp (the update meets the other axis warps at a barrier).
+    float incR = 0.f, incN[3] = {0.f, 0.f, 0.f};
+    bool pend = false;
+    auto state_update = [&]() {
+        if (warp >= 3 || !pend) return;
+        const int a = warp, d = lane;
+        const bool on = d < nown;
+        sads N1[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        if (on) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) N1[k] = sads_add({own.Nh[k][d], own.Nl[k][d]}, {incN[k], 0.f});
+            const sads R1 = sads_add({own.Rh[a][d], own.Rl[a][d]}, {incR, 0.f});
+            own.Rh[a][d] = R1.h;
+            own.Rl[a][d] = R1.l;
+        }
+        // every axis warp has read the components of N that the others rewrite
+        // below (whole warps, converged, meet at the barrier)
+        __syncwarp();
+        asm volatile("bar.sync 1, 96;" ::: "memory");
+        if (on) {
+            const sads q = sads_add(sads_add(sads_mul(N1[0], N1[0]), sads_mul(N1[1], N1[1])), sads_mul(N1[2], N1[2]));
+            // y = 1/sqrt(q): FP32 seed, one Newton step y + y (1 - q y^2) / 2
+            const float y0 = rsqrtf(q.h);
+            const sads qy2 = sads_mul(q, sads_mul({y0, 0.f}, {y0, 0.f}));
+            const float e = (1.f - qy2.h) - qy2.l;
+            const sads y = sads_fast(y0, 0.5f * y0 * e);
+            const sads Na = sads_mul(a == 0 ? N1[0] : (a == 1 ? N1[1] : N1[2]), y);
+            own.Nh[a][d] = Na.h;
+            own.Nl[a][d] = Na.l;
+        }
+        pend = false;
+    };
+
+    bool dead = false;
+    for (int ev = 0; ev < 2 * P.K && !dead; ++ev) {
+        const unsigned bit = sac_bit(P.base + (unsigned)ev);
+        const bool corr = (ev & 1) != 0;
+        const unsigned long long *W = P.words + (size_t)(ev & 1) * Spad * 3;
+        // 1. poll the words of the records this CTA does not own, two staggered
+        // rounds of SAC_POLL loads per thread, into shared memory
+        bool ok = true;
+        for (int b0 = 0; b0 < nwords && ok; b0 += SAC_POLL * SA_NT) {
+            unsigned pending = 0;
+#pragma unroll
+            for (int j = 0; j < SAC_POLL; ++j) {
+                const int idx = b0 + j * SA_NT + tid;
+                if (idx < nwords && (idx < own_w0 || idx >= own_w1)) pending |= 1u << j;
+            }
+            auto has = [&](unsigned long long v) { return ((unsigned)(v >> 32) & 1u) == bit; };
+            auto store = [&](int j, unsigned long long v) {
+                const int idx = b0 + j * SA_NT + tid, s = idx / 3, a = idx - 3 * s;
+                ((float *)&tile[s].R)[a] = __uint_as_float((unsigned)v);
+                ((float *)&tile[s].N)[a] = __uint_as_float((unsigned)(v >> 32) & ~1u);
+            };
+            unsigned long long va[SAC_POLL], vb[SAC_POLL];
+            const unsigned long long *base = W + b0 + tid;
+#pragma unroll
+            for (int j = 0; j < SAC_POLL; ++j)
+                if ((pending >> j) & 1u) va[j] = sac_ld(base + j * SA_NT);
+            {
+                const long long c0 = clock64();
+                state_update();
+                while (clock64() - c0 < 300) {
+                }
+            }
+            unsigned long long t0 = 0;
+            for (unsigned it = 0; pending; ++it) {
+                const unsigned pb = pending;
+#pragma unroll
+                for (int j = 0; j < SAC_POLL; ++j)
+                    if ((pb >> j) & 1u) vb[j] = sac_ld(base + j * SA_NT);
+#pragma unroll
+                for (int j = 0; j < SAC_POLL; ++j)
+                    if (((pending >> j) & 1u) && has(va[j])) {
+                        store(j, va[j]);
+                        pending &= ~(1u << j);
+                    }
+                if (!pending) break;
+                const unsigned pa = pending;
+#pragma unroll
+                for (int j = 0; j < SAC_POLL; ++j)
+                    if ((pa >> j) & 1u) va[j] = sac_ld(base + j * SA_NT);
+#pragma unroll
+                for (int j = 0; j < SAC_POLL; ++j)   // pending is within pb: vb[j] was loaded
+                    if (((pending >> j) & 1u) && has(vb[j])) {
+                        store(j, vb[j]);
+                        pending &= ~(1u << j);
+                    }
+                if (!pending) break;
+                if (it == 0) t0 = sac_ns();
+                if ((it & 7u) == 7u) {
+                    if (*(volatile int *)P.flags & SAF_TIMEOUT) { ok = false; break; }
+                    if (sac_ns() - t0 > P.timeout_ns) {
+                        atomicOr(P.flags, SAF_TIMEOUT);
+                        ok = false;
+                        break;
+                    }
+                }
+            }
+        }
+        state_update();   // done in the first gap: ends the live range of its inputs
+        dead = __syncthreads_or(!ok);
+        if (dead) break;
+
+        // 2. sweep: target t against records sl, sl + NSL, ... in compensated chunks
+        float fs[8] = {0, 0, 0, 0, 0, 0, 0, 0}, fc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (act) {
+            const SaRecF32 me = tile[st];
+            const float Rx = me.R.x, Ry = me.R.y, Rz = me.R.z, lam = me.R.w;
+            const float Nx = me.N.x, Ny = me.N.y, Nz = me.N.z, sn = me.sc.x, cs = me.sc.y;
+            for (int t0 = 0; t0 < S; t0 += SAC_CHUNK) {
+                const int len = min(SAC_CHUNK, S - t0);
+                const SaRecF32 *ch = tile + t0;
+                float J[3] = {0, 0, 0}, K[3] = {0, 0, 0};
+                int k = sl;
+                if constexpr (TL >= 4) {
+                    float2 J2[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+                    float2 K2[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+                    for (; k + NSL < len; k += 2 * NSL)
+                        sa_pair2(t0 + k == st, t0 + k + NSL == st, f2s(Rx), f2s(Ry), f2s(Rz), f2s(lam), f2s(Nx),
+                                 f2s(Ny), f2s(Nz), f2s(sn), f2s(cs), ch[k], ch[k + NSL], J2, K2);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        sa_merge(fs[c], fc[c], J2[c].x, 0.f);
+                        sa_merge(fs[c], fc[c], J2[c].y, 0.f);
+                        sa_merge(fs[3 + c], fc[3 + c], K2[c].x, 0.f);
+                        sa_merge(fs[3 + c], fc[3 + c], K2[c].y, 0.f);
+                    }
+                }
+                for (; k < len; k += NSL)
+                    sa_pair<float, SaRecF32>(t0 + k == st, Rx, Ry, Rz, lam, Nx, Ny, Nz, sn, cs, ch[k], J, K);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    sa_merge(fs[c], fc[c], J[c], 0.f);
+                    sa_merge(fs[3 + c], fc[3 + c], K[c], 0.f);
+                }
+            }
+        }
+        // 3. fold: lanes by transposition, then the target's warps in warp order
+        {
+            int ci;
+            sa_fold_lanes<float, LW>(fs, fc, lane, ci);
+            if ((lane & (LW / 8 - 1)) == 0 && ci < 6) {
+                const int row = WPT == 1 ? t : warp;
+                const int col = ci < 3 ? ci : 3 + ci;
+                red[row][col] = fs[0];
+                red[row][col + 3] = fc[0];
+            }
+        }
+        __syncthreads();
+
+        // 4. epilogue: lane d of axis warp a forms its record component of the next
+        // evaluation point from the double-single state and publishes it
+        if (warp < 3) {
+            const int a = warp, d = lane, s = st0 + d;
+            float Rn = 0.f, Nn = 0.f;
+            if (ax) {
+                const int r0w = d * WPT;
+                float js = red[r0w][a], jc = red[r0w][3 + a], ks[3], kc[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    ks[k] = red[r0w][6 + k];
+                    kc[k] = red[r0w][9 + k];
+                }
+                for (int w = 1; w < WPT; ++w) {
+                    sa_merge(js, jc, red[r0w + w][a], red[r0w + w][3 + a]);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) sa_merge(ks[k], kc[k], red[r0w + w][6 + k], red[r0w + w][9 + k]);
+                }
+                const float Jf = CJf * (js + jc);
+                float Kf[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) Kf[k] = CKf * (ks[k] + kc[k]);
+                const float Kfa = a == 0 ? Kf[0] : (a == 1 ? Kf[1] : Kf[2]);
+                if (!corr) {   // x~ = x_n + dt (J, -(I - N N^T) K) at (R_n, N_n)
+                    const float NK = fmaf(own.Nh[0][d], Kf[0], fmaf(own.Nh[1][d], Kf[1], own.Nh[2][d] * Kf[2]));
+                    const float rK = -(Kfa - own.Nh[a][d] * NK);
+                    own.r0f[a][d] = Jf;
+                    own.n0f[a][d] = rK;
+                    Rn = sac_add(own.Rh[a][d], own.Rl[a][d], dtf * Jf);
+                    Nn = sac_add(own.Nh[a][d], own.Nl[a][d], dtf * rK);
+                } else {       // x_{n+1} = x_n + dt/2 (rate0 + rate(x~)), N renormalised
+                    const float4 mN = tile[s].N;   // the predicted point's orientation
+                    const float Nb[3] = {mN.x, mN.y, mN.z};
+                    const float NK = fmaf(Nb[0], Kf[0], fmaf(Nb[1], Kf[1], Nb[2] * Kf[2]));
+                    float N1[3];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        incN[k] = hdtf * (own.n0f[k][d] - (Kf[k] - Nb[k] * NK));
+                        N1[k] = sac_add(own.Nh[k][d], own.Nl[k][d], incN[k]);
+                    }
+                    const float inv = rsqrtf(fmaf(N1[0], N1[0], fmaf(N1[1], N1[1], N1[2] * N1[2])));
+                    incR = hdtf * (own.r0f[a][d] + Jf);
+                    Rn = sac_add(own.Rh[a][d], own.Rl[a][d], incR);
+                    Nn = (a == 0 ? N1[0] : (a == 1 ? N1[1] : N1[2])) * inv;
+                }
+                Nn = sac_nclear(Nn);
+            }
+            if (corr) {   // all three axis warps have read the predicted record before it changes
+                pend = true;
+                __syncwarp();
+                asm volatile("bar.sync 2, 96;" ::: "memory");
+            }
+            if (ax) {
+                ((float *)&tile[s].R)[a] = Rn;
+                ((float *)&tile[s].N)[a] = Nn;
+                if (ev + 1 < 2 * P.K)
+                    sac_st(P.words + ((size_t)((ev + 1) & 1) * Spad + s) * 3 + a, Rn, Nn,
+                           sac_bit(P.base + (unsigned)ev + 1u));
+            }
+        }
+        // no barrier here: the next poll writes only records this CTA does not own,
+        // and the next sweep reads the own records after the poll's barrier
+    }
+    state_update();
+    __syncthreads();
+    // the FP64 state: R - c and N from their double-single pairs, N renormalised
+    if (warp < 3 && lane < nown) {
+        const int a = warp, d = lane, s = st0 + d;
+        double N[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) N[k] = (double)own.Nh[k][d] + (double)own.Nl[k][d];
+        const double inv = sa_inv_norm(fma(N[0], N[0], fma(N[1], N[1], N[2] * N[2])));
+        A.R[3 * (int64_t)s + a] = cen_a + ((double)own.Rh[a][d] + (double)own.Rl[a][d]);
+        A.N[3 * (int64_t)s + a] = (a == 0 ? N[0] : (a == 1 ? N[1] : N[2])) * inv;
+    }
+}
+
 // ---- pair-distance comparison (FP64) ----------------------------------------
 // The upper triangle of pairs (s < r) is cut into 32 x 32 tiles; CTAs take
 // tiles in a grid-stride loop, reduce their pairs in a fixed tree order into a
@@ -593,6 +965,13 @@ struct dbs_sa {
     void *recA = nullptr, *recB = nullptr;
     double cx = 0, cy = 0, cz = 0;
     int sms = 0;   // SMs of the device
+    // cooperative path (sa_flow_kernel): split, exchange words, evaluation counter
+    int path = DBS_PATH_GRID;
+    int coop_T = 0, coop_G = 0;
+    unsigned coop_base = 0;
+    unsigned long long *words = nullptr;
+    int *flags = nullptr;       // SAF_* raised by the cooperative kernel
+    bool recs_stale = false;    // recA behind the state after cooperative steps
 };
 
 static int sa_fail(dbs_sa *h, int st, const char *fmt, ...)
@@ -623,6 +1002,13 @@ static int sa_fail(dbs_sa *h, int st, const char *fmt, ...)
     } while (0)
 
 static bool sa_f64(const dbs_sa *h) { return h->p.precision == DBS_FP64; }
+
+// a refusal that leaves the handle usable (no sticky status)
+static int sa_refuse(dbs_sa *h, int st, const char *msg)
+{
+    snprintf(h->msg, sizeof(h->msg), "%s", msg);
+    return st;
+}
 
 static SaArgs sa_args(const dbs_sa *h)
 {
@@ -702,8 +1088,112 @@ static int sa_repack(dbs_sa *h)
     return DBS_OK;
 }
 
+// ---- cooperative path ---------------------------------------------------------
+constexpr int64_t SAC_MAX_S = 4096;   // every CTA holds all records in shared memory
+constexpr int SAC_MAX_T = 32;
+constexpr int SAC_MAX_STEPS = 1024;   // averaged Heun steps per launch
+
+static const void *sa_flow_fn(int T)
+{
+    switch (T) {
+    case 1: return (const void *)sa_flow_kernel<1>;
+    case 2: return (const void *)sa_flow_kernel<2>;
+    case 4: return (const void *)sa_flow_kernel<4>;
+    case 8: return (const void *)sa_flow_kernel<8>;
+    case 16: return (const void *)sa_flow_kernel<16>;
+    case 32: return (const void *)sa_flow_kernel<32>;
+    default: return nullptr;
+    }
+}
+
+// Split: T dumbbells per CTA, the smallest power of two for which ceil(S / T)
+// CTAs fit the SMs one each with all records in shared memory.
+static int sa_coop_setup(dbs_sa *h)
+{
+    if (sa_f64(h)) return sa_refuse(h, DBS_E_ARG, "cooperative averaged model: FP32C only");
+    if (h->p.S > SAC_MAX_S) return sa_refuse(h, DBS_E_ARG, "cooperative averaged model needs S <= 4096");
+    int coop = 0, optin = 0;
+    SCK(h, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device));
+    SCK(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    if (!coop) return sa_refuse(h, DBS_E_ARG, "device without cooperative launch");
+    int T = 1, G = 0;
+    for (;; T *= 2) {
+        if (T > SAC_MAX_T) return sa_refuse(h, DBS_E_ARG, "cooperative averaged model: grid does not fit the device");
+        G = (int)((h->p.S + T - 1) / T);
+        if (G > h->sms) continue;
+        const void *k = sa_flow_fn(T);
+        cudaFuncAttributes fa{};
+        SCK(h, cudaFuncGetAttributes(&fa, k));
+        const size_t smem = (size_t)G * T * sizeof(SaRecF32);
+        if (smem + fa.sharedSizeBytes > (size_t)optin) continue;
+        // a property of the kernel, shared by every handle: all the device allows
+        SCK(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes));
+        int occ = 0;
+        SCK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, SA_NT, smem));
+        if ((int64_t)occ * h->sms >= G) break;
+    }
+    SCK(h, cudaStreamSynchronize(h->stream));
+    if (h->words) cudaFree(h->words);
+    h->words = nullptr;
+    const size_t nw = 2 * (size_t)G * T * 3;
+    SCK(h, cudaMalloc(&h->words, nw * sizeof(unsigned long long)));
+    // a cleared buffer carries parity bit 0: the counter starts at a multiple of 4,
+    // whose first two evaluations expect bit 1
+    SCK(h, cudaMemsetAsync(h->words, 0, nw * sizeof(unsigned long long), h->stream));
+    h->coop_T = T;
+    h->coop_G = G;
+    h->coop_base = 0;
+    h->path = DBS_PATH_COOP;
+    return DBS_OK;
+}
+
+static int sa_coop_step(dbs_sa *h, int64_t n)
+{
+    for (int64_t left = n; left > 0;) {
+        const int K = (int)std::min<int64_t>(left, SAC_MAX_STEPS);
+        const SaArgs A = sa_args(h);
+        SaFlowArgs P{};
+        P.words = h->words;
+        P.flags = h->flags;
+        P.G = h->coop_G;
+        P.K = K;
+        P.base = h->coop_base;
+        P.timeout_ns = 1000000000ull;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(h->coop_G);
+        cfg.blockDim = dim3(SA_NT);
+        cfg.dynamicSmemBytes = (size_t)h->coop_G * h->coop_T * sizeof(SaRecF32);
+        cfg.stream = h->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        void *args[] = {(void *)&A, (void *)&P};
+        SCK(h, cudaLaunchKernelExC(&cfg, sa_flow_fn(h->coop_T), args));
+        // 2K evaluations per launch: the counter stays even and keeps its residue mod 4
+        h->coop_base += (unsigned)(2 * K);
+        left -= K;
+    }
+    h->recs_stale = true;
+    return DBS_OK;
+}
+
+// after a synchronisation: a fault the cooperative kernel raised becomes the
+// handle's sticky status
+static int sa_check_flags(dbs_sa *h)
+{
+    int f = 0;
+    SCK(h, cudaMemcpy(&f, h->flags, sizeof(int), cudaMemcpyDeviceToHost));
+    if (f & SAF_TIMEOUT) return sa_fail(h, DBS_E_TIMEOUT, "cooperative averaged model: a bounded wait ran out");
+    if (f & SAF_LAUNCH) return sa_fail(h, DBS_E_CUDA, "kernel launched in a grid or cluster shape it cannot run");
+    return DBS_OK;
+}
+
 static void sa_free(dbs_sa *h)
 {
+    if (h->words) cudaFree(h->words);
+    if (h->flags) cudaFree(h->flags);
     void *b[] = {h->R, h->N, h->rate0, h->rate_out, h->lam, h->sinp, h->cosp, h->recA, h->recB};
     for (void *p : b)
         if (p) cudaFree(p);
@@ -772,6 +1262,8 @@ int dbs_sa_create(const dbs_sa_params *p, const double *R, const double *N, cons
     const size_t rb = (size_t)S * (sa_f64(h) ? sizeof(SaRecF64) : sizeof(SaRecF32));
     SCREATE(cudaMalloc(&h->recA, rb));
     SCREATE(cudaMalloc(&h->recB, rb));
+    SCREATE(cudaMalloc(&h->flags, sizeof(int)));
+    SCREATE(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
     std::vector<double> sn(S), cs(S);
     for (int64_t s = 0; s < S; ++s) {
         sn[s] = std::sin(phi[s]);
@@ -792,6 +1284,12 @@ int dbs_sa_create(const dbs_sa_params *p, const double *R, const double *N, cons
     SCREATE(cudaMemcpyAsync(h->sinp, sn.data(), sizeof(double) * S, cudaMemcpyHostToDevice, h->stream));
     SCREATE(cudaMemcpyAsync(h->cosp, cs.data(), sizeof(double) * S, cudaMemcpyHostToDevice, h->stream));
     if ((rc = sa_repack(h)) != DBS_OK) return bail(rc);
+    // FP32C systems that fit take the cooperative path; the others (and a device
+    // that cannot hold it) keep one launch per evaluation
+    if (!sa_f64(h) && S <= SAC_MAX_S) {
+        if ((rc = sa_coop_setup(h)) == DBS_E_NOMEM || rc == DBS_E_CUDA) return bail(rc);
+        h->msg[0] = '\0';
+    }
     SCREATE(cudaStreamSynchronize(h->stream));
 #undef SCREATE
     *out = h;
@@ -813,6 +1311,12 @@ int dbs_sa_step(dbs_sa *h, int64_t n)
 {
     SGUARD(h);
     if (n < 0) return DBS_E_ARG;
+    if (h->path == DBS_PATH_COOP) return sa_coop_step(h, n);
+    if (h->recs_stale) {
+        const int rc = sa_repack(h);
+        if (rc) return rc;
+        h->recs_stale = false;
+    }
     SaArgs A = sa_args(h);
     for (int64_t k = 0; k < n; ++k) {
         A.phase = 0;
@@ -832,6 +1336,11 @@ int dbs_sa_rates(dbs_sa *h, double *Rdot, double *Ndot)
 {
     SGUARD(h);
     if (!Rdot || !Ndot) return DBS_E_ARG;
+    if (h->recs_stale) {
+        const int rc = sa_repack(h);
+        if (rc) return rc;
+        h->recs_stale = false;
+    }
     SaArgs A = sa_args(h);
     A.phase = 2;
     A.rec_in = h->recA;
@@ -840,6 +1349,7 @@ int dbs_sa_rates(dbs_sa *h, double *Rdot, double *Ndot)
     std::vector<double> r(6 * h->p.S);
     SCK(h, cudaMemcpyAsync(r.data(), h->rate_out, sizeof(double) * 6 * h->p.S, cudaMemcpyDeviceToHost, h->stream));
     SCK(h, cudaStreamSynchronize(h->stream));
+    if (const int rc = sa_check_flags(h)) return rc;
     for (int64_t s = 0; s < h->p.S; ++s)
         for (int k = 0; k < 3; ++k) {
             Rdot[3 * s + k] = r[6 * s + k];
@@ -856,6 +1366,26 @@ int dbs_sa_state(dbs_sa *h, double *R, double *N)
     SCK(h, cudaMemcpyAsync(R, h->R, v3, cudaMemcpyDeviceToHost, h->stream));
     SCK(h, cudaMemcpyAsync(N, h->N, v3, cudaMemcpyDeviceToHost, h->stream));
     SCK(h, cudaStreamSynchronize(h->stream));
+    return sa_check_flags(h);
+}
+
+int dbs_sa_set_path(dbs_sa *h, int32_t path)
+{
+    SGUARD(h);
+    if (path == DBS_PATH_GRID) {
+        h->path = DBS_PATH_GRID;
+        return DBS_OK;
+    }
+    if (path != DBS_PATH_COOP) return sa_refuse(h, DBS_E_ARG, "path must be DBS_PATH_GRID or DBS_PATH_COOP");
+    if (h->path == DBS_PATH_COOP) return DBS_OK;
+    return sa_coop_setup(h);
+}
+
+int dbs_sa_get_path(dbs_sa *h, int32_t *path, int32_t *targets_per_cta)
+{
+    if (!h || !path) return DBS_E_ARG;
+    *path = h->path;
+    if (targets_per_cta) *targets_per_cta = h->path == DBS_PATH_COOP ? h->coop_T : 0;
     return DBS_OK;
 }
 

@@ -352,6 +352,15 @@ class StrokeAveraged:
     def step(self, n: int = 1):
         self._check(load().dbs_sa_step(self._h, _i64(int(n))))
 
+    def set_path(self, path: str):
+        """"grid" (one launch per evaluation) or "coop" (FP32C, S <= 4096; the default there)."""
+        self._check(load().dbs_sa_set_path(self._h, ctypes.c_int32(_PATHS[path])))
+
+    def get_path(self):
+        p, t = ctypes.c_int32(), ctypes.c_int32()
+        self._check(load().dbs_sa_get_path(self._h, ctypes.byref(p), ctypes.byref(t)))
+        return {v: k for k, v in _PATHS.items()}[p.value], t.value
+
     def rates(self):
         Rd = np.empty((self.S, 3))
         Nd = np.empty((self.S, 3))
