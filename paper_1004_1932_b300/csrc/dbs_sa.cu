@@ -13,6 +13,11 @@
 //         Dh (3s + 6rq + 6sq^2 - 7s^3 - 21sr^2 - 42qs^2r + 63 s^3 r^2)
 // ((lambda/ell)^2 (ell/D)^4 = lam^s lam^r ell^2 / D^4 for equal amplitudes),
 // then dR/dt = sum J, dN/dt = -(I - N N^T) sum K, Heun in time, N renormalised.
+// N^s is the target's own orientation, so the pair code accumulates
+// sum_r cj pN (one scalar) and sum_r cj pD Dh apart, and the epilogue forms
+// sum J = N^s sum(cj pN) + sum(cj pD Dh); the polynomials are evaluated as
+//   pN = s (2 - 10 r^2) + 4 q r,
+//   pK = s (3 + 6 q^2 - 7 s^2 - 21 r^2 + 63 s^2 r^2) + q r (6 - 42 s^2).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -86,7 +91,7 @@ __device__ __forceinline__ void store_rec(SaRecF64 *o, int64_t s, const double R
 
 template <typename T, typename Rec>
 __device__ __forceinline__ void sa_pair(bool self, T Rx, T Ry, T Rz, T lam_s, T Nx, T Ny, T Nz,
-                                        T sn_s, T cs_s, const Rec &q, T J[3], T K[3])
+                                        T sn_s, T cs_s, const Rec &q, T J[4], T K[3])
 {
     T qRx, qRy, qRz, qlam, qNx, qNy, qNz, qsn, qcs;
     if constexpr (sizeof(T) == 4) {
@@ -109,16 +114,17 @@ __device__ __forceinline__ void sa_pair(bool self, T Rx, T Ry, T Rz, T lam_s, T 
     T amp = lam_s * qlam * sd;
     T w2 = w * w;
     T w4 = w2 * w2;
-    T s2 = s * s, r2 = r * r;
-    T pN = 2 * s + 4 * qq * r - 10 * s * r2;
-    T pD = 1 + 2 * qq * qq - 5 * s2 - 5 * r2 - 20 * qq * s * r + 35 * s2 * r2;
-    T pK = 3 * s + 6 * r * qq + 6 * s * qq * qq - 7 * s2 * s - 21 * s * r2 - 42 * qq * s2 * r
-           + 63 * s2 * s * r2;
+    T s2 = s * s, r2 = r * r, qr = qq * r, s2r2 = s2 * r2;
+    T pN = s * (2 - 10 * r2) + 4 * qr;
+    T pD = 1 + 2 * qq * qq - 5 * s2 - 5 * r2 - 20 * qr * s + 35 * s2r2;
+    T pK = s * (3 + 6 * qq * qq - 7 * s2 - 21 * r2 + 63 * s2r2) + qr * (6 - 42 * s2);
     T cj = amp * w4;        // times CJ in the epilogue
-    T ck = amp * w4 * w * pK;  // times CK in the epilogue
-    J[0] += cj * (Nx * pN + hx * pD);
-    J[1] += cj * (Ny * pN + hy * pD);
-    J[2] += cj * (Nz * pN + hz * pD);
+    T ck = cj * w * pK;     // times CK in the epilogue
+    T cjD = cj * pD;
+    J[0] += cjD * hx;       // the pD part of J; J[3]: sum of cj pN (times N^s in the epilogue)
+    J[1] += cjD * hy;
+    J[2] += cjD * hz;
+    J[3] += cj * pN;
     K[0] += ck * hx;
     K[1] += ck * hy;
     K[2] += ck * hz;
@@ -134,7 +140,7 @@ __device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
 
 __device__ __forceinline__ void sa_pair2(bool self0, bool self1, float2 Rx, float2 Ry, float2 Rz, float2 lam_s,
                                          float2 Nx, float2 Ny, float2 Nz, float2 sn_s, float2 cs_s,
-                                         const SaRecF32 &q0, const SaRecF32 &q1, float2 J[3], float2 K[3])
+                                         const SaRecF32 &q0, const SaRecF32 &q1, float2 J[4], float2 K[3])
 {
     const float2 m1 = f2s(-1.f);
     const float2 Dx = __ffma2_rn(f2(q0.R.x, q1.R.x), m1, Rx);
@@ -161,30 +167,29 @@ __device__ __forceinline__ void sa_pair2(bool self0, bool self1, float2 Rx, floa
     const float2 w2 = __fmul2_rn(w, w);
     const float2 w4 = __fmul2_rn(w2, w2);
     const float2 s2 = __fmul2_rn(s, s), r2 = __fmul2_rn(r, r);
-    const float2 qr = __fmul2_rn(qq, r), sr2 = __fmul2_rn(s, r2), qq2 = __fmul2_rn(qq, qq);
-    const float2 qsr = __fmul2_rn(qr, s), s3 = __fmul2_rn(s2, s);
-    // pN = 2s + 4 q r - 10 s r^2
-    float2 pN = __ffma2_rn(f2s(4.f), qr, __fmul2_rn(f2s(2.f), s));
-    pN = __ffma2_rn(f2s(-10.f), sr2, pN);
+    const float2 qr = __fmul2_rn(qq, r), qq2 = __fmul2_rn(qq, qq), s2r2 = __fmul2_rn(s2, r2);
+    // pN = s (2 - 10 r^2) + 4 q r
+    const float2 pN = __ffma2_rn(f2s(4.f), qr, __fmul2_rn(s, __ffma2_rn(f2s(-10.f), r2, f2s(2.f))));
     // pD = 1 + 2 q^2 - 5 s^2 - 5 r^2 - 20 q s r + 35 s^2 r^2
     float2 pD = __ffma2_rn(f2s(2.f), qq2, f2s(1.f));
     pD = __ffma2_rn(f2s(-5.f), s2, pD);
     pD = __ffma2_rn(f2s(-5.f), r2, pD);
-    pD = __ffma2_rn(f2s(-20.f), qsr, pD);
-    pD = __ffma2_rn(f2s(35.f), __fmul2_rn(s2, r2), pD);
-    // pK = 3s + 6 r q + 6 s q^2 - 7 s^3 - 21 s r^2 - 42 q s^2 r + 63 s^3 r^2
-    float2 pK = __fmul2_rn(f2s(3.f), s);
-    pK = __ffma2_rn(f2s(6.f), qr, pK);
-    pK = __ffma2_rn(f2s(6.f), __fmul2_rn(s, qq2), pK);
-    pK = __ffma2_rn(f2s(-7.f), s3, pK);
-    pK = __ffma2_rn(f2s(-21.f), sr2, pK);
-    pK = __ffma2_rn(f2s(-42.f), __fmul2_rn(qsr, s), pK);
-    pK = __ffma2_rn(f2s(63.f), __fmul2_rn(s3, r2), pK);
+    pD = __ffma2_rn(f2s(-20.f), __fmul2_rn(qr, s), pD);
+    pD = __ffma2_rn(f2s(35.f), s2r2, pD);
+    // pK = s (3 + 6 q^2 - 7 s^2 - 21 r^2 + 63 s^2 r^2) + q r (6 - 42 s^2)
+    float2 pA = __ffma2_rn(f2s(6.f), qq2, f2s(3.f));
+    pA = __ffma2_rn(f2s(-7.f), s2, pA);
+    pA = __ffma2_rn(f2s(-21.f), r2, pA);
+    pA = __ffma2_rn(f2s(63.f), s2r2, pA);
+    const float2 pK = __ffma2_rn(qr, __ffma2_rn(f2s(-42.f), s2, f2s(6.f)), __fmul2_rn(s, pA));
     const float2 cj = __fmul2_rn(amp, w4);          // times CJ in the epilogue
     const float2 ck = __fmul2_rn(__fmul2_rn(cj, w), pK);  // times CK in the epilogue
-    J[0] = __ffma2_rn(cj, __ffma2_rn(hx, pD, __fmul2_rn(Nx, pN)), J[0]);
-    J[1] = __ffma2_rn(cj, __ffma2_rn(hy, pD, __fmul2_rn(Ny, pN)), J[1]);
-    J[2] = __ffma2_rn(cj, __ffma2_rn(hz, pD, __fmul2_rn(Nz, pN)), J[2]);
+    const float2 cjD = __fmul2_rn(cj, pD);
+    // the pD part of J; J[3]: sum of cj pN (times the target's N in the epilogue)
+    J[0] = __ffma2_rn(cjD, hx, J[0]);
+    J[1] = __ffma2_rn(cjD, hy, J[1]);
+    J[2] = __ffma2_rn(cjD, hz, J[2]);
+    J[3] = __ffma2_rn(cj, pN, J[3]);
     K[0] = __ffma2_rn(ck, hx, K[0]);
     K[1] = __ffma2_rn(ck, hy, K[1]);
     K[2] = __ffma2_rn(ck, hz, K[2]);
@@ -303,7 +308,9 @@ __global__ void __launch_bounds__(SA_NT) sa_eval_kernel(SaArgs A)
     constexpr int WPT = NSL > 32 ? NSL / 32 : 1;  // warps per target
     constexpr int TILE = sa_tile<T>();
     __shared__ Rec tile[TILE];
-    __shared__ T red[WPT == 1 ? TL : SA_NT / 32][12];   // J sum, J comp., K sum, K comp. (x, y, z)
+    // per row: the pD part of J (sums 0-2, compensations 3-5), K (6-8, 9-11) and
+    // the sum of cj pN (12, 13)
+    __shared__ T red[WPT == 1 ? TL : SA_NT / 32][14];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int t = tid / NSL, sl = tid - t * NSL;
     const int64_t st = (int64_t)blockIdx.x * TL + t;
@@ -347,20 +354,21 @@ __global__ void __launch_bounds__(SA_NT) sa_eval_kernel(SaArgs A)
         Nx = me.Nx; Ny = me.Ny; Nz = me.Nz; sn = me.sn; cs = me.cs;
     }
     // FP32: per-tile FP32 sums folded into (sum, compensation); FP64: plain sums.
-    // Slots 0-2: J, 3-5: K, 6-7: empty (for the transposing fold).
+    // Slots 0-2: the pD part of J, 3-5: K, 6: sum of cj pN, 7: empty (for the
+    // transposing fold).
     T fs[8] = {0, 0, 0, 0, 0, 0, 0, 0}, fc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int64_t t0 = 0; t0 < A.S; t0 += TILE) {
         const int len = (int)min((int64_t)TILE, A.S - t0);
         __syncthreads();
         for (int k = tid; k < len; k += SA_NT) tile[k] = in[t0 + k];
         __syncthreads();
-        T J[3] = {0, 0, 0}, K[3] = {0, 0, 0};
+        T J[4] = {0, 0, 0, 0}, K[3] = {0, 0, 0};
         if (act) {
             int k = sl;
             // two records per paired call (FP32; with TL <= 2 a thread holds at most
             // two records of a tile, and the paired code would only cost registers)
             if constexpr (sizeof(T) == 4 && TL >= 4) {
-                float2 J2[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+                float2 J2[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
                 float2 K2[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
                 for (; k + NSL < len; k += 2 * NSL)
                     sa_pair2(t0 + k == st, t0 + k + NSL == st, f2s(Rx), f2s(Ry), f2s(Rz), f2s(lam), f2s(Nx),
@@ -372,6 +380,8 @@ __global__ void __launch_bounds__(SA_NT) sa_eval_kernel(SaArgs A)
                     sa_merge(fs[3 + c], fc[3 + c], K2[c].x, T(0));
                     sa_merge(fs[3 + c], fc[3 + c], K2[c].y, T(0));
                 }
+                sa_merge(fs[6], fc[6], J2[3].x, T(0));
+                sa_merge(fs[6], fc[6], J2[3].y, T(0));
             }
             for (; k < len; k += NSL)
                 sa_pair<T, Rec>(t0 + k == st, Rx, Ry, Rz, lam, Nx, Ny, Nz, sn, cs, tile[k], J, K);
@@ -381,24 +391,26 @@ __global__ void __launch_bounds__(SA_NT) sa_eval_kernel(SaArgs A)
             sa_merge(fs[k], fc[k], J[k], T(0));
             sa_merge(fs[3 + k], fc[3 + k], K[k], T(0));
         }
+        sa_merge(fs[6], fc[6], J[3], T(0));
     }
     int ci;
     sa_fold_lanes<T, LW>(fs, fc, lane, ci);
-    if ((lane & (LW / 8 - 1)) == 0 && ci < 6) {
+    if ((lane & (LW / 8 - 1)) == 0 && ci < 7) {
         const int row = WPT == 1 ? t : warp;
-        const int col = ci < 3 ? ci : 3 + ci;   // J: sum ci, comp. 3 + ci; K: sum 6 + k, comp. 9 + k
+        // pD part of J: sum ci, comp. 3 + ci; K: sum 6 + k, comp. 9 + k; cj pN: 12, 13
+        const int col = ci < 3 ? ci : (ci < 6 ? 3 + ci : 12);
         red[row][col] = fs[0];
-        red[row][col + 3] = fc[0];
+        red[row][col + (ci < 6 ? 3 : 1)] = fc[0];
     }
     __syncthreads();
     if (warp >= 3) return;
     // ---- epilogue: lane ta of axis warp a --------------------------------------
     const int a = ea;
     if (!EARLY) load_state();
-    double Ja = 0.0, Kd[3] = {0.0, 0.0, 0.0};
+    double JD = 0.0, JN = 0.0, Kd[3] = {0.0, 0.0, 0.0};
     if (on) {
         const int r0w = ta * WPT;
-        T js = red[r0w][a], jc = red[r0w][3 + a];
+        T js = red[r0w][a], jc = red[r0w][3 + a], ns = red[r0w][12], nc = red[r0w][13];
         T ks[3], kc[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -407,10 +419,12 @@ __global__ void __launch_bounds__(SA_NT) sa_eval_kernel(SaArgs A)
         }
         for (int w = 1; w < WPT; ++w) {   // the target's warps, in warp order
             sa_merge(js, jc, red[r0w + w][a], red[r0w + w][3 + a]);
+            sa_merge(ns, nc, red[r0w + w][12], red[r0w + w][13]);
 #pragma unroll
             for (int k = 0; k < 3; ++k) sa_merge(ks[k], kc[k], red[r0w + w][6 + k], red[r0w + w][9 + k]);
         }
-        Ja = A.CJ * ((double)js + (double)jc);
+        JD = (double)js + (double)jc;
+        JN = (double)ns + (double)nc;
 #pragma unroll
         for (int k = 0; k < 3; ++k) Kd[k] = A.CK * ((double)ks[k] + (double)kc[k]);
     }
@@ -422,6 +436,8 @@ __global__ void __launch_bounds__(SA_NT) sa_eval_kernel(SaArgs A)
     double Nb[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) Nb[k] = A.phase == 1 ? fma(A.dt, n0[k], Nn[k]) : Nn[k];
+    // J along a: the target's orientation at the evaluation point times the cj pN sum
+    const double Ja = A.CJ * fma(a == 0 ? Nb[0] : (a == 1 ? Nb[1] : Nb[2]), JN, JD);
     const double NK = fma(Nb[0], Kd[0], fma(Nb[1], Kd[1], Nb[2] * Kd[2]));
     double rK[3];
 #pragma unroll
@@ -490,6 +506,10 @@ __global__ void sa_pack_kernel(SaArgs A)
 // FP32 (the corrector's N normalised in FP32 for its record); the
 // double-single update runs in the next poll's gap.
 constexpr int SAF_TIMEOUT = 4, SAF_LAUNCH = 8;
+#ifndef DBS_SA_COOP_UNROLL
+#define DBS_SA_COOP_UNROLL 4
+#endif
+constexpr int kSaCoopUnroll = DBS_SA_COOP_UNROLL;   // paired calls in flight per thread in the sweep
 constexpr int SAC_CHUNK = 512;     // records per compensated partial sum (as sa_eval_kernel's tile)
 constexpr int SAC_POLL = 8;        // words per thread and round of a poll
 
@@ -566,7 +586,7 @@ __global__ void __launch_bounds__(SA_NT, 1) sa_flow_kernel(const SaArgs A, const
     constexpr int WPT = NSL > 32 ? NSL / 32 : 1;
     extern __shared__ float4 sac_smem[];          // all records, SaRecF32
     __shared__ SaOwn<TL> own;
-    __shared__ float red[WPT == 1 ? TL : SA_NT / 32][12];
+    __shared__ float red[WPT == 1 ? TL : SA_NT / 32][14];   // as in sa_eval_kernel
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = blockIdx.x;
     const int S = (int)A.S;
@@ -719,11 +739,12 @@ __global__ void __launch_bounds__(SA_NT, 1) sa_flow_kernel(const SaArgs A, const
             for (int t0 = 0; t0 < S; t0 += SAC_CHUNK) {
                 const int len = min(SAC_CHUNK, S - t0);
                 const SaRecF32 *ch = tile + t0;
-                float J[3] = {0, 0, 0}, K[3] = {0, 0, 0};
+                float J[4] = {0, 0, 0, 0}, K[3] = {0, 0, 0};
                 int k = sl;
                 if constexpr (TL >= 4) {
-                    float2 J2[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+                    float2 J2[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
                     float2 K2[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll kSaCoopUnroll
                     for (; k + NSL < len; k += 2 * NSL)
                         sa_pair2(t0 + k == st, t0 + k + NSL == st, f2s(Rx), f2s(Ry), f2s(Rz), f2s(lam), f2s(Nx),
                                  f2s(Ny), f2s(Nz), f2s(sn), f2s(cs), ch[k], ch[k + NSL], J2, K2);
@@ -734,6 +755,8 @@ __global__ void __launch_bounds__(SA_NT, 1) sa_flow_kernel(const SaArgs A, const
                         sa_merge(fs[3 + c], fc[3 + c], K2[c].x, 0.f);
                         sa_merge(fs[3 + c], fc[3 + c], K2[c].y, 0.f);
                     }
+                    sa_merge(fs[6], fc[6], J2[3].x, 0.f);
+                    sa_merge(fs[6], fc[6], J2[3].y, 0.f);
                 }
                 for (; k < len; k += NSL)
                     sa_pair<float, SaRecF32>(t0 + k == st, Rx, Ry, Rz, lam, Nx, Ny, Nz, sn, cs, ch[k], J, K);
@@ -742,17 +765,18 @@ __global__ void __launch_bounds__(SA_NT, 1) sa_flow_kernel(const SaArgs A, const
                     sa_merge(fs[c], fc[c], J[c], 0.f);
                     sa_merge(fs[3 + c], fc[3 + c], K[c], 0.f);
                 }
+                sa_merge(fs[6], fc[6], J[3], 0.f);
             }
         }
         // 3. fold: lanes by transposition, then the target's warps in warp order
         {
             int ci;
             sa_fold_lanes<float, LW>(fs, fc, lane, ci);
-            if ((lane & (LW / 8 - 1)) == 0 && ci < 6) {
+            if ((lane & (LW / 8 - 1)) == 0 && ci < 7) {
                 const int row = WPT == 1 ? t : warp;
-                const int col = ci < 3 ? ci : 3 + ci;
+                const int col = ci < 3 ? ci : (ci < 6 ? 3 + ci : 12);
                 red[row][col] = fs[0];
-                red[row][col + 3] = fc[0];
+                red[row][col + (ci < 6 ? 3 : 1)] = fc[0];
             }
         }
         __syncthreads();
@@ -764,7 +788,8 @@ __global__ void __launch_bounds__(SA_NT, 1) sa_flow_kernel(const SaArgs A, const
             float Rn = 0.f, Nn = 0.f;
             if (ax) {
                 const int r0w = d * WPT;
-                float js = red[r0w][a], jc = red[r0w][3 + a], ks[3], kc[3];
+                float js = red[r0w][a], jc = red[r0w][3 + a], ns = red[r0w][12], nc = red[r0w][13];
+                float ks[3], kc[3];
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     ks[k] = red[r0w][6 + k];
@@ -772,10 +797,14 @@ __global__ void __launch_bounds__(SA_NT, 1) sa_flow_kernel(const SaArgs A, const
                 }
                 for (int w = 1; w < WPT; ++w) {
                     sa_merge(js, jc, red[r0w + w][a], red[r0w + w][3 + a]);
+                    sa_merge(ns, nc, red[r0w + w][12], red[r0w + w][13]);
 #pragma unroll
                     for (int k = 0; k < 3; ++k) sa_merge(ks[k], kc[k], red[r0w + w][6 + k], red[r0w + w][9 + k]);
                 }
-                const float Jf = CJf * (js + jc);
+                // the target's orientation in the record the sums were taken at
+                const float4 mN = tile[s].N;
+                const float Nrec = a == 0 ? mN.x : (a == 1 ? mN.y : mN.z);
+                const float Jf = CJf * fmaf(Nrec, ns + nc, js + jc);
                 float Kf[3];
 #pragma unroll
                 for (int k = 0; k < 3; ++k) Kf[k] = CKf * (ks[k] + kc[k]);
@@ -788,8 +817,7 @@ __global__ void __launch_bounds__(SA_NT, 1) sa_flow_kernel(const SaArgs A, const
                     Rn = sac_add(own.Rh[a][d], own.Rl[a][d], dtf * Jf);
                     Nn = sac_add(own.Nh[a][d], own.Nl[a][d], dtf * rK);
                 } else {       // x_{n+1} = x_n + dt/2 (rate0 + rate(x~)), N renormalised
-                    const float4 mN = tile[s].N;   // the predicted point's orientation
-                    const float Nb[3] = {mN.x, mN.y, mN.z};
+                    const float Nb[3] = {mN.x, mN.y, mN.z};   // the predicted point's orientation
                     const float NK = fmaf(Nb[0], Kf[0], fmaf(Nb[1], Kf[1], Nb[2] * Kf[2]));
                     float N1[3];
 #pragma unroll
