@@ -628,6 +628,16 @@ DBS_API int dbs_test_flow_misshape(dbs_suspension *h);
  */
 DBS_API int dbs_test_ensemble_misshape(dbs_ensemble *e);
 
+/*
+ * Diagnostic of the averaged model's cooperative kernel's launch-shape check:
+ * one averaged step whose kernel is told it has one CTA more than it was
+ * launched with.  Every CTA must refuse before touching the state or the
+ * exchange words; returns what the flag check then returns (DBS_E_CUDA
+ * expected; the handle keeps that error).  DBS_E_STATE if the handle is not on
+ * the cooperative path.
+ */
+DBS_API int dbs_test_sa_flow_misshape(dbs_sa *h);
+
 /* Library version string. */
 DBS_API const char *dbs_version(void);
 

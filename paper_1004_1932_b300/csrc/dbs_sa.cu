@@ -1000,6 +1000,7 @@ struct dbs_sa {
     unsigned long long *words = nullptr;
     int *flags = nullptr;       // SAF_* raised by the cooperative kernel
     bool recs_stale = false;    // recA behind the state after cooperative steps
+    int test_dG = 0;            // diagnostic: CTAs the kernel is told beyond those launched
 };
 
 static int sa_fail(dbs_sa *h, int st, const char *fmt, ...)
@@ -1183,7 +1184,7 @@ static int sa_coop_step(dbs_sa *h, int64_t n)
         SaFlowArgs P{};
         P.words = h->words;
         P.flags = h->flags;
-        P.G = h->coop_G;
+        P.G = h->coop_G + h->test_dG;
         P.K = K;
         P.base = h->coop_base;
         P.timeout_ns = 1000000000ull;
@@ -1407,6 +1408,19 @@ int dbs_sa_set_path(dbs_sa *h, int32_t path)
     if (path != DBS_PATH_COOP) return sa_refuse(h, DBS_E_ARG, "path must be DBS_PATH_GRID or DBS_PATH_COOP");
     if (h->path == DBS_PATH_COOP) return DBS_OK;
     return sa_coop_setup(h);
+}
+
+int dbs_test_sa_flow_misshape(dbs_sa *h)
+{
+    SGUARD(h);
+    if (h->path != DBS_PATH_COOP) return sa_refuse(h, DBS_E_STATE, "not on the cooperative path");
+    // one averaged step whose kernel is told it has one CTA more than it was launched with
+    h->test_dG = 1;
+    const int rc = sa_coop_step(h, 1);
+    h->test_dG = 0;
+    if (rc) return rc;
+    SCK(h, cudaStreamSynchronize(h->stream));
+    return sa_check_flags(h);
 }
 
 int dbs_sa_get_path(dbs_sa *h, int32_t *path, int32_t *targets_per_cta)

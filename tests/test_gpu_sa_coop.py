@@ -10,6 +10,9 @@
 * Runs longer than one launch (1024 averaged steps) continue where the last
   launch ended, the rates read after cooperative steps are those of the
   current state, and two runs from one state are bit-identical.
+* The kernel refuses a launch in a shape other than the one it was told
+  (DBS_E_CUDA), before touching state or exchange words; the device and the
+  path stay usable.
 """
 import numpy as np
 import pytest
@@ -110,3 +113,26 @@ def test_switching_paths_mid_run():
         R, N = h.state()
     assert _motion_bound(R, R_ref, s.R0, TOL)
     np.testing.assert_allclose(np.linalg.norm(N, axis=1), 1.0, rtol=1e-14)
+
+
+def test_cooperative_kernel_refuses_a_launch_shape_it_was_not_built_for():
+    # told one CTA more than it was launched with, every CTA refuses before
+    # touching state or exchange words; the host reports it, the state is kept
+    lib = dbs.load()
+    s = inputs.paper_scale(512, seed=5)
+    h = _sa(s)
+    h.step(3)
+    R0, N0 = h.state()
+    assert lib.dbs_test_sa_flow_misshape(h._h) == dbs.E_CUDA
+    assert "shape" in lib.dbs_sa_last_error(h._h).decode()
+    with pytest.raises(dbs.DbsError):          # sticky
+        h.step(1)
+    h.close()
+    # the device and the cooperative path stay usable, from the same state
+    with dbs.StrokeAveraged(R0, N0, s.phi, s.lam, a=s.a, ell=s.ell, omega=s.omega, dt=0.1) as h2:
+        assert h2.get_path()[0] == "coop"
+        h2.step(4)
+        R, N = h2.state()
+    assert np.isfinite(R).all() and np.isfinite(N).all()
+    with _sa(s, precision="fp64") as hf:       # not on the cooperative path
+        assert lib.dbs_test_sa_flow_misshape(hf._h) == dbs.E_STATE
