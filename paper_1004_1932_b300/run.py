@@ -110,6 +110,7 @@ def breakdown(s, a):
             dbs.StrokeAveraged(s.R0, s.N0, s.phi, s.lam, a=s.a, ell=s.ell, omega=s.omega, dt=T / 10,
                                precision="fp32c", stream=stream) as sa, torch.cuda.stream(stream):
         h.set_path(a.path, a.cluster)
+        sa.set_path("grid")   # as in bench.py, where it overlaps the microscopic model
         h.enable_period_average(m, max_periods=a.breakdown + 2)
         ref = torch.empty((a.S, 3), dtype=torch.float64, device="cuda")
         for k in range(a.breakdown + 2):
