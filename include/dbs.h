@@ -293,8 +293,8 @@ DBS_API int dbs_sa_state(dbs_sa *h, double *R, double *N);
  *                 precision).
  *  DBS_PATH_COOP  one cooperative launch of up to one CTA per SM advances up to
  *                 1024 averaged steps; each CTA owns T dumbbells (T the
- *                 smallest power of two <= 32 for which ceil(S / T) CTAs fit the
- *                 SMs), holds every record in shared memory and sums its
+ *                 smallest power of two from 2 to 32 for which ceil(S / T) CTAs
+ *                 fit the SMs), holds every record in shared memory and sums its
  *                 targets over all of them; CTAs exchange only (R, N), one
  *                 64-bit word per dumbbell and axis with a parity bit in the
  *                 lowest significand bit of N's component (cleared on use),
