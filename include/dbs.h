@@ -377,7 +377,7 @@ DBS_API int dbs_pair_distance_error(int64_t S, const double *A0_dev, const doubl
  *                    the largest power of two not above min(c, the T limit),
  *                    raised until ceil(S / T) CTAs fit the SMs; 0 restores the
  *                    built-in choice (the smallest T that fits; FP32C: 16 for
- *                    S <= 16).
+ *                    S <= 16, at least 2 above).
  */
 #define DBS_PATH_COOP 2
 DBS_API int dbs_set_path(dbs_suspension *h, int32_t path, int32_t cluster_size);

@@ -757,8 +757,9 @@ static cudaLaunchConfig_t flow_config(const dbs_suspension *h, int G, int T, cud
 
 // Split: T dumbbells per CTA, the smallest power of two (at least the largest
 // one not above a dbs_set_chunks request; FP32C: 16 for S <= 16, so that one CTA
-// holds a tiny system; FP64 spreads even a tiny system over the SMs, whose FP64
-// pipes are the bound) for which all ceil(S / T) CTAs fit the SMs, one CTA each.
+// holds a tiny system, else at least 2; FP64 spreads even a tiny system over the
+// SMs, whose FP64 pipes are the bound) for which all ceil(S / T) CTAs fit the
+// SMs, one CTA each.
 int coop_setup(dbs_suspension *h)
 {
     const bool f64 = is_f64(h);
@@ -772,7 +773,9 @@ int coop_setup(dbs_suspension *h)
     CK(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     if (!coop) return refuse(h, DBS_E_ARG, "device without cooperative launch");
     // tiny FP32C systems: one CTA holds all dumbbells and no record leaves it
-    int T = (!f64 && h->S <= 16) ? 16 : 1;
+    // FP32C: at least two dumbbells per CTA (S = 64 / 128 / 148: 3.51 / 3.80 / 4.39
+    // us per Heun step with one, 3.30 / 3.47 / 3.70 with two, measured)
+    int T = f64 ? 1 : (h->S <= 16 ? 16 : 2);
     if (h->flow_creq > 0) {
         T = 1;
         while (2 * T <= std::min(h->flow_creq, max_t)) T *= 2;
