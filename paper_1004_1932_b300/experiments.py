@@ -274,17 +274,24 @@ def serving_full():
             "small_budget": small}
 
 
-def colloids_rate(N=2000, steps=2000, mobility="oseen", precision="fp32c"):
+def colloids_rate(N=2000, steps=2000, mobility="oseen", precision="fp32c", path="auto"):
+    """Heun steps per second of N colloids under a constant force; `path` "auto"
+    times the stepping paths first (autotune.choose_path) and keeps the fastest."""
+    from . import autotune
     s, F = inputs.colloids(N, mobility=mobility)
     with dbs.Suspension.from_inputs(s, precision=precision) as h:
         h.set_external_force(F)
+        if path == "auto":
+            path = autotune.choose_path(h)["path"]
+        else:
+            h.set_path(path)
         h.step(64)
         h.sync()
         t0 = time.perf_counter()
         h.step(steps)
         h.sync()
         el = time.perf_counter() - t0
-    return {"N": N, "steps": steps, "seconds": el, "heun_steps_per_s": steps / el,
+    return {"N": N, "steps": steps, "path": path, "seconds": el, "heun_steps_per_s": steps / el,
             "pairs_per_s": 2 * N * (N - 1) * steps / el}
 
 
@@ -301,6 +308,7 @@ def main(argv=None):
     co = sub.add_parser("colloids")
     co.add_argument("--N", type=int, default=2000)
     co.add_argument("--steps", type=int, default=2000)
+    co.add_argument("--path", default="auto", choices=["auto", "grid", "cluster", "coop"])
     sv = sub.add_parser("serving")
     sv.add_argument("--full", action="store_true", help="the three runs of serving_full()")
     sv.add_argument("--requests", type=int, default=48)
@@ -320,7 +328,7 @@ def main(argv=None):
                                                        dt_over_T=a.dt_over_T)["msd_over_ell2"]
             print(json.dumps(r), flush=True)
     else:
-        print(json.dumps(colloids_rate(a.N, a.steps)), flush=True)
+        print(json.dumps(colloids_rate(a.N, a.steps, path=a.path)), flush=True)
 
 
 if __name__ == "__main__":

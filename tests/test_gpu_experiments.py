@@ -19,11 +19,13 @@ from paper_1004_1932_b300 import dbs, experiments, inputs
 pytestmark = pytest.mark.gpu
 
 
-def test_colloids_follow_oracle():
+@pytest.mark.parametrize("path", ["grid", "coop"])
+def test_colloids_follow_oracle(path):
     s, F = inputs.colloids(200, seed=2)
     ref = oracle.heun(s.x0, 0, 300, dt=s.dt, mobility=oracle.OSEEN, Fext=F, **s.phys())
     with dbs.Suspension.from_inputs(s) as h:
         h.set_external_force(F)
+        h.set_path(path)
         h.step(300)
         x = h.positions()
     assert np.abs(x - ref).max() <= 1e-4
