@@ -143,9 +143,11 @@ DBS_API int dbs_set_noise(dbs_suspension *h, double kT, uint64_t seed);
  * more approach the exact constraint solution), each one pair sum of Eq. (3)
  * with the exact tensors; then Heun on centre R and axis N (N renormalised),
  * spheres placed at R -/+ N L(t)/2.  Entering it projects the current
- * positions onto L(t_n) (R and N kept).  Grid path only, no external force,
- * no noise (DBS_E_STATE otherwise); k0 is ignored.  dbs_velocities then
- * reports the shape-driven velocities.
+ * positions onto L(t_n) (R and N kept).  Grid path, or in FP32C the
+ * cooperative path (DBS_PATH_COOP: one launch per <= 1024 steps, one exchange
+ * per pair sum; the state double-single within a launch, FP64 between
+ * launches); no external force, no noise (DBS_E_STATE otherwise); k0 is
+ * ignored.  dbs_velocities then reports the shape-driven velocities.
  */
 #define DBS_DYN_SPRING 0
 #define DBS_DYN_SHAPE 1

@@ -520,8 +520,8 @@ int dbs_set_path(dbs_suspension *h, int32_t path, int32_t cluster_size)
         cudaStreamSynchronize(h->stream);
         solo_destroy(h);
     }
-    if (path != DBS_PATH_GRID && h->dyn != DBS_DYN_SPRING)
-        return refuse(h, DBS_E_STATE, "shape-driven dynamics run on the grid path only");
+    if (h->dyn != DBS_DYN_SPRING && !(path == DBS_PATH_GRID || (path == DBS_PATH_COOP && h->p.precision != DBS_FP64)))
+        return refuse(h, DBS_E_STATE, "shape-driven dynamics run on the grid path, or the cooperative one in FP32C");
     h->path = DBS_PATH_GRID;
     if (path == DBS_PATH_GRID) return DBS_OK;
     if (path == DBS_PATH_COOP) {

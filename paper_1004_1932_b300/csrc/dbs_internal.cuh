@@ -69,6 +69,7 @@ int coop_setup(dbs_suspension *h);
 void launch_apply(const dbs_suspension *h, const dbs::EvalArgs &A);
 // defined in dbs_shape.cu (shape-driven dynamics)
 int shape_step(dbs_suspension *h, int64_t n);
+int shape_finish(dbs_suspension *h);
 int shape_reset(dbs_suspension *h);
 void shape_free(dbs_suspension *h);
 // defined in dbs_suspension.cu: spring records and forces of the current state into packA / Fd

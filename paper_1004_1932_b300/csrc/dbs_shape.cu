@@ -13,7 +13,8 @@
 // itself; b^{ss} = 2 h_c - 2/(6 pi mu a).  Then v = H F (Eq. (3)) gives
 //   dR^s/dt = (v^{s1} + v^{s2})/2,  dN^s/dt = (I - N N^T)(v^{s2} - v^{s1}) / L^s,
 // integrated by Heun on (R, N) with N renormalised and the spheres placed at
-// R -/+ N L(t)/2.  Grid path only; no external force or noise.
+// R -/+ N L(t)/2.  Grid path here (FP32C or FP64); the cooperative path (FP32C)
+// runs the same iteration in sd_flow_kernel.  No external force or noise.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -305,8 +306,16 @@ int shape_step(dbs_suspension *h, int64_t n)
     }
     sd_launch(sd_set_step_kernel, 1, 1, h->stream, h->step, h->n_host);
     SCK(h, cudaGetLastError());
-    // leave packA / Fd describing the current state, for dbs_velocities and friends
-    int rc = shape_eval(h, h->x, h->n_host);
+    return shape_finish(h);
+}
+
+// Leave packA / Fd describing the current state (constraint forces and records
+// at x_n), for dbs_velocities and friends.
+int shape_finish(dbs_suspension *h)
+{
+    int rc = ensure_trig(h, h->n_host + 1);
+    if (rc) return rc;
+    rc = shape_eval(h, h->x, h->n_host);
     if (rc) return rc;
     SCK(h, cudaMemcpyAsync(h->packA, h->packT, (size_t)h->S * (h->p.precision == DBS_FP64 ? sizeof(DbF64) : sizeof(DbF32)),
                            cudaMemcpyDeviceToDevice, h->stream));
@@ -351,18 +360,28 @@ int dbs_set_dynamics(dbs_suspension *h, int32_t model, int32_t iterations)
             h->dyn = DBS_DYN_SPRING;
             int rc = spring_repack(h);   // the spring's records and forces at the current state
             if (rc) return rc;
+            if (h->path == DBS_PATH_COOP && (rc = coop_setup(h)) != DBS_OK) return rc;   // the spring's kernel
             SCK(h, cudaStreamSynchronize(h->stream));
         }
         return DBS_OK;
     }
-    if (h->path != DBS_PATH_GRID || h->Fext || h->noise_sigma > 0.0)
-        return refuse(h, DBS_E_STATE, "shape-driven dynamics: grid path, no external force, no noise");
+    const bool coop_ok = h->path == DBS_PATH_COOP && h->p.precision != DBS_FP64;
+    if ((h->path != DBS_PATH_GRID && !coop_ok) || h->Fext || h->noise_sigma > 0.0)
+        return refuse(h, DBS_E_STATE,
+                      "shape-driven dynamics: grid path (or cooperative, FP32C), no external force, no noise");
     if (!h->sd_buf) SCK(h, cudaMalloc(&h->sd_buf, sizeof(double) * sd_doubles(h->S)));
     drop_graph(h);
+    const int prev_dyn = h->dyn;
     h->dyn = DBS_DYN_SHAPE;
     h->sd_iters = iterations;
     int rc = shape_reset(h);
     if (rc) return rc;
+    if (h->path == DBS_PATH_COOP && prev_dyn != DBS_DYN_SHAPE && (rc = coop_setup(h)) != DBS_OK) {
+        h->dyn = prev_dyn;       // the cooperative shape-driven kernel cannot hold it
+        shape_free(h);
+        if (spring_repack(h) == DBS_OK) cudaStreamSynchronize(h->stream);
+        return rc;
+    }
     SCK(h, cudaStreamSynchronize(h->stream));
     return DBS_OK;
 }

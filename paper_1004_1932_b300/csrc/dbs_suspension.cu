@@ -15,6 +15,7 @@
 #include "dbs_common.cuh"
 #include "eval_kernel.cuh"
 #include "flow_kernel.cuh"
+#include "sd_flow_kernel.cuh"
 #include "flow64_kernel.cuh"
 #include "dbs_internal.cuh"
 
@@ -727,8 +728,23 @@ static const void *flow64_pick(int T)
     }
 }
 
+template <int MOB>
+static const void *sd_pick(int T)
+{
+    switch (T) {
+    case 1: return (const void *)sd_flow_kernel<MOB, 1>;
+    case 2: return (const void *)sd_flow_kernel<MOB, 2>;
+    case 4: return (const void *)sd_flow_kernel<MOB, 4>;
+    case 8: return (const void *)sd_flow_kernel<MOB, 8>;
+    case 16: return (const void *)sd_flow_kernel<MOB, 16>;
+    case 32: return (const void *)sd_flow_kernel<MOB, 32>;
+    default: return nullptr;
+    }
+}
+
 static const void *flow_fn(const dbs_suspension *h, int T)
 {
+    if (h->dyn == DBS_DYN_SHAPE && !is_f64(h)) return h->p.mobility == DBS_OSEEN ? sd_pick<0>(T) : sd_pick<1>(T);
     if (is_f64(h)) return h->p.mobility == DBS_OSEEN ? flow64_pick<0>(T) : flow64_pick<1>(T);
     const bool noise = h->noise_sigma > 0.0;
     if (h->p.mobility == DBS_OSEEN) return noise ? flow_pick<0, true>(T) : flow_pick<0, false>(T);
@@ -764,6 +780,8 @@ int coop_setup(dbs_suspension *h)
 {
     const bool f64 = is_f64(h);
     if (h->S > FLOW_MAX_S) return refuse(h, DBS_E_ARG, "cooperative path needs S <= 4096");
+    if (h->dyn == DBS_DYN_SHAPE && f64)
+        return refuse(h, DBS_E_ARG, "cooperative shape-driven dynamics: FP32C only (FP64 runs on the grid path)");
     if (f64 && h->noise_sigma > 0.0)
         return refuse(h, DBS_E_ARG, "cooperative FP64 path: no additive noise (use the grid path)");
     const int max_t = f64 ? FLOW64_MAX_T : FLOW_MAX_T;
@@ -837,16 +855,20 @@ static int coop_step(dbs_suspension *h, int64_t n)
         P64.timeout_ns = P.timeout_ns;
         cudaLaunchAttribute attr[1];
         const cudaLaunchConfig_t cfg = flow_config(h, h->flow_G, h->flow_T, attr);
-        void *args[] = {(void *)&A, is_f64(h) ? (void *)&P64 : (void *)&P};
+        const bool sd = h->dyn == DBS_DYN_SHAPE;
+        const int M = h->sd_iters;   // shape-driven: pair sums per evaluation point
+        void *args[] = {(void *)&A, is_f64(h) ? (void *)&P64 : (void *)&P, (void *)&M};
         cudaError_t e = cudaLaunchKernelExC(&cfg, flow_fn(h, h->flow_T), args);
         if (e != cudaSuccess) return fail(h, DBS_E_CUDA, "cooperative launch: %s", cudaGetErrorString(e));
         // the evaluation counter runs on from launch to launch (2K evaluations per
-        // launch, so it stays even; modulo 2^32 it keeps its residue mod 4, which is
-        // all the parity bits depend on)
-        h->flow_base += (unsigned)(2 * K);
+        // launch, 2MK for the shape-driven kernel, so it stays even; modulo 2^32 it
+        // keeps its residue mod 4, which is all the parity bits depend on)
+        h->flow_base += (unsigned)(2 * K * (sd ? M : 1));
         h->n_host += K;
         left -= K;
     }
+    // shape-driven: the one-launch records and FP64 forces of the current state
+    if (h->dyn == DBS_DYN_SHAPE && n > 0) return shape_finish(h);
     return DBS_OK;
 }
 
@@ -859,8 +881,8 @@ int dbs_step(dbs_suspension *h, int64_t n)
     if (n < 0) return DBS_E_ARG;
     if (h->shard_nib > 0) return refuse(h, DBS_E_STATE, "a row-sharded handle steps with dbs_shard_eval");
     if (h->solo) return solo_step(h, n);
-    if (h->dyn == DBS_DYN_SHAPE) return shape_step(h, n);
     if (h->path == DBS_PATH_COOP) return coop_step(h, n);
+    if (h->dyn == DBS_DYN_SHAPE) return shape_step(h, n);
     int64_t left = n, k = h->n_host;
     int rc;
     if (left >= GRAPH_STEPS) {

@@ -6,8 +6,9 @@
 * Lengths stay on L(t); an isolated dumbbell neither moves nor turns.
 * dbs_velocities in this mode reports H F for the constraint forces.
 * Stroke averages accumulate as in the spring model (trapezoid rule).
-* The mode refuses other paths, noise and external forces (DBS_E_STATE), and
-  switching back to the spring continues the run.
+* The mode refuses the cluster path, noise and external forces (DBS_E_STATE),
+  and switching back to the spring continues the run (the cooperative path:
+  test_gpu_shape_coop.py).
 """
 import math
 
@@ -105,7 +106,7 @@ def test_shape_mode_restrictions_and_return_to_spring():
     s = inputs.make_suspension(16, seed=11, side=8.0)
     with _handle(s) as h:
         h.set_dynamics("shape", 2)
-        for call in (lambda: h.set_path("coop"), lambda: h.set_path("cluster"),
+        for call in (lambda: h.set_path("cluster"),
                      lambda: h.set_noise(1e-3, 1), lambda: h.set_external_force(np.ones((32, 3)))):
             with pytest.raises(dbs.DbsError) as ei:
                 call()
