@@ -6,7 +6,8 @@
 * At paper scale (splits of 2 to 16 dumbbells per CTA, ragged last CTAs) the
   cooperative path ends where the grid path ends; runs longer than one launch
   (1024 steps) continue where the last launch ended; stroke averages match the
-  grid path's; dbs_velocities afterwards reports H F for the constraint forces.
+  grid path's; dbs_velocities afterwards reports H F for the constraint forces;
+  the kernel refuses a launch shape other than the one it was told (DBS_E_CUDA).
 * FP64 stays on the grid path (DBS_E_STATE), and switching back to the spring
   model on the cooperative path continues the run.
 """
@@ -111,3 +112,21 @@ def test_coop_shape_restrictions_and_return_to_spring():
         x = h.positions()
     ref = oracle.heun(x_mid, n_mid, 50, dt=s.dt, mobility=MOB[s.mobility], **s.phys())
     assert np.abs(x - ref).max() <= 1e-4 * s.ell
+
+
+def test_coop_shape_kernel_refuses_a_launch_shape_it_was_not_built_for():
+    # told one CTA more than it was launched with, every CTA refuses before
+    # touching state or exchange words; the device and the path stay usable
+    lib = dbs.load()
+    s = inputs.paper_scale(512, seed=13)
+    h = _handle(s)
+    h.set_path("coop")
+    h.set_dynamics("shape", 2)
+    assert lib.dbs_test_flow_misshape(h._h) == dbs.E_CUDA
+    assert "shape" in lib.dbs_last_error(h._h).decode()
+    h.close()
+    with _handle(s) as h2:
+        h2.set_path("coop")
+        h2.set_dynamics("shape", 2)
+        h2.step(4)
+        assert np.isfinite(h2.positions()).all()
