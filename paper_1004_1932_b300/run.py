@@ -51,6 +51,8 @@ def main(argv=None):
             h.set_noise(a.kT, a.seed)
         if a.shape > 0:
             import time
+            if a.path == "coop":          # shape-driven: grid (default) or cooperative path
+                h.set_path("coop")
             h.set_dynamics("shape", a.shape)
             h.step(8)
             h.sync()
@@ -59,7 +61,7 @@ def main(argv=None):
             h.sync()
             el = time.perf_counter() - t0
             print(json.dumps({"S": a.S, "N": N, "mobility": a.mobility, "precision": a.precision,
-                              "dynamics": "shape", "iterations": a.shape,
+                              "dynamics": "shape", "iterations": a.shape, "path": h.get_path()[0],
                               "ms_per_step": 1e3 * el / a.steps,
                               "pair_sums_per_step": 2 * a.shape}))
             return
