@@ -845,8 +845,12 @@ __global__ void __launch_bounds__(SA_NT, 1) sa_flow_kernel(const SaArgs A, const
                            sac_bit(P.base + (unsigned)ev + 1u));
             }
         }
-        // no barrier here: the next poll writes only records this CTA does not own,
-        // and the next sweep reads the own records after the poll's barrier
+        // The other warps wait here for the axis warps' epilogue: started at once,
+        // their polls ran ahead of this CTA's own publish and every evaluation took
+        // longer (S = 128 / 512 / 1024: 4.6-4.8 / 7.7 / 13.0 us per averaged step
+        // without this barrier, 3.8-3.9 / 5.3-5.4 / 11.2 with it, measured).  The
+        // next poll writes only records this CTA does not own.
+        __syncthreads();
     }
     state_update();
     __syncthreads();

@@ -195,6 +195,10 @@ __global__ void __launch_bounds__(FLOW_NT, 1) sd_flow_kernel(const EvalArgs A, c
         const bool last = (e % M) == M - 1;        // last iteration at this point
         const int64_t n = P.n0 + ev / (2 * M);
         const ulonglong2 *R = P.rec + (size_t)par * Spad * 3;
+        // (sin, cos)(w t_{n+1}) for the last iteration's placement, loaded while the
+        // records are on their way
+        float4 tr1 = make_float4(0.f, 0.f, 1.f, 0.f);
+        if (ep && last) tr1 = A.trig_df[(n + 1) & A.trig_mask];
 
         // 1. poll the records this CTA does not own (as flow_kernel)
         bool ok = true;
@@ -321,7 +325,7 @@ __global__ void __launch_bounds__(FLOW_NT, 1) sd_flow_kernel(const EvalArgs A, c
                 }
                 if (corr) hn = n;   // the double-single update of step n runs in the next poll
                 const float inv = rsqrtf(fmaf(Nn[0], Nn[0], fmaf(Nn[1], Nn[1], Nn[2] * Nn[2])));
-                const float4 tr = A.trig_df[(n + 1) & A.trig_mask];
+                const float4 tr = tr1;
                 const float lam = own.lam[d], sp = own.sph[d], cp = own.cph[d];
                 const float L1 = ellf + lam * fmaf(tr.x, cp, tr.z * sp);
                 const float Ld1 = lam * omf * fmaf(tr.z, cp, -tr.x * sp);
@@ -353,8 +357,12 @@ __global__ void __launch_bounds__(FLOW_NT, 1) sd_flow_kernel(const EvalArgs A, c
                             flow_bit(P.base + (unsigned)ev + 1u));
             }
         }
-        // no barrier here: the next poll writes only records this CTA does not own,
-        // and the next sweep reads the own records after the poll's barrier
+        // The other warps wait here for warp 0's epilogue: started at once, their
+        // polls ran ahead of this CTA's own publish, and every pair sum took longer
+        // (S = 128 / 512, 2 iterations: 12.7 / 17.2 us per Heun step without this
+        // barrier, 7.6 / 14.1 with it; with the clock prefetched above as well 7.0 /
+        // 10.7, measured).  The next poll writes only records this CTA does not own.
+        __syncthreads();
     }
 
     // ---- the FP64 state: R and N from their pairs (N renormalised in FP64), the
