@@ -319,8 +319,12 @@ __global__ void __launch_bounds__(FLOW64_NT, 1) flow64_kernel(const EvalArgs A, 
                 if (corr) hn = n;   // its stroke average runs in the next poll's gap
             }
         }
-        // no barrier here: the next poll writes only records this CTA does not own,
-        // and the next sweep reads the own records after the poll's barrier
+        // The other warps wait here for warp 0's epilogue: started at once, their
+        // polls ran ahead of this CTA's own publish and every evaluation took longer
+        // (S = 16 / 64 / 148: 7.3-7.7 / 9.6-10.5 / 15.7-16.2 us per Heun step without
+        // this barrier, 6.8 / 8.5 / 13.6 with it, measured).  The next poll writes
+        // only records this CTA does not own.
+        __syncthreads();
     }
 
     // ---- write the owned state back ----------------------------------------------
