@@ -138,20 +138,21 @@ __device__ __forceinline__ void sa_pair(bool self, T Rx, T Ry, T Rz, T lam_s, T 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
 
-__device__ __forceinline__ void sa_pair2(bool self0, bool self1, float2 Rx, float2 Ry, float2 Rz, float2 lam_s,
-                                         float2 Nx, float2 Ny, float2 Nz, float2 sn_s, float2 cs_s,
-                                         const SaRecF32 &q0, const SaRecF32 &q1, float2 J[4], float2 K[3])
+__device__ __forceinline__ void sa_pair2f(bool self0, bool self1, float2 Rx, float2 Ry, float2 Rz, float2 lam_s,
+                                          float2 Nx, float2 Ny, float2 Nz, float2 sn_s, float2 cs_s,
+                                          float2 qRx, float2 qRy, float2 qRz, float2 qlam, float2 qNx,
+                                          float2 qNy, float2 qNz, float2 qsn, float2 qcs, float2 J[4],
+                                          float2 K[3])
 {
     const float2 m1 = f2s(-1.f);
-    const float2 Dx = __ffma2_rn(f2(q0.R.x, q1.R.x), m1, Rx);
-    const float2 Dy = __ffma2_rn(f2(q0.R.y, q1.R.y), m1, Ry);
-    const float2 Dz = __ffma2_rn(f2(q0.R.z, q1.R.z), m1, Rz);
+    const float2 Dx = __ffma2_rn(qRx, m1, Rx);
+    const float2 Dy = __ffma2_rn(qRy, m1, Ry);
+    const float2 Dz = __ffma2_rn(qRz, m1, Rz);
     float2 D2 = __fmul2_rn(Dx, Dx);
     D2 = __ffma2_rn(Dy, Dy, D2);
     D2 = __ffma2_rn(Dz, Dz, D2);
     const float2 w = f2(self0 ? 0.f : rsqrtf(D2.x), self1 ? 0.f : rsqrtf(D2.y));
     const float2 hx = __fmul2_rn(Dx, w), hy = __fmul2_rn(Dy, w), hz = __fmul2_rn(Dz, w);
-    const float2 qNx = f2(q0.N.x, q1.N.x), qNy = f2(q0.N.y, q1.N.y), qNz = f2(q0.N.z, q1.N.z);
     float2 s = __fmul2_rn(hx, Nx);
     s = __ffma2_rn(hy, Ny, s);
     s = __ffma2_rn(hz, Nz, s);
@@ -162,8 +163,8 @@ __device__ __forceinline__ void sa_pair2(bool self0, bool self1, float2 Rx, floa
     qq = __ffma2_rn(Ny, qNy, qq);
     qq = __ffma2_rn(Nz, qNz, qq);
     // sin(phi^s - phi^r) = sin phi^s cos phi^r - cos phi^s sin phi^r
-    const float2 sd = __ffma2_rn(sn_s, f2(q0.sc.y, q1.sc.y), __fmul2_rn(__fmul2_rn(cs_s, m1), f2(q0.sc.x, q1.sc.x)));
-    const float2 amp = __fmul2_rn(__fmul2_rn(lam_s, f2(q0.R.w, q1.R.w)), sd);
+    const float2 sd = __ffma2_rn(sn_s, qcs, __fmul2_rn(__fmul2_rn(cs_s, m1), qsn));
+    const float2 amp = __fmul2_rn(__fmul2_rn(lam_s, qlam), sd);
     const float2 w2 = __fmul2_rn(w, w);
     const float2 w4 = __fmul2_rn(w2, w2);
     const float2 s2 = __fmul2_rn(s, s), r2 = __fmul2_rn(r, r);
@@ -193,6 +194,31 @@ __device__ __forceinline__ void sa_pair2(bool self0, bool self1, float2 Rx, floa
     K[0] = __ffma2_rn(ck, hx, K[0]);
     K[1] = __ffma2_rn(ck, hy, K[1]);
     K[2] = __ffma2_rn(ck, hz, K[2]);
+}
+
+// the pair term for two source records q0 (lane .x) and q1 (lane .y)
+__device__ __forceinline__ void sa_pair2(bool self0, bool self1, float2 Rx, float2 Ry, float2 Rz, float2 lam_s,
+                                         float2 Nx, float2 Ny, float2 Nz, float2 sn_s, float2 cs_s,
+                                         const SaRecF32 &q0, const SaRecF32 &q1, float2 J[4], float2 K[3])
+{
+    sa_pair2f(self0, self1, Rx, Ry, Rz, lam_s, Nx, Ny, Nz, sn_s, cs_s, f2(q0.R.x, q1.R.x), f2(q0.R.y, q1.R.y),
+              f2(q0.R.z, q1.R.z), f2(q0.R.w, q1.R.w), f2(q0.N.x, q1.N.x), f2(q0.N.y, q1.N.y), f2(q0.N.z, q1.N.z),
+              f2(q0.sc.x, q1.sc.x), f2(q0.sc.y, q1.sc.y), J, K);
+}
+
+// Two source records stored pair-interleaved (record k in lanes .x, record
+// k + NSL in .y of every field), so that the paired operands load as they are:
+// a = (Rx, Ry), b = (Rz, lambda), c = (Nx, Ny), d = (Nz, sin phi), e = (cos phi, -).
+struct __align__(16) SaPairF32 {
+    float4 a, b, c, d, e;
+};
+__device__ __forceinline__ void sa_pair2(bool self0, bool self1, float2 Rx, float2 Ry, float2 Rz, float2 lam_s,
+                                         float2 Nx, float2 Ny, float2 Nz, float2 sn_s, float2 cs_s,
+                                         const SaPairF32 &q, float2 J[4], float2 K[3])
+{
+    const float4 a = q.a, b = q.b, c = q.c, d = q.d, e = q.e;
+    sa_pair2f(self0, self1, Rx, Ry, Rz, lam_s, Nx, Ny, Nz, sn_s, cs_s, f2(a.x, a.y), f2(a.z, a.w), f2(b.x, b.y),
+              f2(b.z, b.w), f2(c.x, c.y), f2(c.z, c.w), f2(d.x, d.y), f2(d.z, d.w), f2(e.x, e.y), J, K);
 }
 
 // (s, c) += (s2, c2): FP32 with Knuth's two-sum on the sums, FP64 plain sums.
@@ -357,22 +383,45 @@ __global__ void __launch_bounds__(SA_NT) sa_eval_kernel(SaArgs A)
     // Slots 0-2: the pD part of J, 3-5: K, 6: sum of cj pN, 7: empty (for the
     // transposing fold).
     T fs[8] = {0, 0, 0, 0, 0, 0, 0, 0}, fc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // FP32 with TL >= 4: two records per paired call (with TL <= 2 a thread holds at
+    // most two records of a tile, and the paired code would only cost registers),
+    // the tile stored pair-interleaved so that the paired operands load as they are
+    constexpr bool PAIRED = sizeof(T) == 4 && TL >= 4;
+    SaPairF32 *ptile = reinterpret_cast<SaPairF32 *>(tile);   // TILE / 2 pairs of 80 bytes
     for (int64_t t0 = 0; t0 < A.S; t0 += TILE) {
         const int len = (int)min((int64_t)TILE, A.S - t0);
+        // records k and k + NSL (k mod 2 NSL < NSL) share pair (k div 2 NSL) NSL + k mod NSL;
+        // the records past the tile's end up to a whole group of 2 NSL are zero-amplitude
+        // stand-ins far away, whose terms are exactly zero
+        const int kmax = PAIRED ? (len + 2 * NSL - 1) / (2 * NSL) * (2 * NSL) : len;
         __syncthreads();
-        for (int k = tid; k < len; k += SA_NT) tile[k] = in[t0 + k];
+        if constexpr (PAIRED) {
+            for (int k = tid; k < kmax; k += SA_NT) {
+                const int i = k / (2 * NSL), r = k - i * 2 * NSL, h = r / NSL;
+                float *f = (float *)(ptile + i * NSL + (r - h * NSL));
+                if (k < len) {
+                    const Rec q = in[t0 + k];
+                    f[h] = q.R.x; f[2 + h] = q.R.y; f[4 + h] = q.R.z; f[6 + h] = q.R.w;
+                    f[8 + h] = q.N.x; f[10 + h] = q.N.y; f[12 + h] = q.N.z; f[14 + h] = q.sc.x;
+                    f[16 + h] = q.sc.y;
+                } else {
+                    f[h] = 1.0e18f; f[2 + h] = 1.0e18f; f[4 + h] = 1.0e18f; f[6 + h] = 0.f;
+                    f[8 + h] = 1.f; f[10 + h] = 0.f; f[12 + h] = 0.f; f[14 + h] = 0.f; f[16 + h] = 0.f;
+                }
+            }
+        } else {
+            for (int k = tid; k < len; k += SA_NT) tile[k] = in[t0 + k];
+        }
         __syncthreads();
         T J[4] = {0, 0, 0, 0}, K[3] = {0, 0, 0};
         if (act) {
             int k = sl;
-            // two records per paired call (FP32; with TL <= 2 a thread holds at most
-            // two records of a tile, and the paired code would only cost registers)
-            if constexpr (sizeof(T) == 4 && TL >= 4) {
+            if constexpr (PAIRED) {
                 float2 J2[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
                 float2 K2[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-                for (; k + NSL < len; k += 2 * NSL)
+                for (; k < kmax; k += 2 * NSL)
                     sa_pair2(t0 + k == st, t0 + k + NSL == st, f2s(Rx), f2s(Ry), f2s(Rz), f2s(lam), f2s(Nx),
-                             f2s(Ny), f2s(Nz), f2s(sn), f2s(cs), tile[k], tile[k + NSL], J2, K2);
+                             f2s(Ny), f2s(Nz), f2s(sn), f2s(cs), ptile[(k / (2 * NSL)) * NSL + sl], J2, K2);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     sa_merge(fs[c], fc[c], J2[c].x, T(0));
