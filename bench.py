@@ -39,9 +39,9 @@ STEPS_PER_PERIOD = 1000
 SA_STEPS_PER_PERIOD = 10
 FLOPS_PER_PAIR = {"oseen": 27, "rpy": 34}   # algorithmic FP32 flops (FMA = 2), rsqrt not counted
 # the stroke-averaged pair term (Eqs. (9b), (9c)) as the kernel evaluates it: the
-# difference vector, its norm, three projections, the phase factor and the three
+# difference vector, its norm, three projections, the amplitude-phase product and the three
 # polynomials, the J and K updates; FMA = 2, rsqrt not counted
-SA_FLOPS_PER_PAIR = 98
+SA_FLOPS_PER_PAIR = 96
 # DRAM bytes (read + write) per launch of the dominant kernel, copied from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the same launch:
 # the cooperative kernel, 1024 Heun steps, S = 512, RPY (null for any other path

@@ -36,20 +36,21 @@ using namespace dbs;
 namespace {
 
 constexpr int SA_NT = 256;    // threads per CTA
-// source records per shared-memory tile: 24 KB either way (one tile holds a
+// source records per shared-memory tile: 16 KB either way (one tile holds a
 // 512-dumbbell suspension in FP32)
 template <typename T> __host__ __device__ constexpr int sa_tile() { return sizeof(T) == 4 ? 512 : 256; }
 thread_local char g_sa_create_error[256] = "";
 
+// Amplitude and phase enter the pair term only through lam^s lam^r sin(phi^s -
+// phi^r) = (lam sin phi)^s (lam cos phi)^r - (lam cos phi)^s (lam sin phi)^r, so a
+// record carries the two products (formed in FP64, then rounded).
 struct __align__(16) SaRecF32 {
-    float4 R;   // centre - c, amplitude lambda
-    float4 N;   // orientation, 0
-    float4 sc;  // sin phi, cos phi, 0, 0
+    float4 R;   // centre - c, lam sin phi
+    float4 N;   // orientation, lam cos phi
 };
 struct __align__(16) SaRecF64 {
-    double Rx, Ry, Rz, lam;
-    double Nx, Ny, Nz, pad;
-    double sn, cs, pad2, pad3;
+    double Rx, Ry, Rz, ls;   // centre - c, lam sin phi
+    double Nx, Ny, Nz, lc;   // orientation, lam cos phi
 };
 
 struct SaArgs {
@@ -74,32 +75,32 @@ __device__ __forceinline__ void store_rec(SaRecF32 *o, int64_t s, const double R
                                           const SaArgs &A)
 {
     SaRecF32 r;
-    r.R = make_float4((float)(R[0] - A.cx), (float)(R[1] - A.cy), (float)(R[2] - A.cz), (float)A.lam[s]);
-    r.N = make_float4((float)N[0], (float)N[1], (float)N[2], 0.f);
-    r.sc = make_float4((float)A.sinp[s], (float)A.cosp[s], 0.f, 0.f);
+    r.R = make_float4((float)(R[0] - A.cx), (float)(R[1] - A.cy), (float)(R[2] - A.cz),
+                      (float)(A.lam[s] * A.sinp[s]));
+    r.N = make_float4((float)N[0], (float)N[1], (float)N[2], (float)(A.lam[s] * A.cosp[s]));
     o[s] = r;
 }
 __device__ __forceinline__ void store_rec(SaRecF64 *o, int64_t s, const double R[3], const double N[3],
                                           const SaArgs &A)
 {
     SaRecF64 r;
-    r.Rx = R[0] - A.cx; r.Ry = R[1] - A.cy; r.Rz = R[2] - A.cz; r.lam = A.lam[s];
-    r.Nx = N[0]; r.Ny = N[1]; r.Nz = N[2]; r.pad = 0;
-    r.sn = A.sinp[s]; r.cs = A.cosp[s]; r.pad2 = 0; r.pad3 = 0;
+    r.Rx = R[0] - A.cx; r.Ry = R[1] - A.cy; r.Rz = R[2] - A.cz; r.ls = A.lam[s] * A.sinp[s];
+    r.Nx = N[0]; r.Ny = N[1]; r.Nz = N[2]; r.lc = A.lam[s] * A.cosp[s];
     o[s] = r;
 }
 
+// Target s: centre R, orientation N, ls_s = lam sin phi, mlc_s = -lam cos phi.
 template <typename T, typename Rec>
-__device__ __forceinline__ void sa_pair(bool self, T Rx, T Ry, T Rz, T lam_s, T Nx, T Ny, T Nz,
-                                        T sn_s, T cs_s, const Rec &q, T J[4], T K[3])
+__device__ __forceinline__ void sa_pair(bool self, T Rx, T Ry, T Rz, T ls_s, T Nx, T Ny, T Nz,
+                                        T mlc_s, const Rec &q, T J[4], T K[3])
 {
-    T qRx, qRy, qRz, qlam, qNx, qNy, qNz, qsn, qcs;
+    T qRx, qRy, qRz, qls, qNx, qNy, qNz, qlc;
     if constexpr (sizeof(T) == 4) {
-        qRx = q.R.x; qRy = q.R.y; qRz = q.R.z; qlam = q.R.w;
-        qNx = q.N.x; qNy = q.N.y; qNz = q.N.z; qsn = q.sc.x; qcs = q.sc.y;
+        qRx = q.R.x; qRy = q.R.y; qRz = q.R.z; qls = q.R.w;
+        qNx = q.N.x; qNy = q.N.y; qNz = q.N.z; qlc = q.N.w;
     } else {
-        qRx = q.Rx; qRy = q.Ry; qRz = q.Rz; qlam = q.lam;
-        qNx = q.Nx; qNy = q.Ny; qNz = q.Nz; qsn = q.sn; qcs = q.cs;
+        qRx = q.Rx; qRy = q.Ry; qRz = q.Rz; qls = q.ls;
+        qNx = q.Nx; qNy = q.Ny; qNz = q.Nz; qlc = q.lc;
     }
     T Dx = Rx - qRx, Dy = Ry - qRy, Dz = Rz - qRz;
     T D2 = Dx * Dx + Dy * Dy + Dz * Dz;
@@ -110,8 +111,7 @@ __device__ __forceinline__ void sa_pair(bool self, T Rx, T Ry, T Rz, T lam_s, T 
     T s = hx * Nx + hy * Ny + hz * Nz;
     T r = hx * qNx + hy * qNy + hz * qNz;
     T qq = Nx * qNx + Ny * qNy + Nz * qNz;
-    T sd = sn_s * qcs - cs_s * qsn;          // sin(phi^s - phi^r)
-    T amp = lam_s * qlam * sd;
+    T amp = ls_s * qlc + mlc_s * qls;        // lam^s lam^r sin(phi^s - phi^r)
     T w2 = w * w;
     T w4 = w2 * w2;
     T s2 = s * s, r2 = r * r, qr = qq * r, s2r2 = s2 * r2;
@@ -138,11 +138,10 @@ __device__ __forceinline__ void sa_pair(bool self, T Rx, T Ry, T Rz, T lam_s, T 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
 
-__device__ __forceinline__ void sa_pair2f(bool self0, bool self1, float2 Rx, float2 Ry, float2 Rz, float2 lam_s,
-                                          float2 Nx, float2 Ny, float2 Nz, float2 sn_s, float2 cs_s,
-                                          float2 qRx, float2 qRy, float2 qRz, float2 qlam, float2 qNx,
-                                          float2 qNy, float2 qNz, float2 qsn, float2 qcs, float2 J[4],
-                                          float2 K[3])
+__device__ __forceinline__ void sa_pair2f(bool self0, bool self1, float2 Rx, float2 Ry, float2 Rz, float2 ls_s,
+                                          float2 Nx, float2 Ny, float2 Nz, float2 mlc_s, float2 qRx,
+                                          float2 qRy, float2 qRz, float2 qls, float2 qNx, float2 qNy,
+                                          float2 qNz, float2 qlc, float2 J[4], float2 K[3])
 {
     const float2 m1 = f2s(-1.f);
     const float2 Dx = __ffma2_rn(qRx, m1, Rx);
@@ -162,9 +161,8 @@ __device__ __forceinline__ void sa_pair2f(bool self0, bool self1, float2 Rx, flo
     float2 qq = __fmul2_rn(Nx, qNx);
     qq = __ffma2_rn(Ny, qNy, qq);
     qq = __ffma2_rn(Nz, qNz, qq);
-    // sin(phi^s - phi^r) = sin phi^s cos phi^r - cos phi^s sin phi^r
-    const float2 sd = __ffma2_rn(sn_s, qcs, __fmul2_rn(__fmul2_rn(cs_s, m1), qsn));
-    const float2 amp = __fmul2_rn(__fmul2_rn(lam_s, qlam), sd);
+    // lam^s lam^r sin(phi^s - phi^r)
+    const float2 amp = __ffma2_rn(ls_s, qlc, __fmul2_rn(mlc_s, qls));
     const float2 w2 = __fmul2_rn(w, w);
     const float2 w4 = __fmul2_rn(w2, w2);
     const float2 s2 = __fmul2_rn(s, s), r2 = __fmul2_rn(r, r);
@@ -196,29 +194,52 @@ __device__ __forceinline__ void sa_pair2f(bool self0, bool self1, float2 Rx, flo
     K[2] = __ffma2_rn(ck, hz, K[2]);
 }
 
-// the pair term for two source records q0 (lane .x) and q1 (lane .y)
-__device__ __forceinline__ void sa_pair2(bool self0, bool self1, float2 Rx, float2 Ry, float2 Rz, float2 lam_s,
-                                         float2 Nx, float2 Ny, float2 Nz, float2 sn_s, float2 cs_s,
-                                         const SaRecF32 &q0, const SaRecF32 &q1, float2 J[4], float2 K[3])
-{
-    sa_pair2f(self0, self1, Rx, Ry, Rz, lam_s, Nx, Ny, Nz, sn_s, cs_s, f2(q0.R.x, q1.R.x), f2(q0.R.y, q1.R.y),
-              f2(q0.R.z, q1.R.z), f2(q0.R.w, q1.R.w), f2(q0.N.x, q1.N.x), f2(q0.N.y, q1.N.y), f2(q0.N.z, q1.N.z),
-              f2(q0.sc.x, q1.sc.x), f2(q0.sc.y, q1.sc.y), J, K);
-}
-
 // Two source records stored pair-interleaved (record k in lanes .x, record
 // k + NSL in .y of every field), so that the paired operands load as they are:
-// a = (Rx, Ry), b = (Rz, lambda), c = (Nx, Ny), d = (Nz, sin phi), e = (cos phi, -).
+// a = (Rx, Ry), b = (Rz, lam sin phi), c = (Nx, Ny), d = (Nz, lam cos phi); in
+// sa_eval_kernel's shared memory each of a, b, c, d is a plane of its own.
 struct __align__(16) SaPairF32 {
-    float4 a, b, c, d, e;
+    float4 a, b, c, d;
 };
-__device__ __forceinline__ void sa_pair2(bool self0, bool self1, float2 Rx, float2 Ry, float2 Rz, float2 lam_s,
-                                         float2 Nx, float2 Ny, float2 Nz, float2 sn_s, float2 cs_s,
-                                         const SaPairF32 &q, float2 J[4], float2 K[3])
+__device__ __forceinline__ void sa_pair2(bool self0, bool self1, float2 Rx, float2 Ry, float2 Rz, float2 ls_s,
+                                         float2 Nx, float2 Ny, float2 Nz, float2 mlc_s, const SaPairF32 &q,
+                                         float2 J[4], float2 K[3])
 {
-    const float4 a = q.a, b = q.b, c = q.c, d = q.d, e = q.e;
-    sa_pair2f(self0, self1, Rx, Ry, Rz, lam_s, Nx, Ny, Nz, sn_s, cs_s, f2(a.x, a.y), f2(a.z, a.w), f2(b.x, b.y),
-              f2(b.z, b.w), f2(c.x, c.y), f2(c.z, c.w), f2(d.x, d.y), f2(d.z, d.w), f2(e.x, e.y), J, K);
+    const float4 a = q.a, b = q.b, c = q.c, d = q.d;
+    sa_pair2f(self0, self1, Rx, Ry, Rz, ls_s, Nx, Ny, Nz, mlc_s, f2(a.x, a.y), f2(a.z, a.w), f2(b.x, b.y),
+              f2(b.z, b.w), f2(c.x, c.y), f2(c.z, c.w), f2(d.x, d.y), f2(d.z, d.w), J, K);
+}
+
+// Records in shared memory as planes of 16-byte fields (FP32: R[k], N[k]; FP64:
+// (Rx, Ry), (Rz, ls), (Nx, Ny), (Nz, lc)), so that the 16-byte loads of
+// consecutive records by consecutive lanes hit distinct banks (a 32- or 64-byte
+// record stride puts two or four lanes of each quarter-warp on the same banks).
+// NP: records per plane.
+template <int NP>
+__device__ __forceinline__ void sa_tile_put(float4 *tb, int k, const SaRecF32 &q)
+{
+    tb[k] = q.R;
+    tb[NP + k] = q.N;
+}
+template <int NP>
+__device__ __forceinline__ void sa_tile_put(float4 *tb, int k, const SaRecF64 &q)
+{
+    double2 *d = reinterpret_cast<double2 *>(tb);
+    d[k] = make_double2(q.Rx, q.Ry);
+    d[NP + k] = make_double2(q.Rz, q.ls);
+    d[2 * NP + k] = make_double2(q.Nx, q.Ny);
+    d[3 * NP + k] = make_double2(q.Nz, q.lc);
+}
+template <typename Rec, int NP>
+__device__ __forceinline__ Rec sa_tile_get(const float4 *tb, int k)
+{
+    if constexpr (sizeof(Rec) == sizeof(SaRecF32)) {
+        return Rec{tb[k], tb[NP + k]};
+    } else {
+        const double2 *d = reinterpret_cast<const double2 *>(tb);
+        const double2 a = d[k], b = d[NP + k], c = d[2 * NP + k], e = d[3 * NP + k];
+        return Rec{a.x, a.y, b.x, b.y, c.x, c.y, e.x, e.y};
+    }
 }
 
 // (s, c) += (s2, c2): FP32 with Knuth's two-sum on the sums, FP64 plain sums.
@@ -294,12 +315,8 @@ __device__ __forceinline__ void store_rec_axis(SaRecF32 *o, int64_t s, int a, do
     f[a] = (float)(R - (a == 0 ? A.cx : (a == 1 ? A.cy : A.cz)));
     f[4 + a] = (float)N;
     if (a == 0) {
-        f[3] = (float)A.lam[s];
-        f[7] = 0.f;
-        f[8] = (float)A.sinp[s];
-        f[9] = (float)A.cosp[s];
-        f[10] = 0.f;
-        f[11] = 0.f;
+        f[3] = (float)(A.lam[s] * A.sinp[s]);
+        f[7] = (float)(A.lam[s] * A.cosp[s]);
     }
 }
 __device__ __forceinline__ void store_rec_axis(SaRecF64 *o, int64_t s, int a, double R, double N,
@@ -309,12 +326,8 @@ __device__ __forceinline__ void store_rec_axis(SaRecF64 *o, int64_t s, int a, do
     f[a] = R - (a == 0 ? A.cx : (a == 1 ? A.cy : A.cz));
     f[4 + a] = N;
     if (a == 0) {
-        f[3] = A.lam[s];
-        f[7] = 0.0;
-        f[8] = A.sinp[s];
-        f[9] = A.cosp[s];
-        f[10] = 0.0;
-        f[11] = 0.0;
+        f[3] = A.lam[s] * A.sinp[s];
+        f[7] = A.lam[s] * A.cosp[s];
     }
 }
 
@@ -333,7 +346,7 @@ __global__ void __launch_bounds__(SA_NT) sa_eval_kernel(SaArgs A)
     constexpr int LW = NSL < 32 ? NSL : 32;       // lanes of a target within a warp
     constexpr int WPT = NSL > 32 ? NSL / 32 : 1;  // warps per target
     constexpr int TILE = sa_tile<T>();
-    __shared__ Rec tile[TILE];
+    __shared__ float4 tile[TILE * sizeof(Rec) / sizeof(float4)];   // planes, see sa_tile_put
     // per row: the pD part of J (sums 0-2, compensations 3-5), K (6-8, 9-11) and
     // the sum of cj pN (12, 13)
     __shared__ T red[WPT == 1 ? TL : SA_NT / 32][14];
@@ -371,13 +384,13 @@ __global__ void __launch_bounds__(SA_NT) sa_eval_kernel(SaArgs A)
     const Rec *in = (const Rec *)A.rec_in;
     Rec me{};
     if (act) me = in[st];
-    T Rx, Ry, Rz, lam, Nx, Ny, Nz, sn, cs;
+    T Rx, Ry, Rz, ls, Nx, Ny, Nz, mlc;
     if constexpr (sizeof(T) == 4) {
-        Rx = me.R.x; Ry = me.R.y; Rz = me.R.z; lam = me.R.w;
-        Nx = me.N.x; Ny = me.N.y; Nz = me.N.z; sn = me.sc.x; cs = me.sc.y;
+        Rx = me.R.x; Ry = me.R.y; Rz = me.R.z; ls = me.R.w;
+        Nx = me.N.x; Ny = me.N.y; Nz = me.N.z; mlc = -me.N.w;
     } else {
-        Rx = me.Rx; Ry = me.Ry; Rz = me.Rz; lam = me.lam;
-        Nx = me.Nx; Ny = me.Ny; Nz = me.Nz; sn = me.sn; cs = me.cs;
+        Rx = me.Rx; Ry = me.Ry; Rz = me.Rz; ls = me.ls;
+        Nx = me.Nx; Ny = me.Ny; Nz = me.Nz; mlc = -me.lc;
     }
     // FP32: per-tile FP32 sums folded into (sum, compensation); FP64: plain sums.
     // Slots 0-2: the pD part of J, 3-5: K, 6: sum of cj pN, 7: empty (for the
@@ -385,9 +398,10 @@ __global__ void __launch_bounds__(SA_NT) sa_eval_kernel(SaArgs A)
     T fs[8] = {0, 0, 0, 0, 0, 0, 0, 0}, fc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     // FP32 with TL >= 4: two records per paired call (with TL <= 2 a thread holds at
     // most two records of a tile, and the paired code would only cost registers),
-    // the tile stored pair-interleaved so that the paired operands load as they are
+    // the tile stored pair-interleaved (TILE / 2 pairs: four planes a, b, c, d of
+    // TILE / 2 float4) so that the paired operands load as they are
     constexpr bool PAIRED = sizeof(T) == 4 && TL >= 4;
-    SaPairF32 *ptile = reinterpret_cast<SaPairF32 *>(tile);   // TILE / 2 pairs of 80 bytes
+    constexpr int PH = TILE / 2;
     for (int64_t t0 = 0; t0 < A.S; t0 += TILE) {
         const int len = (int)min((int64_t)TILE, A.S - t0);
         // records k and k + NSL (k mod 2 NSL < NSL) share pair (k div 2 NSL) NSL + k mod NSL;
@@ -398,19 +412,20 @@ __global__ void __launch_bounds__(SA_NT) sa_eval_kernel(SaArgs A)
         if constexpr (PAIRED) {
             for (int k = tid; k < kmax; k += SA_NT) {
                 const int i = k / (2 * NSL), r = k - i * 2 * NSL, h = r / NSL;
-                float *f = (float *)(ptile + i * NSL + (r - h * NSL));
+                const int p = i * NSL + (r - h * NSL);
+                float *fa = (float *)(tile + p), *fb = (float *)(tile + PH + p);
+                float *fc = (float *)(tile + 2 * PH + p), *fd = (float *)(tile + 3 * PH + p);
                 if (k < len) {
                     const Rec q = in[t0 + k];
-                    f[h] = q.R.x; f[2 + h] = q.R.y; f[4 + h] = q.R.z; f[6 + h] = q.R.w;
-                    f[8 + h] = q.N.x; f[10 + h] = q.N.y; f[12 + h] = q.N.z; f[14 + h] = q.sc.x;
-                    f[16 + h] = q.sc.y;
+                    fa[h] = q.R.x; fa[2 + h] = q.R.y; fb[h] = q.R.z; fb[2 + h] = q.R.w;
+                    fc[h] = q.N.x; fc[2 + h] = q.N.y; fd[h] = q.N.z; fd[2 + h] = q.N.w;
                 } else {
-                    f[h] = 1.0e18f; f[2 + h] = 1.0e18f; f[4 + h] = 1.0e18f; f[6 + h] = 0.f;
-                    f[8 + h] = 1.f; f[10 + h] = 0.f; f[12 + h] = 0.f; f[14 + h] = 0.f; f[16 + h] = 0.f;
+                    fa[h] = 1.0e18f; fa[2 + h] = 1.0e18f; fb[h] = 1.0e18f; fb[2 + h] = 0.f;
+                    fc[h] = 1.f; fc[2 + h] = 0.f; fd[h] = 0.f; fd[2 + h] = 0.f;
                 }
             }
         } else {
-            for (int k = tid; k < len; k += SA_NT) tile[k] = in[t0 + k];
+            for (int k = tid; k < len; k += SA_NT) sa_tile_put<TILE>(tile, k, in[t0 + k]);
         }
         __syncthreads();
         T J[4] = {0, 0, 0, 0}, K[3] = {0, 0, 0};
@@ -419,9 +434,12 @@ __global__ void __launch_bounds__(SA_NT) sa_eval_kernel(SaArgs A)
             if constexpr (PAIRED) {
                 float2 J2[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
                 float2 K2[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-                for (; k < kmax; k += 2 * NSL)
-                    sa_pair2(t0 + k == st, t0 + k + NSL == st, f2s(Rx), f2s(Ry), f2s(Rz), f2s(lam), f2s(Nx),
-                             f2s(Ny), f2s(Nz), f2s(sn), f2s(cs), ptile[(k / (2 * NSL)) * NSL + sl], J2, K2);
+                for (; k < kmax; k += 2 * NSL) {
+                    const int p = (k / (2 * NSL)) * NSL + sl;
+                    const SaPairF32 q{tile[p], tile[PH + p], tile[2 * PH + p], tile[3 * PH + p]};
+                    sa_pair2(t0 + k == st, t0 + k + NSL == st, f2s(Rx), f2s(Ry), f2s(Rz), f2s(ls), f2s(Nx),
+                             f2s(Ny), f2s(Nz), f2s(mlc), q, J2, K2);
+                }
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     sa_merge(fs[c], fc[c], J2[c].x, T(0));
@@ -433,7 +451,8 @@ __global__ void __launch_bounds__(SA_NT) sa_eval_kernel(SaArgs A)
                 sa_merge(fs[6], fc[6], J2[3].y, T(0));
             }
             for (; k < len; k += NSL)
-                sa_pair<T, Rec>(t0 + k == st, Rx, Ry, Rz, lam, Nx, Ny, Nz, sn, cs, tile[k], J, K);
+                sa_pair<T, Rec>(t0 + k == st, Rx, Ry, Rz, ls, Nx, Ny, Nz, mlc, sa_tile_get<Rec, TILE>(tile, k),
+                                J, K);
         }
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -561,6 +580,17 @@ constexpr int SAF_TIMEOUT = 4, SAF_LAUNCH = 8;
 constexpr int kSaCoopUnroll = DBS_SA_COOP_UNROLL;   // paired calls in flight per thread in the sweep
 constexpr int SAC_CHUNK = 512;     // records per compensated partial sum (as sa_eval_kernel's tile)
 constexpr int SAC_POLL = 8;        // words per thread and round of a poll
+// Records of the cooperative kernel's shared-memory tile: Spad rounded up to a
+// whole group of 2 (256 / TL) records (the paired sweep's stand-ins), 48 bytes
+// each (R with lam sin phi, N with lam cos phi, 16 bytes unused).  Measured
+// against a pair-interleaved tile of four 16-byte planes (as sa_eval_kernel's)
+// and records as two 16-byte planes R[s], N[s]: S = 512 4.95 / 5.44 / 5.53,
+// S = 1024 10.0 / 10.9 / 11.1, S = 4096 84.9 / 85.1 / 89.7 us per averaged step.
+constexpr int SAC_REC = 48;
+__host__ __device__ constexpr int sac_records(int Spad, int TL)
+{
+    return (Spad + 512 / TL - 1) / (512 / TL) * (512 / TL);
+}
 
 struct SaFlowArgs {
     unsigned long long *words;     // [2][Spad][3]
@@ -633,7 +663,7 @@ __global__ void __launch_bounds__(SA_NT, 1) sa_flow_kernel(const SaArgs A, const
     constexpr int NSL = SA_NT / TL;
     constexpr int LW = NSL < 32 ? NSL : 32;
     constexpr int WPT = NSL > 32 ? NSL / 32 : 1;
-    extern __shared__ float4 sac_smem[];          // all records, SaRecF32
+    extern __shared__ float4 sac_smem[];          // all records, 3 float4 each (SAC_REC)
     __shared__ SaOwn<TL> own;
     __shared__ float red[WPT == 1 ? TL : SA_NT / 32][14];   // as in sa_eval_kernel
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -641,7 +671,9 @@ __global__ void __launch_bounds__(SA_NT, 1) sa_flow_kernel(const SaArgs A, const
     const int S = (int)A.S;
     const int Spad = P.G * TL;
     const int st0 = g * TL, nown = min(TL, S - st0);
-    SaRecF32 *tile = (SaRecF32 *)sac_smem;
+    // field f of record s: 0-2 R - c, 3 lam sin phi, 4-6 N, 7 lam cos phi
+    float4 *const tile = sac_smem;
+    auto sac_slot = [&](int s, int f) -> float * { return (float *)tile + 12 * s + f; };
     if (gridDim.x != (unsigned)P.G || blockDim.x != (unsigned)SA_NT) {
         if (tid == 0) atomicOr(P.flags, SAF_LAUNCH);
         return;
@@ -650,10 +682,14 @@ __global__ void __launch_bounds__(SA_NT, 1) sa_flow_kernel(const SaArgs A, const
     const double cen_a = warp == 0 ? A.cx : (warp == 1 ? A.cy : A.cz);   // axis warps
 
     // ---- static record fields of every dumbbell; the owned state; evaluation 0
-    for (int s = tid; s < S; s += SA_NT) {
-        tile[s].R.w = (float)A.lam[s];
-        tile[s].N.w = 0.f;
-        tile[s].sc = make_float4((float)A.sinp[s], (float)A.cosp[s], 0.f, 0.f);
+    for (int s = tid; s < sac_records(Spad, TL); s += SA_NT) {
+        if (s < S) {
+            *sac_slot(s, 3) = (float)(A.lam[s] * A.sinp[s]);
+            *sac_slot(s, 7) = (float)(A.lam[s] * A.cosp[s]);
+        } else {
+#pragma unroll
+            for (int f = 0; f < 8; ++f) *sac_slot(s, f) = f < 3 ? 1.0e18f : (f == 4 ? 1.f : 0.f);
+        }
     }
     if (warp < 3 && lane < nown) {
         const int a = warp, d = lane, s = st0 + d;
@@ -661,8 +697,8 @@ __global__ void __launch_bounds__(SA_NT, 1) sa_flow_kernel(const SaArgs A, const
         sads_split(R, own.Rh[a][d], own.Rl[a][d]);
         sads_split(N, own.Nh[a][d], own.Nl[a][d]);
         const float Rf = (float)R, Nf = sac_nclear((float)N);
-        ((float *)&tile[s].R)[a] = Rf;
-        ((float *)&tile[s].N)[a] = Nf;
+        *sac_slot(s, a) = Rf;
+        *sac_slot(s, 4 + a) = Nf;
         sac_st(P.words + (size_t)s * 3 + a, Rf, Nf, sac_bit(P.base));
     }
     __syncthreads();
@@ -726,8 +762,8 @@ __global__ void __launch_bounds__(SA_NT, 1) sa_flow_kernel(const SaArgs A, const
             auto has = [&](unsigned long long v) { return ((unsigned)(v >> 32) & 1u) == bit; };
             auto store = [&](int j, unsigned long long v) {
                 const int idx = b0 + j * SA_NT + tid, s = idx / 3, a = idx - 3 * s;
-                ((float *)&tile[s].R)[a] = __uint_as_float((unsigned)v);
-                ((float *)&tile[s].N)[a] = __uint_as_float((unsigned)(v >> 32) & ~1u);
+                *sac_slot(s, a) = __uint_as_float((unsigned)v);
+                *sac_slot(s, 4 + a) = __uint_as_float((unsigned)(v >> 32) & ~1u);
             };
             unsigned long long va[SAC_POLL], vb[SAC_POLL];
             const unsigned long long *base = W + b0 + tid;
@@ -782,21 +818,24 @@ __global__ void __launch_bounds__(SA_NT, 1) sa_flow_kernel(const SaArgs A, const
         // 2. sweep: target t against records sl, sl + NSL, ... in compensated chunks
         float fs[8] = {0, 0, 0, 0, 0, 0, 0, 0}, fc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         if (act) {
-            const SaRecF32 me = tile[st];
-            const float Rx = me.R.x, Ry = me.R.y, Rz = me.R.z, lam = me.R.w;
-            const float Nx = me.N.x, Ny = me.N.y, Nz = me.N.z, sn = me.sc.x, cs = me.sc.y;
+            const float4 mR = tile[3 * st], mN = tile[3 * st + 1];
             for (int t0 = 0; t0 < S; t0 += SAC_CHUNK) {
                 const int len = min(SAC_CHUNK, S - t0);
-                const SaRecF32 *ch = tile + t0;
-                float J[4] = {0, 0, 0, 0}, K[3] = {0, 0, 0};
-                int k = sl;
                 if constexpr (TL >= 4) {
+                    // two records per paired call (the partners missing at the end of
+                    // the last chunk are stand-ins)
+                    const int kmax = (len + 2 * NSL - 1) / (2 * NSL) * (2 * NSL);
                     float2 J2[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
                     float2 K2[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll kSaCoopUnroll
-                    for (; k + NSL < len; k += 2 * NSL)
-                        sa_pair2(t0 + k == st, t0 + k + NSL == st, f2s(Rx), f2s(Ry), f2s(Rz), f2s(lam), f2s(Nx),
-                                 f2s(Ny), f2s(Nz), f2s(sn), f2s(cs), ch[k], ch[k + NSL], J2, K2);
+                    for (int k = sl; k < kmax; k += 2 * NSL) {
+                        const float4 R0 = tile[3 * (t0 + k)], N0 = tile[3 * (t0 + k) + 1];
+                        const float4 R1 = tile[3 * (t0 + k + NSL)], N1 = tile[3 * (t0 + k + NSL) + 1];
+                        const SaPairF32 q{make_float4(R0.x, R1.x, R0.y, R1.y), make_float4(R0.z, R1.z, R0.w, R1.w),
+                                          make_float4(N0.x, N1.x, N0.y, N1.y), make_float4(N0.z, N1.z, N0.w, N1.w)};
+                        sa_pair2(t0 + k == st, t0 + k + NSL == st, f2s(mR.x), f2s(mR.y), f2s(mR.z), f2s(mR.w),
+                                 f2s(mN.x), f2s(mN.y), f2s(mN.z), f2s(-mN.w), q, J2, K2);
+                    }
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         sa_merge(fs[c], fc[c], J2[c].x, 0.f);
@@ -806,15 +845,21 @@ __global__ void __launch_bounds__(SA_NT, 1) sa_flow_kernel(const SaArgs A, const
                     }
                     sa_merge(fs[6], fc[6], J2[3].x, 0.f);
                     sa_merge(fs[6], fc[6], J2[3].y, 0.f);
-                }
-                for (; k < len; k += NSL)
-                    sa_pair<float, SaRecF32>(t0 + k == st, Rx, Ry, Rz, lam, Nx, Ny, Nz, sn, cs, ch[k], J, K);
+                } else {
+                    // TL = 2: a thread holds at most two records of a chunk; the paired
+                    // form with a stand-in was slower (S = 64: 4.0 against 3.68 us per
+                    // averaged step, measured)
+                    float J[4] = {0, 0, 0, 0}, K[3] = {0, 0, 0};
+                    for (int k = sl; k < len; k += NSL)
+                        sa_pair<float, SaRecF32>(t0 + k == st, mR.x, mR.y, mR.z, mR.w, mN.x, mN.y, mN.z, -mN.w,
+                                                 SaRecF32{tile[3 * (t0 + k)], tile[3 * (t0 + k) + 1]}, J, K);
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    sa_merge(fs[c], fc[c], J[c], 0.f);
-                    sa_merge(fs[3 + c], fc[3 + c], K[c], 0.f);
+                    for (int c = 0; c < 3; ++c) {
+                        sa_merge(fs[c], fc[c], J[c], 0.f);
+                        sa_merge(fs[3 + c], fc[3 + c], K[c], 0.f);
+                    }
+                    sa_merge(fs[6], fc[6], J[3], 0.f);
                 }
-                sa_merge(fs[6], fc[6], J[3], 0.f);
             }
         }
         // 3. fold: lanes by transposition, then the target's warps in warp order
@@ -851,8 +896,8 @@ __global__ void __launch_bounds__(SA_NT, 1) sa_flow_kernel(const SaArgs A, const
                     for (int k = 0; k < 3; ++k) sa_merge(ks[k], kc[k], red[r0w + w][6 + k], red[r0w + w][9 + k]);
                 }
                 // the target's orientation in the record the sums were taken at
-                const float4 mN = tile[s].N;
-                const float Nrec = a == 0 ? mN.x : (a == 1 ? mN.y : mN.z);
+                const float mN[3] = {*sac_slot(s, 4), *sac_slot(s, 5), *sac_slot(s, 6)};
+                const float Nrec = mN[a];
                 const float Jf = CJf * fmaf(Nrec, ns + nc, js + jc);
                 float Kf[3];
 #pragma unroll
@@ -866,7 +911,7 @@ __global__ void __launch_bounds__(SA_NT, 1) sa_flow_kernel(const SaArgs A, const
                     Rn = sac_add(own.Rh[a][d], own.Rl[a][d], dtf * Jf);
                     Nn = sac_add(own.Nh[a][d], own.Nl[a][d], dtf * rK);
                 } else {       // x_{n+1} = x_n + dt/2 (rate0 + rate(x~)), N renormalised
-                    const float Nb[3] = {mN.x, mN.y, mN.z};   // the predicted point's orientation
+                    const float *Nb = mN;   // the predicted point's orientation
                     const float NK = fmaf(Nb[0], Kf[0], fmaf(Nb[1], Kf[1], Nb[2] * Kf[2]));
                     float N1[3];
 #pragma unroll
@@ -887,8 +932,8 @@ __global__ void __launch_bounds__(SA_NT, 1) sa_flow_kernel(const SaArgs A, const
                 asm volatile("bar.sync 2, 96;" ::: "memory");
             }
             if (ax) {
-                ((float *)&tile[s].R)[a] = Rn;
-                ((float *)&tile[s].N)[a] = Nn;
+                *sac_slot(s, a) = Rn;
+                *sac_slot(s, 4 + a) = Nn;
                 if (ev + 1 < 2 * P.K)
                     sac_st(P.words + ((size_t)((ev + 1) & 1) * Spad + s) * 3 + a, Rn, Nn,
                            sac_bit(P.base + (unsigned)ev + 1u));
@@ -1208,7 +1253,7 @@ static int sa_coop_setup(dbs_sa *h)
         const void *k = sa_flow_fn(T);
         cudaFuncAttributes fa{};
         SCK(h, cudaFuncGetAttributes(&fa, k));
-        const size_t smem = (size_t)G * T * sizeof(SaRecF32);
+        const size_t smem = (size_t)sac_records(G * T, T) * SAC_REC;
         if (smem + fa.sharedSizeBytes > (size_t)optin) continue;
         // a property of the kernel, shared by every handle: all the device allows
         SCK(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes));
@@ -1246,7 +1291,7 @@ static int sa_coop_step(dbs_sa *h, int64_t n)
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(h->coop_G);
         cfg.blockDim = dim3(SA_NT);
-        cfg.dynamicSmemBytes = (size_t)h->coop_G * h->coop_T * sizeof(SaRecF32);
+        cfg.dynamicSmemBytes = (size_t)sac_records(h->coop_G * h->coop_T, h->coop_T) * SAC_REC;
         cfg.stream = h->stream;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeCooperative;
