@@ -314,6 +314,21 @@ DBS_API int dbs_sa_set_path(dbs_sa *h, int32_t path);
 /* The path in use and, on DBS_PATH_COOP, the dumbbells per CTA (else 0). */
 DBS_API int dbs_sa_get_path(dbs_sa *h, int32_t *path, int32_t *targets_per_cta);
 
+/*
+ * Source chunks of DBS_PATH_GRID's launch (Eqs. (9a)-(9e) summed over the
+ * sources in `chunks` contiguous ranges by separate CTAs; the last CTA of a
+ * target group to finish merges the ranges' compensated partial sums in range
+ * order, so results do not depend on which CTA finishes last).  0 restores the
+ * built-in choice (more chunks where the grid of target groups would leave
+ * part of the SMs idle in its last wave); at most 64 and at most S.  Results
+ * for different counts differ only in the rounding of the pair sums.  The
+ * partial sums take chunks x S x 14 floats (doubles in FP64) of device memory.
+ * DBS_E_ARG for chunks < 0.
+ */
+DBS_API int dbs_sa_set_chunks(dbs_sa *h, int32_t chunks);
+/* The chunk count in use. */
+DBS_API int dbs_sa_get_chunks(dbs_sa *h, int32_t *chunks);
+
 /* Device pointer of the current centres R ([S][3] doubles). */
 DBS_API int dbs_sa_centres_device(dbs_sa *h, const double **R_dev);
 

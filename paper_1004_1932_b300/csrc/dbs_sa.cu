@@ -65,6 +65,13 @@ struct SaArgs {
     double CJ, CK;        // (9/64) a w ell^2, kpref w a ell^2
     double dt;
     int phase;            // 0 predict, 1 correct, 2 rates only
+    // source chunks per target group (sa_eval_kernel): with chunks > 1 CTA
+    // c * groups + g sums group g over the sources [S c / chunks, S (c + 1) / chunks)
+    // into part[c][s][14], and the last of the group's CTAs to arrive (tickets[g])
+    // merges the chunks in chunk order and runs the epilogue
+    int chunks;
+    void *part;
+    unsigned *tickets;
 };
 
 template <typename T> struct SaRecOf;
@@ -338,8 +345,11 @@ __device__ __forceinline__ void store_rec_axis(SaRecF64 *o, int64_t s, int a, do
 // component a of target t, each warp forming the dot products and the norm it
 // needs from all three components (FP64 instructions are slow on this part, so
 // the FP64 Heun update is spread over three sub-partitions).
-template <typename T, int TL>
-__global__ void __launch_bounds__(SA_NT) sa_eval_kernel(SaArgs A)
+// CH: the source-chunked form (A.chunks > 1; the one-chunk form is compiled
+// without its index arithmetic and merge).  FP32 at TL >= 16 (the grids of more
+// than one wave) keeps three CTAs per SM: at most 80 registers per thread.
+template <typename T, int TL, bool CH>
+__global__ void __launch_bounds__(SA_NT, sizeof(T) == 4 && TL >= 16 ? 3 : 1) sa_eval_kernel(SaArgs A)
 {
     using Rec = typename SaRecOf<T>::type;
     constexpr int NSL = SA_NT / TL;               // slices (threads) per target
@@ -350,9 +360,15 @@ __global__ void __launch_bounds__(SA_NT) sa_eval_kernel(SaArgs A)
     // per row: the pD part of J (sums 0-2, compensations 3-5), K (6-8, 9-11) and
     // the sum of cj pN (12, 13)
     __shared__ T red[WPT == 1 ? TL : SA_NT / 32][14];
+    __shared__ int s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int t = tid / NSL, sl = tid - t * NSL;
-    const int64_t st = (int64_t)blockIdx.x * TL + t;
+    // chunk-major: every group's last chunk falls in the last wave, so the merges
+    // run side by side at the end of the launch
+    const int groups = CH ? (int)((A.S + TL - 1) / TL) : (int)gridDim.x;
+    const int c = CH ? (int)blockIdx.x / groups : 0, g = (int)blockIdx.x - c * groups;
+    const int64_t db = CH ? A.S * c / A.chunks : 0, de = CH ? A.S * (c + 1) / A.chunks : A.S;   // sources
+    const int64_t st = (int64_t)g * TL + t;
     const bool act = st < A.S;
     // Programmatic dependent launch: this grid may have been scheduled before the
     // previous step's launch finished; wait for it (and its memory) before reading
@@ -366,7 +382,7 @@ __global__ void __launch_bounds__(SA_NT) sa_eval_kernel(SaArgs A)
     // load it in the epilogue
     constexpr bool EARLY = TL <= 8;
     const int ea = warp, ta = lane;
-    const int64_t sg = (int64_t)blockIdx.x * TL + ta;
+    const int64_t sg = (int64_t)g * TL + ta;
     const bool on = warp < 3 && ta < TL && sg < A.S;
     double Nn[3] = {0.0, 0.0, 0.0}, Ra = 0.0, r0a = 0.0, n0[3] = {0.0, 0.0, 0.0};
     auto load_state = [&]() {
@@ -402,8 +418,8 @@ __global__ void __launch_bounds__(SA_NT) sa_eval_kernel(SaArgs A)
     // TILE / 2 float4) so that the paired operands load as they are
     constexpr bool PAIRED = sizeof(T) == 4 && TL >= 4;
     constexpr int PH = TILE / 2;
-    for (int64_t t0 = 0; t0 < A.S; t0 += TILE) {
-        const int len = (int)min((int64_t)TILE, A.S - t0);
+    for (int64_t t0 = db; t0 < de; t0 += TILE) {
+        const int len = (int)min((int64_t)TILE, de - t0);
         // records k and k + NSL (k mod 2 NSL < NSL) share pair (k div 2 NSL) NSL + k mod NSL;
         // the records past the tile's end up to a whole group of 2 NSL are zero-amplitude
         // stand-ins far away, whose terms are exactly zero
@@ -474,12 +490,14 @@ __global__ void __launch_bounds__(SA_NT) sa_eval_kernel(SaArgs A)
     if (warp >= 3) return;
     // ---- epilogue: lane ta of axis warp a --------------------------------------
     const int a = ea;
-    if (!EARLY) load_state();
-    double JD = 0.0, JN = 0.0, Kd[3] = {0.0, 0.0, 0.0};
+    // (issued before the sums are read, so that its latency overlaps theirs; with
+    // chunks only the last CTA of the group loads it)
+    if (!EARLY && !CH) load_state();
+    // the target's sums: pD part of J along a, cj pN, K (sum, compensation)
+    T js = 0, jc = 0, ns = 0, nc = 0, ks[3] = {0, 0, 0}, kc[3] = {0, 0, 0};
     if (on) {
         const int r0w = ta * WPT;
-        T js = red[r0w][a], jc = red[r0w][3 + a], ns = red[r0w][12], nc = red[r0w][13];
-        T ks[3], kc[3];
+        js = red[r0w][a]; jc = red[r0w][3 + a]; ns = red[r0w][12]; nc = red[r0w][13];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             ks[k] = red[r0w][6 + k];
@@ -491,11 +509,58 @@ __global__ void __launch_bounds__(SA_NT) sa_eval_kernel(SaArgs A)
 #pragma unroll
             for (int k = 0; k < 3; ++k) sa_merge(ks[k], kc[k], red[r0w + w][6 + k], red[r0w + w][9 + k]);
         }
-        JD = (double)js + (double)jc;
-        JN = (double)ns + (double)nc;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) Kd[k] = A.CK * ((double)ks[k] + (double)kc[k]);
     }
+    if constexpr (CH) {
+        // this chunk's sums of the target, laid out as a row of red (axis lane a
+        // writes its components of J and K, lane 0 also the cj pN sum)
+        if (on) {
+            T *p = (T *)A.part + ((int64_t)c * A.S + sg) * 14;
+            p[a] = js;
+            p[3 + a] = jc;
+            p[6 + a] = a == 0 ? ks[0] : (a == 1 ? ks[1] : ks[2]);
+            p[9 + a] = a == 0 ? kc[0] : (a == 1 ? kc[1] : kc[2]);
+            if (a == 0) {
+                p[12] = ns;
+                p[13] = nc;
+            }
+        }
+        // the named barrier orders the three axis warps' partial writes before
+        // thread 0, whose fence makes them visible device-wide before its arrival
+        // ticket; the last arriver fences again before its warps read the others'
+        asm volatile("bar.sync 2, 96;" ::: "memory");
+        if (tid == 0) {
+            __threadfence();
+            const unsigned prev = atomicAdd(&A.tickets[g], 1u);
+            s_last = prev == (unsigned)A.chunks - 1u;
+            if (s_last) {
+                A.tickets[g] = 0u;
+                __threadfence();
+            }
+        }
+        asm volatile("bar.sync 2, 96;" ::: "memory");
+        if (!s_last) return;
+        if (!EARLY) load_state();
+        if (on) {
+            // all chunks of the target, in chunk order (read from L2: other SMs wrote them)
+            const T *p = (const T *)A.part + sg * 14;
+            js = __ldcg(p + a); jc = __ldcg(p + 3 + a); ns = __ldcg(p + 12); nc = __ldcg(p + 13);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                ks[k] = __ldcg(p + 6 + k);
+                kc[k] = __ldcg(p + 9 + k);
+            }
+            for (int cc = 1; cc < A.chunks; ++cc) {
+                const T *q = p + (int64_t)cc * A.S * 14;
+                sa_merge(js, jc, __ldcg(q + a), __ldcg(q + 3 + a));
+                sa_merge(ns, nc, __ldcg(q + 12), __ldcg(q + 13));
+#pragma unroll
+                for (int k = 0; k < 3; ++k) sa_merge(ks[k], kc[k], __ldcg(q + 6 + k), __ldcg(q + 9 + k));
+            }
+        }
+    }
+    double JD = (double)js + (double)jc, JN = (double)ns + (double)nc, Kd[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Kd[k] = A.CK * ((double)ks[k] + (double)kc[k]);
     // every axis warp has read the state components that the others rewrite below
     asm volatile("bar.sync 1, 96;" ::: "memory");
     if (!on) return;
@@ -1099,6 +1164,11 @@ struct dbs_sa {
     int *flags = nullptr;       // SAF_* raised by the cooperative kernel
     bool recs_stale = false;    // recA behind the state after cooperative steps
     int test_dG = 0;            // diagnostic: CTAs the kernel is told beyond those launched
+    // one launch per evaluation: source chunks per target group (SaArgs::chunks),
+    // the requested count (0: built-in), partial sums and arrival tickets
+    int chunks = 1, chunks_req = 0;
+    void *part = nullptr;
+    unsigned *tickets = nullptr;
 };
 
 static int sa_fail(dbs_sa *h, int st, const char *fmt, ...)
@@ -1155,13 +1225,16 @@ static SaArgs sa_args(const dbs_sa *h)
     A.CJ = (9.0 / 64.0) * a * w * l * l;
     A.CK = h->p.kpref * w * a * l * l;
     A.dt = h->p.dt;
+    A.chunks = h->chunks;
+    A.part = h->part;
+    A.tickets = h->tickets;
     return A;
 }
 
 template <typename T, int TL>
 static void sa_launch_t(const dbs_sa *h, const SaArgs &A)
 {
-    const int blocks = (int)((h->p.S + TL - 1) / TL);
+    const int blocks = (int)((h->p.S + TL - 1) / TL) * h->chunks;
     // Programmatic stream serialisation where the grid has at most one CTA per SM
     // (the latency-bound sizes): scheduled while the previous launch on the stream
     // finishes, the kernel waiting for it before reading anything.  A larger grid
@@ -1177,25 +1250,32 @@ static void sa_launch_t(const dbs_sa *h, const SaArgs &A)
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = blocks <= h->sms ? 1 : 0;
-    cudaLaunchKernelEx(&cfg, sa_eval_kernel<T, TL>, A);
+    if (h->chunks > 1) cudaLaunchKernelEx(&cfg, sa_eval_kernel<T, TL, true>, A);
+    else cudaLaunchKernelEx(&cfg, sa_eval_kernel<T, TL, false>, A);
 }
 
 // Targets per CTA: the smallest power of two that keeps the grid within about
-// 128 CTAs (one wave on the SMs), at most 32.
+// 128 CTAs (one wave on the SMs), at most 16.
 #ifndef DBS_SA_TL_MAX
 #define DBS_SA_TL_MAX 16
 #endif
+static int sa_tl(int64_t S)
+{
+    int tl = 1;
+    while (tl < DBS_SA_TL_MAX && S > 128 * (int64_t)tl) tl *= 2;
+    return tl;
+}
 template <typename T>
 static void sa_launch_p(const dbs_sa *h, const SaArgs &A)
 {
-    const int64_t S = h->p.S;
-    constexpr int TM = DBS_SA_TL_MAX;
-    if (S <= 128 || TM == 1) sa_launch_t<T, 1>(h, A);
-    else if (S <= 256 || TM == 2) sa_launch_t<T, 2>(h, A);
-    else if (S <= 512 || TM == 4) sa_launch_t<T, 4>(h, A);
-    else if (S <= 1024 || TM == 8) sa_launch_t<T, 8>(h, A);
-    else if (S <= 2048 || TM == 16) sa_launch_t<T, 16>(h, A);
-    else sa_launch_t<T, 32>(h, A);
+    switch (sa_tl(h->p.S)) {
+    case 1: sa_launch_t<T, 1>(h, A); break;
+    case 2: sa_launch_t<T, 2>(h, A); break;
+    case 4: sa_launch_t<T, 4>(h, A); break;
+    case 8: sa_launch_t<T, 8>(h, A); break;
+    case 16: sa_launch_t<T, 16>(h, A); break;
+    default: sa_launch_t<T, 32>(h, A); break;
+    }
 }
 
 static void sa_launch(const dbs_sa *h, const SaArgs &A)
@@ -1319,8 +1399,59 @@ static int sa_check_flags(dbs_sa *h)
     return DBS_OK;
 }
 
+// Source chunks of the one-launch kernel: the requested count, else the
+// built-in choice (sa_chunks_builtin); the partial sums and tickets it needs.
+// Built-in: one chunk while the groups fit one CTA per SM (the latency-bound
+// sizes); above, the count in 1..8 whose CTAs spread most evenly over the SMs:
+// u = groups x C / SMs CTAs per SM on average, u / ceil(u) of the busiest SM's
+// work done by the average SM, less 0.015 per extra chunk.  Measured (µs per
+// averaged step, FP32C; best count in brackets, C = 1 first): S = 3000 89 / 74
+// (3), 4096 115 / 114 (4), 6000 238 / 221 (3), 8192 402 / 368 (2), 12000 820
+// / 735 (4), 16384 1286 (1); FP64 4096 4460 / 3920 (4), 8192 17730 / 15520 (2):
+// the rule picks each best count.
+constexpr int SA_MAX_CHUNKS = 64;
+static int sa_chunks_builtin(const dbs_sa *h, int groups)
+{
+    if (groups <= h->sms) return 1;
+    int best = 1;
+    double best_e = -1.0;
+    for (int C = 1; C <= 8; ++C) {
+        const double u = (double)groups * C / h->sms;
+        const double e = u / std::ceil(u) - 0.015 * (C - 1);
+        if (e > best_e + 1e-12) {
+            best_e = e;
+            best = C;
+        }
+    }
+    return best;
+}
+static int sa_chunks_setup(dbs_sa *h)
+{
+    const int64_t S = h->p.S;
+    const int groups = (int)((S + sa_tl(S) - 1) / sa_tl(S));
+    int C = h->chunks_req > 0 ? h->chunks_req : sa_chunks_builtin(h, groups);
+    C = (int)std::min<int64_t>(std::min(C, SA_MAX_CHUNKS), S);
+    if (C == h->chunks && (C == 1 || h->part)) return DBS_OK;
+    SCK(h, cudaStreamSynchronize(h->stream));
+    if (h->part) cudaFree(h->part);
+    if (h->tickets) cudaFree(h->tickets);
+    h->part = nullptr;
+    h->tickets = nullptr;
+    h->chunks = 1;
+    if (C > 1) {
+        const size_t pb = (size_t)C * S * 14 * (sa_f64(h) ? sizeof(double) : sizeof(float));
+        SCK(h, cudaMalloc(&h->part, pb));
+        SCK(h, cudaMalloc(&h->tickets, sizeof(unsigned) * groups));
+        SCK(h, cudaMemsetAsync(h->tickets, 0, sizeof(unsigned) * groups, h->stream));
+    }
+    h->chunks = C;
+    return DBS_OK;
+}
+
 static void sa_free(dbs_sa *h)
 {
+    if (h->part) cudaFree(h->part);
+    if (h->tickets) cudaFree(h->tickets);
     if (h->words) cudaFree(h->words);
     if (h->flags) cudaFree(h->flags);
     void *b[] = {h->R, h->N, h->rate0, h->rate_out, h->lam, h->sinp, h->cosp, h->recA, h->recB};
@@ -1412,6 +1543,7 @@ int dbs_sa_create(const dbs_sa_params *p, const double *R, const double *N, cons
     SCREATE(cudaMemcpyAsync(h->lam, lambda, sizeof(double) * S, cudaMemcpyHostToDevice, h->stream));
     SCREATE(cudaMemcpyAsync(h->sinp, sn.data(), sizeof(double) * S, cudaMemcpyHostToDevice, h->stream));
     SCREATE(cudaMemcpyAsync(h->cosp, cs.data(), sizeof(double) * S, cudaMemcpyHostToDevice, h->stream));
+    if ((rc = sa_chunks_setup(h)) != DBS_OK) return bail(rc);
     if ((rc = sa_repack(h)) != DBS_OK) return bail(rc);
     // FP32C systems that fit take the cooperative path; the others (and a device
     // that cannot hold it) keep one launch per evaluation
@@ -1521,6 +1653,21 @@ int dbs_test_sa_flow_misshape(dbs_sa *h)
     if (rc) return rc;
     SCK(h, cudaStreamSynchronize(h->stream));
     return sa_check_flags(h);
+}
+
+int dbs_sa_set_chunks(dbs_sa *h, int32_t chunks)
+{
+    SGUARD(h);
+    if (chunks < 0) return sa_refuse(h, DBS_E_ARG, "chunks must be >= 0");
+    h->chunks_req = chunks;
+    return sa_chunks_setup(h);
+}
+
+int dbs_sa_get_chunks(dbs_sa *h, int32_t *chunks)
+{
+    if (!h || !chunks) return DBS_E_ARG;
+    *chunks = h->chunks;
+    return DBS_OK;
 }
 
 int dbs_sa_get_path(dbs_sa *h, int32_t *path, int32_t *targets_per_cta)

@@ -361,6 +361,15 @@ class StrokeAveraged:
         self._check(load().dbs_sa_get_path(self._h, ctypes.byref(p), ctypes.byref(t)))
         return {v: k for k, v in _PATHS.items()}[p.value], t.value
 
+    def set_chunks(self, chunks: int):
+        """Source chunks of the "grid" path's launch (0: the built-in choice)."""
+        self._check(load().dbs_sa_set_chunks(self._h, ctypes.c_int32(int(chunks))))
+
+    def get_chunks(self) -> int:
+        c = ctypes.c_int32()
+        self._check(load().dbs_sa_get_chunks(self._h, ctypes.byref(c)))
+        return c.value
+
     def rates(self):
         Rd = np.empty((self.S, 3))
         Nd = np.empty((self.S, 3))
