@@ -214,7 +214,8 @@ struct FlowArgs {
 template <int T>
 struct FlowOwner {
     double x[6][T];                   // x - centre, spheres 2s (0..2) and 2s+1 (3..5)
-    double R[3][T];                   // stroke-average sums (trapezoid rule)
+    float2 Q[3][T];                   // stroke-average sums (trapezoid rule) of x_a + x_b - 2 c,
+                                      // double-single (see flush_fp64)
     float2 xs[6][T];                  // x as double-single (hi, lo): the critical path's copy,
                                       // set from x at launch, then advanced with x
     float lamh[T], laml[T], sph[T], spl[T], cph[T], cpl[T];
@@ -411,8 +412,16 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
         t = ds_of(A.cosphi[s]);
         own.cph[d] = t.h; own.cpl[d] = t.l;
         if (A.avg_m > 0) {
+            // the FP64 sum carried between launches, sum of w_i R_i with R the
+            // geometric centre and the weights w summing to 1/2 + (k mod m) after
+            // sample k, as Q = sum of w_i (x_a + x_b - 2 c)_i = 2 (sum - c sum w)
+            const int64_t kl = P.n0 - A.avg_n0;
+            const double sw = 0.5 + (double)(kl > 0 ? kl % A.avg_m : 0);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) own.R[k][d] = A.Racc[3 * (int64_t)s + k];
+            for (int k = 0; k < 3; ++k) {
+                const ds q = ds_of(2.0 * (A.Racc[3 * (int64_t)s + k] - cen[k] * sw));
+                own.Q[k][d] = make_float2(q.h, q.l);
+            }
         }
         const unsigned bit = flow_bit(P.base);
 #pragma unroll
@@ -441,6 +450,13 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
     // flight (the end of the launch runs the last one).
     float hsa = 0.f, hsb = 0.f, hza = 0.f, hzb = 0.f;   // v0 + v1 and the normals along a
     int64_t hn = -1;                                    // -1: nothing pending
+    // the stroke average's sample index k = n + 1 - avg_n0 of the next flush and its
+    // residue mod avg_m, advanced by one per flush (the flushes take consecutive
+    // steps): no 64-bit division per step.  (A 32-bit residue computed from n, and
+    // advancing only with averaging on, measured slower: the gap's code is
+    // sensitive to its schedule.)
+    int64_t k_next = P.n0 + 1 - A.avg_n0;
+    int64_t k_mod = A.avg_m > 0 ? ((k_next % A.avg_m) + A.avg_m) % A.avg_m : 0;
     auto flush_fp64 = [&]() {
         if (hn < 0) return;
         const int a = warp, d = lane;
@@ -453,20 +469,27 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
         own.x[a][d] = xa;
         own.x[a + 3][d] = xb;
         if (!(finite1(xa) && finite1(xb))) atomicOr(A.flags, FLAG_NONFINITE);
-        const int64_t k_local = hn + 1 - A.avg_n0;
+        const int64_t k_local = k_next;   // hn + 1 - avg_n0
         if (A.avg_m > 0 && k_local > 0) {
-            const double Rt = 0.5 * (xa + xb) + (a == 0 ? A.cx : (a == 1 ? A.cy : A.cz));
-            double acc = own.R[a][d];
-            if ((k_local % A.avg_m) == 0) {
-                acc += 0.5 * Rt;
+            // the sample x_a + x_b of step n + 1 from the double-single copy (FP32
+            // instructions; three FP64 ones per step here cost 1-2 % of the step)
+            const ds xs = ds_add({own.xs[a][d].x, own.xs[a][d].y}, {own.xs[a + 3][d].x, own.xs[a + 3][d].y});
+            ds q = {own.Q[a][d].x, own.Q[a][d].y};
+            if (k_mod == 0) {   // the period's last sample (weight 1/2), the next one's first
+                const ds half = {0.5f * xs.h, 0.5f * xs.l};
+                q = ds_add(q, half);
                 const int64_t kidx = k_local / A.avg_m - 1;
-                if (kidx < A.avg_maxk) A.Rbar[kidx * 3 * A.S + 3 * (int64_t)(st0 + d) + a] = acc / (double)A.avg_m;
-                acc = 0.5 * Rt;
+                if (kidx < A.avg_maxk)
+                    A.Rbar[kidx * 3 * A.S + 3 * (int64_t)(st0 + d) + a] =
+                        (a == 0 ? A.cx : (a == 1 ? A.cy : A.cz)) + 0.5 * ds_to_double(q) / (double)A.avg_m;
+                q = half;
             } else {
-                acc += Rt;
+                q = ds_add(q, xs);
             }
-            own.R[a][d] = acc;
+            own.Q[a][d] = make_float2(q.h, q.l);
         }
+        ++k_next;
+        if (++k_mod == A.avg_m) k_mod = 0;
         hn = -1;
     };
 
@@ -687,8 +710,11 @@ __global__ void __launch_bounds__(FLOW_NT, 1) flow_kernel(const EvalArgs A, cons
             A.Fd[o + k] = (double)own.F[k][d];
         }
         if (A.avg_m > 0) {
+            const int64_t kl = P.n0 + P.K - A.avg_n0;   // the last sample taken
+            const double sw = 0.5 + (double)(kl % A.avg_m);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) A.Racc[3 * (int64_t)s + k] = own.R[k][d];
+            for (int k = 0; k < 3; ++k)
+                A.Racc[3 * (int64_t)s + k] = cen[k] * sw + 0.5 * ds_to_double({own.Q[k][d].x, own.Q[k][d].y});
         }
     }
     if (g == 0 && tid == 0) *A.step = P.n0 + P.K;

@@ -127,6 +127,26 @@ def test_coop_period_averages_match_oracle():
     assert np.abs(got - ref).max() <= 1e-4 * s.ell
 
 
+def test_coop_period_averages_across_launches_match_grid_path():
+    # averaging enabled mid-run and launches that end mid-period: the cooperative
+    # kernel carries the period sums between launches in the grid path's FP64 form
+    s = inputs.make_suspension(40, seed=14, side=12.0, mobility="rpy")
+    m, periods = 700, 3
+    out = []
+    for path in ("grid", "coop"):
+        with _handle(s) as h:
+            h.set_path(path)
+            h.step(50)
+            h.enable_period_average(m, max_periods=periods)
+            for n in (37, 1500, 563):
+                h.step(n)
+            assert h.period_count() == periods
+            out.append((h.period_averages(0, periods), h.positions()))
+    (ag, xg), (ac, xc) = out
+    assert np.abs(xc - xg).max() <= 1e-6 * s.ell
+    assert np.abs(ac - ag).max() <= 1e-6 * s.ell
+
+
 @pytest.mark.parametrize("tag", [0xFFFFFFFF - 300, 0xFFFFFFFF - 3000])
 def test_coop_tag_wraparound(tag):
     # the first launch (first case) or the second (second case) would run past
