@@ -4,7 +4,8 @@
   CTAs and merged in range order by the last CTA of each target group, the
   rates follow the FP64 oracle within the one-chunk tolerances (FP32C 1e-5,
   FP64 1e-12 of the largest rate) for chunk counts that do and do not fall on
-  tile boundaries, with ragged last groups and ranges of a single source.
+  tile boundaries, with ragged last groups and ranges of a single source, and
+  at the benchmark's size (S = 8192) and S = 12000 on the built-in split.
 * Heun steps on the chunked launch follow the oracle's, two runs are
   bit-identical (the merge order does not depend on which CTA finishes last),
   and changing the count mid-run continues the same trajectory.
@@ -17,6 +18,7 @@ import math
 import numpy as np
 import pytest
 import torch
+from scipy.spatial import cKDTree
 
 import oracle
 from paper_1004_1932_b300 import dbs, inputs
@@ -51,6 +53,26 @@ def test_chunked_rates_match_oracle(S, C, prec):
         Rd, Nd = h.rates()
     assert _relerr(Rd, Rd_ref) <= TOL[prec]
     assert _relerr(Nd, Nd_ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("S", [8192, 12000])
+def test_benchmark_size_rates_on_the_built_in_split(S):
+    # the launch the benchmark times at S = 8192 (2 chunks) and a size whose
+    # built-in count does not divide the tiles (12000: 4 chunks of 3000 sources)
+    s = inputs.paper_scale(S, seed=5)
+    Rd_ref, Nd_ref = oracle.sa_rates(s.R0, s.N0, s.phi, s.lam, **_kw(s))
+    with _sa(s) as h:
+        assert h.get_chunks() > 1
+        Rd, Nd = h.rates()
+    # at these sizes the FP32 rounding of the records' positions (relative to
+    # the centre c of the bounding box) sets the error: one ulp of max|R - c| in
+    # each coordinate of D, amplified 5x relatively by the D^-5 of the K term
+    # at the closest pair
+    c = 0.5 * (s.R0.min(0) + s.R0.max(0))
+    dmin = cKDTree(s.R0).query(s.R0, k=2)[0][:, 1].min()
+    tol = TOL["fp32c"] + 5 * math.sqrt(3) * float(np.spacing(np.float32(np.abs(s.R0 - c).max()))) / dmin
+    assert _relerr(Rd, Rd_ref) <= tol
+    assert _relerr(Nd, Nd_ref) <= tol
 
 
 @pytest.mark.parametrize("prec", ["fp32c", "fp64"])
