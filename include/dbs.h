@@ -353,6 +353,17 @@ DBS_API int dbs_pair_distance_error(int64_t S, const double *A0_dev, const doubl
                             const double *B0_dev, const double *B1_dev, double *out,
                             void *stream);
 
+/*
+ * The same four values into out_dev (device, 4 doubles), enqueued on `stream`
+ * without synchronising (one kernel launch; the caller reads out_dev after the
+ * stream has reached it).  Calls share one device array of partial sums: calls
+ * on one stream are ordered; calls on different streams must not overlap.
+ * DBS_E_ARG for S < 2 or null pointers, DBS_E_CUDA if the launch fails.
+ */
+DBS_API int dbs_pair_distance_error_async(int64_t S, const double *A0_dev, const double *A1_dev,
+                                          const double *B0_dev, const double *B1_dev, double *out_dev,
+                                          void *stream);
+
 /* ======================================================================== */
 /* Cluster-resident execution: one system or an ensemble of independent ones */
 /* ======================================================================== */

@@ -1030,7 +1030,9 @@ __global__ void __launch_bounds__(SA_NT, 1) sa_flow_kernel(const SaArgs A, const
 // tiles in a grid-stride loop, reduce their pairs in a fixed tree order into a
 // per-CTA partial, and the last CTA to finish (arrival ticket) combines the
 // partials in CTA order, so the result does not depend on CTA timing.  The
-// partials live in a file-scope device array: calls are serialised on the host.
+// partials live in a file-scope device array: calls are serialised on the host,
+// and enqueued calls (dbs_pair_distance_error_async) must not overlap on
+// different streams.
 constexpr int PD_T = 32;
 constexpr int PD_BT = 256;
 constexpr int PD_MAX_BLOCKS = 1184;
@@ -1057,8 +1059,9 @@ __device__ __forceinline__ double pd_dist(const double *a, const double *b)
     return sqrt(fma(z, z, fma(y, y, x * x)));
 }
 
+// out: when not null, also the final {max, RMS of the error, RMS of dB, pairs}
 __global__ void __launch_bounds__(PD_BT) pair_dist_kernel(int64_t S, const double *A0, const double *A1,
-                                                           const double *B0, const double *B1)
+                                                           const double *B0, const double *B1, double *out)
 {
     __shared__ double rows[4][PD_T][3], cols[4][PD_T][3];
     __shared__ double smax[PD_BT], ssq[PD_BT], sref[PD_BT];
@@ -1139,6 +1142,13 @@ __global__ void __launch_bounds__(PD_BT) pair_dist_kernel(int64_t S, const doubl
         g_pd_out[1] = ssq[0];
         g_pd_out[2] = sref[0];
         g_pd_ticket = 0u;
+        if (out) {
+            const double pairs = (double)S * (double)(S - 1) / 2.0;
+            out[0] = smax[0];
+            out[1] = sqrt(ssq[0] / pairs);
+            out[2] = sqrt(sref[0] / pairs);
+            out[3] = pairs;
+        }
     }
 }
 
@@ -1703,7 +1713,7 @@ int dbs_pair_distance_error(int64_t S, const double *A0, const double *A1, const
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t nb = (S + PD_T - 1) / PD_T, ntiles = nb * (nb + 1) / 2;
     const int blocks = (int)std::min<int64_t>(PD_MAX_BLOCKS, ntiles);
-    pair_dist_kernel<<<blocks, PD_BT, 0, st>>>(S, A0, A1, B0, B1);
+    pair_dist_kernel<<<blocks, PD_BT, 0, st>>>(S, A0, A1, B0, B1, nullptr);
     double hb[3];
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyFromSymbolAsync(hb, g_pd_out, sizeof(hb), 0, cudaMemcpyDeviceToHost, st);
@@ -1715,6 +1725,16 @@ int dbs_pair_distance_error(int64_t S, const double *A0, const double *A1, const
     out[2] = std::sqrt(hb[2] / pairs);
     out[3] = pairs;
     return DBS_OK;
+}
+
+int dbs_pair_distance_error_async(int64_t S, const double *A0, const double *A1, const double *B0,
+                                  const double *B1, double *out_dev, void *stream)
+{
+    if (S < 2 || S > (int64_t)1 << 31 || !A0 || !A1 || !B0 || !B1 || !out_dev) return DBS_E_ARG;
+    const int64_t nb = (S + PD_T - 1) / PD_T, ntiles = nb * (nb + 1) / 2;
+    const int blocks = (int)std::min<int64_t>(PD_MAX_BLOCKS, ntiles);
+    pair_dist_kernel<<<blocks, PD_BT, 0, (cudaStream_t)stream>>>(S, A0, A1, B0, B1, out_dev);
+    return cudaGetLastError() == cudaSuccess ? DBS_OK : DBS_E_CUDA;
 }
 
 }  // extern "C"

@@ -403,6 +403,16 @@ def pair_distance_error(S, A0, A1, B0, B1, stream=None):
     return {"max": float(out[0]), "rms": float(out[1]), "ref_rms": float(out[2]), "pairs": int(out[3])}
 
 
+def pair_distance_error_async(S, A0, A1, B0, B1, out, stream=None):
+    """The same four values (max, RMS, RMS of dB, pairs) into ``out``, a device
+    tensor of 4 doubles, enqueued on ``stream`` without synchronising."""
+    rc = load().dbs_pair_distance_error_async(
+        _i64(int(S)), *(ctypes.c_void_p(_devptr(t)) for t in (A0, A1, B0, B1, out)),
+        None if stream is None else ctypes.c_void_p(_devptr_stream(stream)))
+    if rc != OK:
+        raise DbsError(rc, "dbs_pair_distance_error_async")
+
+
 class Ensemble:
     """Independent suspensions advanced together on thread-block clusters
     (``dbs_ensemble_*``).  Members stay usable as ordinary handles."""

@@ -87,6 +87,8 @@ def test_sa_and_compare_reject_bad_sizes(lib):
     out = np.zeros(4)
     assert lib.dbs_pair_distance_error(ctypes.c_int64(1), None, None, None, None,
                                        out.ctypes.data_as(dp), None) == dbs.E_ARG
+    assert lib.dbs_pair_distance_error_async(ctypes.c_int64(1), None, None, None, None, None,
+                                             None) == dbs.E_ARG
 
 
 def test_null_handles_are_rejected(lib):

@@ -245,3 +245,13 @@ def test_pair_distance_error_matches_oracle(S):
     assert got["max"] == pytest.approx(ref["max"], rel=1e-12)
     assert got["rms"] == pytest.approx(ref["rms"], rel=1e-10)
     assert got["ref_rms"] == pytest.approx(ref["ref_rms"], rel=1e-10)
+    # the enqueued form: the same kernel, its values left on the device (two calls
+    # in a row on one stream, into two rows)
+    out = torch.zeros((2, 4), dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    dbs.pair_distance_error_async(S, *t, out[0], stream=s)
+    dbs.pair_distance_error_async(S, t[0], t[2], t[0], t[2], out[1], stream=s)
+    s.synchronize()
+    o = out.cpu().numpy()
+    assert list(o[0]) == [got["max"], got["rms"], got["ref_rms"], got["pairs"]]
+    assert o[1, 0] == 0.0 and o[1, 1] == 0.0 and o[1, 3] == S * (S - 1) / 2
