@@ -38,7 +38,7 @@ struct SdOwn {
     float hc[T], bss[T], f[T];   // h_c, b^ss and the current iterate f at the point
     float r0[6][T];              // predictor rates dR/dt, dN/dt
     float lam[T], sph[T], cph[T];
-    double Racc[3][T];           // stroke-average running sums
+    float2 Q[3][T];              // stroke-average running sums of R - c, double-single
 };
 
 // the first iterate of a point with axis N and rest length L: h_c, b^ss, f_(1)
@@ -117,7 +117,14 @@ __global__ void __launch_bounds__(FLOW_NT, 1) sd_flow_kernel(const EvalArgs A, c
             own.Nh[k][d] = Nk.h;
             own.Nl[k][d] = Nk.l;
             own.Np[k][d] = Nk.h;
-            if (A.avg_m > 0) own.Racc[k][d] = A.Racc[3 * (int64_t)s + k];
+            if (A.avg_m > 0) {
+                // the FP64 sum carried between launches, sum of w_i R_i with weights
+                // summing to 1/2 + (k mod m) after sample k, as sum of w_i (R_i - c)
+                const int64_t kl = P.n0 - A.avg_n0;
+                const double sw = 0.5 + (double)(kl > 0 ? kl % A.avg_m : 0);
+                const ds q = ds_of(A.Racc[3 * (int64_t)s + k] - cen[k] * sw);
+                own.Q[k][d] = make_float2(q.h, q.l);
+            }
             const float pa = (float)(x[k] - cen[k]), pb = (float)(x[3 + k] - cen[k]);
             const float ga = g_clear(f * Nk.h * k8), gb = g_clear(-f * Nk.h * k8);
             put_axis(tile + s, k, pa, ga, pb, gb);
@@ -139,6 +146,10 @@ __global__ void __launch_bounds__(FLOW_NT, 1) sd_flow_kernel(const EvalArgs A, c
     // double-single state, renormalises N and accumulates the stroke average.
     float incR[3] = {0.f, 0.f, 0.f}, incN[3] = {0.f, 0.f, 0.f};
     int64_t hn = -1;
+    // the stroke average's sample index k = n + 1 - avg_n0 of the next update and
+    // its residue mod avg_m, advanced by one per update (consecutive steps)
+    int64_t k_next = P.n0 + 1 - A.avg_n0;
+    int64_t k_mod = A.avg_m > 0 ? ((k_next % A.avg_m) + A.avg_m) % A.avg_m : 0;
     auto state_update = [&]() {
         if (hn < 0) return;
         const int d = lane;
@@ -161,24 +172,28 @@ __global__ void __launch_bounds__(FLOW_NT, 1) sd_flow_kernel(const EvalArgs A, c
             own.Nh[k][d] = Nk.h;
             own.Nl[k][d] = Nk.l;
         }
-        const int64_t k_local = hn + 1 - A.avg_n0;
-        if (A.avg_m > 0 && k_local > 0) {   // trapezoid rule, as the spring model's
-            const bool end = (k_local % A.avg_m) == 0;
-            const int64_t kidx = k_local / A.avg_m - 1;
+        const int64_t k_local = k_next;   // hn + 1 - avg_n0
+        if (A.avg_m > 0 && k_local > 0) {   // trapezoid rule, as the spring model's, in double-single
+            const bool end = k_mod == 0;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                const double Rt = ((double)own.Rh[k][d] + (double)own.Rl[k][d]) + cen[k];
-                double acc = own.Racc[k][d];
+                const ds Rk = {own.Rh[k][d], own.Rl[k][d]};
+                ds q = {own.Q[k][d].x, own.Q[k][d].y};
                 if (end) {
-                    acc += 0.5 * Rt;
-                    if (kidx < A.avg_maxk) A.Rbar[kidx * 3 * A.S + 3 * (int64_t)(st0 + d) + k] = acc / (double)A.avg_m;
-                    acc = 0.5 * Rt;
+                    const ds half = {0.5f * Rk.h, 0.5f * Rk.l};
+                    q = ds_add(q, half);
+                    const int64_t kidx = k_local / A.avg_m - 1;
+                    if (kidx < A.avg_maxk)
+                        A.Rbar[kidx * 3 * A.S + 3 * (int64_t)(st0 + d) + k] = cen[k] + ds_to_double(q) / (double)A.avg_m;
+                    q = half;
                 } else {
-                    acc += Rt;
+                    q = ds_add(q, Rk);
                 }
-                own.Racc[k][d] = acc;
+                own.Q[k][d] = make_float2(q.h, q.l);
             }
         }
+        ++k_next;
+        if (++k_mod == A.avg_m) k_mod = 0;
         hn = -1;
     };
     auto gap = [&]() {
@@ -386,7 +401,11 @@ __global__ void __launch_bounds__(FLOW_NT, 1) sd_flow_kernel(const EvalArgs A, c
         for (int k = 0; k < 3; ++k) {
             x[k] = fma(-0.5 * L, N[k] * inv, R[k]);
             x[3 + k] = fma(0.5 * L, N[k] * inv, R[k]);
-            if (A.avg_m > 0) A.Racc[3 * (int64_t)s + k] = own.Racc[k][d];
+            if (A.avg_m > 0) {
+                const int64_t kl = P.n0 + P.K - A.avg_n0;   // the last sample taken
+                A.Racc[3 * (int64_t)s + k] =
+                    cen[k] * (0.5 + (double)(kl % A.avg_m)) + ds_to_double({own.Q[k][d].x, own.Q[k][d].y});
+            }
         }
     }
     if (g == 0 && tid == 0) *A.step = P.n0 + P.K;
