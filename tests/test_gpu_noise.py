@@ -95,6 +95,26 @@ def test_noise_continues_across_launches_and_paths():
     assert np.abs(x - ref).max() <= 1e-4 * s.ell
 
 
+def test_noisy_period_averages_agree_across_paths():
+    # the stroke averages of a noisy run: grid path (FP64 sums in the epilogue,
+    # its noisy trajectory checked against the oracle above) against the
+    # cooperative one (double-single sums of the noisy positions within a
+    # launch), with a period that straddles two launches
+    s = inputs.make_suspension(24, seed=9, side=9.0, mobility="rpy")
+    kT, seed, m, periods = _kT_for(s), 77, 500, 3
+    s.dt = 1.0 / m
+    out = []
+    for path in ("grid", "coop"):
+        with _handle(s) as h:
+            h.set_path(path)
+            h.set_noise(kT, seed)
+            h.enable_period_average(m, max_periods=periods)
+            h.step(700)
+            h.step(800)
+            out.append(h.period_averages(0, periods))
+    assert np.abs(out[1] - out[0]).max() <= 1e-6 * s.ell
+
+
 def test_free_spheres_diffuse_with_stokes_einstein_variance():
     s, F = inputs.colloids(2000, mobility="oseen")
     kT, nsteps = 1e-3, 200
