@@ -1265,20 +1265,23 @@ static void sa_launch_t(const dbs_sa *h, const SaArgs &A)
 }
 
 // Targets per CTA: the smallest power of two that keeps the grid within about
-// 128 CTAs (one wave on the SMs), at most 16.
-#ifndef DBS_SA_TL_MAX
-#define DBS_SA_TL_MAX 16
-#endif
-static int sa_tl(int64_t S)
+// 128 CTAs (one wave on the SMs), at most 16; 32 for FP32 once groups of 32
+// outnumber the SMs, where the source chunks spread them over the SMs and each
+// source tile then serves twice the targets (S = 6000 / 8192 / 12000 / 16384:
+// 196 / 334 / 693 / 1195 -> 180 / 302 / 638 / 1123 us per averaged step,
+// measured; at S = 2500 - 4096 and in FP64 up to 4096 it was 3-45 % slower, at
+// FP64 8192 equal).
+static int sa_tl(int64_t S, bool f64, int sms)
 {
+    const int tl_max = (!f64 && S > 32 * (int64_t)sms) ? 32 : 16;
     int tl = 1;
-    while (tl < DBS_SA_TL_MAX && S > 128 * (int64_t)tl) tl *= 2;
+    while (tl < tl_max && S > 128 * (int64_t)tl) tl *= 2;
     return tl;
 }
 template <typename T>
 static void sa_launch_p(const dbs_sa *h, const SaArgs &A)
 {
-    switch (sa_tl(h->p.S)) {
+    switch (sa_tl(h->p.S, sa_f64(h), h->sms)) {
     case 1: sa_launch_t<T, 1>(h, A); break;
     case 2: sa_launch_t<T, 2>(h, A); break;
     case 4: sa_launch_t<T, 4>(h, A); break;
@@ -1438,7 +1441,8 @@ static int sa_chunks_builtin(const dbs_sa *h, int groups)
 static int sa_chunks_setup(dbs_sa *h)
 {
     const int64_t S = h->p.S;
-    const int groups = (int)((S + sa_tl(S) - 1) / sa_tl(S));
+    const int tl = sa_tl(S, sa_f64(h), h->sms);
+    const int groups = (int)((S + tl - 1) / tl);
     int C = h->chunks_req > 0 ? h->chunks_req : sa_chunks_builtin(h, groups);
     C = (int)std::min<int64_t>(std::min(C, SA_MAX_CHUNKS), S);
     if (C == h->chunks && (C == 1 || h->part)) return DBS_OK;

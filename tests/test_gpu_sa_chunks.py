@@ -110,8 +110,11 @@ def test_changing_the_count_mid_run_continues_the_trajectory():
 
 
 def _builtin(S, sms):
-    tl = 1                       # targets per CTA: grid within about 128 CTAs, at most 16
-    while tl < 16 and S > 128 * tl:
+    # targets per CTA: grid within about 128 CTAs, at most 16, or 32 (FP32) once
+    # groups of 32 outnumber the SMs
+    tl_max = 32 if S > 32 * sms else 16
+    tl = 1
+    while tl < tl_max and S > 128 * tl:
         tl *= 2
     groups = -(-S // tl)
     if groups <= sms:
